@@ -427,7 +427,7 @@ static void one_step(orc_sim *s)
     /* ---- steps 4-7 per node ---- */
     const double omega = 1.0 / s->p.tau;
     const double cmu = 1.0 - s->p.mu;
-    const double c_noise = s->p.sigma / 150994944.0; /* sigma / (9 * 2^24) */
+    const double two_sigma = 2.0 * s->p.sigma;
     for (int y = yr; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             size_t n = (size_t)y * W + x;
@@ -456,19 +456,25 @@ static void one_step(orc_sim *s)
                     double fss = (WQ[i] * rho) * t1;
                     fo[i] = fs[i] - omega * (fs[i] - fss);
                 }
-                /* step 6: mass-conserving noise (Eq. 4), 24-bit uniforms */
+                /* step 6: mass-conserving noise (Eq. 4). Nine uniforms u_i on (0,1)
+                 * with 23 random bits each (two Philox blocks: the top 23 bits of
+                 * the eight words, and the low 9+9+5 bits of the first three);
+                 * eta~_i = sigma (2 u_i - 1), so eta_i = eta~_i - mean(eta~) =
+                 * 2 sigma (u_i - mean(u)). */
                 if (s->p.sigma != 0.0) {
                     uint32_t a[4], b[4];
                     draw(s, (uint32_t)n, t, STREAM_NOISE + 0u, a);
                     draw(s, (uint32_t)n, t, STREAM_NOISE + 1u, b);
                     uint32_t wd[8] = {a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3]};
-                    int32_t sv[NQ];
-                    int32_t S = 0;
-                    for (int i = 0; i < 8; ++i) sv[i] = 2 * (int32_t)(wd[i] >> 8) + 1 - 16777216;
-                    sv[8] = 2 * (int32_t)(((wd[0] & 255u) << 16) | ((wd[1] & 255u) << 8) | (wd[2] & 255u)) +
-                            1 - 16777216;
-                    for (int i = 0; i < NQ; ++i) S += sv[i];
-                    for (int i = 0; i < NQ; ++i) fo[i] = fo[i] + c_noise * (double)(9 * sv[i] - S);
+                    uint32_t m[NQ];
+                    for (int i = 0; i < 8; ++i) m[i] = wd[i] >> 9;
+                    m[8] = ((wd[0] & 511u) << 14) | ((wd[1] & 511u) << 5) | ((wd[2] & 511u) >> 4);
+                    double u[NQ];
+                    for (int i = 0; i < NQ; ++i) u[i] = ((double)m[i] + 0.5) * 1.1920928955078125e-07;
+                    double S = u[0];
+                    for (int i = 1; i < NQ; ++i) S = S + u[i];
+                    const double ubar = S / 9.0;
+                    for (int i = 0; i < NQ; ++i) fo[i] = fo[i] + two_sigma * (u[i] - ubar);
                 }
                 /* step 7: correct negative populations */
                 if (s->p.negfix_mode == NEGFIX_LITERAL) {

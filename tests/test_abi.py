@@ -1,0 +1,87 @@
+"""The C-ABI library loads, exports every function declared in include/lbm.h,
+and its host-only logic (parameter checks, footprint, error strings) works
+without a GPU. No compute call is made here."""
+import ctypes
+
+import pytest
+
+from paper_2303_02210_gb300 import lbm
+from paper_2303_02210_gb300 import workloads as wl
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return lbm.load_library()
+
+
+def test_exports_every_declared_function(lib):
+    names = lbm.header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lbm._SIGNATURES), "binding and header disagree"
+
+
+def test_struct_layouts_match_header():
+    # 13 doubles, 1 uint64, 14 int32 words
+    assert ctypes.sizeof(lbm.lbm_params_t) == 13 * 8 + 8 + 14 * 4
+    assert ctypes.sizeof(lbm.lbm_stats_t) == 13 * 8 + 6 * 8 + 6 * 4
+
+
+def test_version_and_strerror(lib):
+    assert b"sm_103a" in lib.lbm_version()
+    for code in (0, -1, -2, -3, -4, -5, 12345):
+        assert lib.lbm_strerror(code)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(tau=0.5), dict(tau=0.4), dict(width=0), dict(height=2), dict(width=40000),
+    dict(rho_cell=0.0), dict(growth_rate=-1.0), dict(sigma=-0.1), dict(growth_mode=7),
+    dict(front_kind=9), dict(wall_mode=3), dict(negfix_mode=2), dict(y_periodic=2),
+    dict(growth_mode="density", rho0=0.0), dict(growth_mode="band", band_rows=0),
+    dict(front_kind="sinusoidal", front_kmin=5, front_kmax=2),
+])
+def test_validate_rejects(bad):
+    p = wl.lattice_small()
+    p.update(bad)
+    assert lbm.lbm_validate(p) == -1
+
+
+def test_validate_accepts_workloads():
+    for fn in wl.WORKLOADS.values():
+        assert lbm.lbm_validate(fn()) == 0
+        assert lbm.lbm_validate(fn(), "fp64") == 0
+    assert lbm.lbm_validate(wl.lattice_small(width=1)) == 0
+
+
+def test_footprint_scales_with_lattice_and_precision():
+    a = lbm.lbm_footprint(wl.lattice_small())
+    b = lbm.lbm_footprint(wl.lattice_small(), "fp64")
+    c = lbm.lbm_footprint(wl.lattice_edge())
+    # two FP32 copies of 9 populations at 4096 x 2048 dominate
+    assert c >= 2 * 9 * 4096 * 2048 * 4
+    assert b > a
+    assert lbm.lbm_footprint(wl.lattice_small(width=33)) == lbm.lbm_footprint(wl.lattice_small(width=64))
+
+
+def test_footprint_rejects_null(lib):
+    p = lbm.make_params(wl.lattice_small())
+    assert lib.lbm_footprint(ctypes.byref(p), None) == -1
+    assert lib.lbm_validate(None) == -1
+
+
+def test_handle_calls_reject_null(lib):
+    assert lib.lbm_step(None, 1) == -1
+    assert lib.lbm_stats(None, None) == -1
+    assert lib.lbm_front_heights(None, None, None, None) == -1
+    lib.lbm_destroy(None)
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    p = lbm.make_params(wl.lattice_small())
+    h = ctypes.c_void_p()
+    rc = lib.lbm_create(ctypes.byref(p), None, None, 0, ctypes.byref(h))
+    assert rc in (-3, -5) and not h.value

@@ -143,6 +143,29 @@ def test_noise_is_mass_conserving_with_rescale():
     assert f[:, occ].min() >= 0.0
 
 
+def test_noise_statistics_match_eq4():
+    """Eq. 4: eta_i = eta~_i - mean_j(eta~_j) with eta~ iid uniform on
+    [-sigma, sigma]. On a rest state the BGK step is the identity, so one step
+    exposes eta directly: per node it sums to zero, var(eta_i) = (8/27) sigma^2,
+    corr(eta_i, eta_j) = -1/8, |eta_i| <= (16/9) sigma, and all nine
+    directions are alike."""
+    sigma = 1e-3
+    p = periodic(width=64, height=64, sigma=sigma)
+    s = OracleSim(p)
+    f0 = s.pops()
+    s.step(1)
+    eta = (s.pops() - f0).reshape(9, -1)
+    assert np.abs(eta.sum(0)).max() < 1e-15
+    var = eta.var(axis=1)
+    assert np.all(np.abs(var / (8 / 27 * sigma ** 2) - 1) < 0.06)
+    c = np.corrcoef(eta)
+    off = c[~np.eye(9, dtype=bool)]
+    assert np.all(np.abs(off + 1 / 8) < 0.05)
+    assert np.abs(eta).max() <= 16 / 9 * sigma * (1 + 1e-12)
+    assert np.abs(eta).max() > 1.3 * sigma  # well beyond a single 8/9 sigma term
+    assert np.abs(eta.mean(axis=1)).max() < 3 * np.sqrt(8 / 27) * sigma / 64
+
+
 def test_literal_negative_fix_adds_twice_the_deficit():
     """App. A step 7 read literally: f_opp(i) += |f_i| and f_i = 0 adds 2|f_i|
     of mass (and keeps momentum). With growth off, the mass gained equals the
