@@ -1,0 +1,335 @@
+"""Throughput benchmark of the fused growing-tissue LBM step on GB300.
+
+Default workload: the 4096 x 2048 D2Q9 lattice with edge-restricted growth
+(divisions within 8 rows of the front), tau = 0.8, sinusoidal initial front
+(wavenumbers 1..64, amplitude 1), FP32 storage, fixed rear wall: about 4.2M
+active nodes per step, so each FP32 population copy of the active window is
+about 300 MB, well above the 129 MB L2 (no L2 flush is needed between steps).
+
+A step is one full time step of the method: the proliferation planner, the
+fused update kernel and the observables kernel (App. A steps 1-7 plus the
+front heights, Eq. 6 and the rear wall).
+
+Reports MLUPS = active-window node updates per second (whole job, all ranks),
+the fused kernel's achieved HBM bandwidth against the measured copy peak,
+an end-to-end figure through the C ABI with host buffers, the FP64 CPU oracle
+timed on a bounded sample as the CPU baseline, and the SM clocks seen during
+the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs one independent replica (its own seed); there is
+no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2303_02210_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "MLUPS"
+UNIT = "MLUPS"
+WORKLOAD_NAME = "lattice_edge"
+
+
+def workload_params(rank: int = 0) -> dict:
+    return wl.lattice_edge(seed=1 + rank, sim_id=rank)
+
+
+def workload_config(precision: str) -> dict:
+    p = workload_params()
+    return {
+        "workload": (f"D2Q9 {p['width']}x{p['height']}, edge-restricted growth depth {p['edge_depth']}, "
+                     f"tau {p['tau']}, g {p['growth_rate']}, sinusoidal front k {p['front_kmin']}-"
+                     f"{p['front_kmax']} amplitude {p['front_amp']} at row {int(p['front_row'])}, "
+                     f"sigma {p['sigma']}, fixed rear wall, {precision} storage"),
+        "lattice": [p["width"], p["height"]],
+        "growth_mode": p["growth_mode"],
+        "precision": precision,
+        "l2": "no flush: the active window's two FP32 population copies (~600 MB) exceed the 129 MB L2",
+        "parallelism": "replicas",
+    }
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lbm_kernels.cuh", "lbm_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2303_02210_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(bytes_per_node_alg: int, nodes_per_launch: float):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    scaled to this launch's node count; None if absent or if the kernel source
+    changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "k_update_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_node"]) * nodes_per_launch
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def oracle_rate(params: dict, steps: int):
+    """The FP64 CPU oracle, as it stands, on `steps` steps of the workload.
+    Returns (MLUPS counted over the same active window the GPU updates,
+    seconds, window nodes per step)."""
+    import numpy as np
+    from oracle.oracle import OracleSim
+    o = OracleSim(params)
+    rho = o.pops().sum(0)
+    rows = np.nonzero(rho.any(1))[0]
+    y_hi = min(params["height"], int(rows.max()) + 2) if len(rows) else 1
+    window = params["width"] * (y_hi - o.stats()["y_r"])
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    o.close()
+    return window * steps / dt / 1e6, dt, window
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle (no reference code exists for this
+    paper) on the host cores, same workload, metric and unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    params = workload_params()
+    warm = min(args.warmup, 1)
+    steps = max(1, min(args.steps, 12))
+    if warm:
+        oracle_rate(params, warm)
+    rate, dt, window = oracle_rate(params, steps)
+    sample = (f"{steps} oracle steps (after {warm} warm-up) of the full {params['width']}x"
+              f"{params['height']} workload, single thread; rate counted over the "
+              f"{window} active-window nodes per step the GPU updates")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config("fp64 (oracle)"),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--cpu-steps", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2303_02210_gb300.lbm import Simulation
+
+    params = workload_params(rank)
+    sim = Simulation(params, precision=args.precision)
+    stream = sim.stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident throughput (inputs resident in HBM) ----
+    sim.step(args.warmup)
+    sim.sync()
+    st0 = sim.stats()
+    sim.lbm_timing_enable(args.steps)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    st1 = sim.stats()
+    k_launches, k_ms, k_nodes = sim.lbm_timing_read()
+    nodes = st1["node_updates"] - st0["node_updates"]
+    launches = st1["launches"] - st0["launches"]
+    bpn = sim.lbm_bytes_per_node()
+    status = st1["status"]
+    sim.close()
+    del sim
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    n = torch.tensor([float(nodes)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    nodes_all = float(n.item())
+    value = nodes_all / (ms_max * 1e-3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers ----
+    import numpy as np
+    e2e_steps = max(1, min(args.steps, 100))
+    barrier()
+    torch.cuda.synchronize()
+    h = np.empty(params["width"], dtype=np.int32)
+    t0 = time.perf_counter()
+    sim2 = Simulation(params, precision=args.precision)
+    for _ in range(e2e_steps):
+        sim2.step(1)
+        h, hbar, w = sim2.front_heights()
+    st2 = sim2.stats()
+    sim2.close()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    n = torch.tensor([float(st2["node_updates"])], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    e2e_value = float(n.item()) / float(t.item()) / 1e6
+    # bytes that cross the bus: the initial front profile (W int32) once at
+    # creation; W int32 heights plus hbar and w (two doubles) every step
+    h2d = params["width"] * 4 / e2e_steps
+    d2h = params["width"] * 4 + 16
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peak()
+    nodes_per_launch = k_nodes / max(k_launches, 1)
+    achieved = bpn * k_nodes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
+    traffic = profiled_traffic(bpn, nodes_per_launch)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic", "config": workload_config(args.precision),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_update (fused stream/collide/front/noise)",
+                     "algorithmic_bytes_per_launch": bpn * nodes_per_launch,
+                     "avg_launch_ms": k_ms / max(k_launches, 1), "peak_source": peak_kind},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "what": (f"lbm_create from host parameters, then {e2e_steps} x (lbm_step(1) + "
+                         f"lbm_front_heights into a host buffer), lbm_destroy")},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "status": status,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        rate, dt, window = oracle_rate(workload_params(), args.cpu_steps)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{args.cpu_steps} steps of the FP64 CPU oracle on the full "
+                       f"{params['width']}x{params['height']} workload ({dt:.1f} s, one thread); "
+                       f"rate over the {window} active-window nodes per step"),
+        }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

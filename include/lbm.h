@@ -1,0 +1,206 @@
+/*
+ * lbm.h — C ABI of the GB300 (sm_103a) library for the growing-tissue lattice
+ * Boltzmann method of Killeen, Partridge, Bertrand & Lee (arXiv 2303.02210).
+ *
+ * One simulation is one D2Q9 lattice, W columns (x, periodic) by H rows
+ * (y, the growth direction), whose populations stay resident in device memory.
+ * Every call that does arithmetic launches hand-written CUDA kernels on the
+ * stream given at creation; nothing is computed on the host except the
+ * initial front profile (App. A, first paragraph) and argument marshalling.
+ *
+ * Conventions for every function:
+ *  - Return value: 0 (LBM_OK) on success, a negative LBM_ERR_* code on
+ *    error, never an exception or an abort. lbm_strerror() names a code.
+ *  - Host pointers are caller-owned and only read or written during the call.
+ *  - Device pointers are caller-owned; the library never frees them.
+ *  - A handle is not thread-safe: calls on one handle must be serialised.
+ *  - Calls marked "syncs" wait for the handle's stream; all others only
+ *    enqueue work and return.
+ */
+#ifndef LBM_GB300_LBM_H
+#define LBM_GB300_LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define LBM_OK 0
+#define LBM_ERR_INVALID_ARG (-1) /* a parameter is out of range or a pointer is NULL */
+#define LBM_ERR_OOM (-2)         /* device allocation failed or the arena is too small */
+#define LBM_ERR_CUDA (-3)        /* a CUDA call failed (see lbm_last_cuda_error) */
+#define LBM_ERR_CAPACITY (-4)    /* one step asked for more divisions than the planner holds */
+#define LBM_ERR_NO_DEVICE (-5)   /* no CUDA device of compute capability 10.3 */
+
+/* ---- device status bits (lbm_stats_t.status; sticky until lbm_clear_status) ---- */
+#define LBM_STATUS_FRONT_AT_TOP 1   /* mass reached row H-1 (the top wall) */
+#define LBM_STATUS_GROWTH_STARVED 2 /* a step accepted fewer than n_s divisions */
+#define LBM_STATUS_CAPACITY 4       /* n_s exceeded the planner capacity; growth skipped */
+
+/* ---- enumerations used in lbm_params_t ---- */
+enum {
+    LBM_GROW_NONE = 0,
+    LBM_GROW_BULK = 1,    /* uniform over occupied active nodes (Sec. III) */
+    LBM_GROW_DENSITY = 2, /* accept with p = 1 - rho/rho0 if rho > rho_c (Eq. 5) */
+    LBM_GROW_EDGE = 3,    /* occupied and at most edge_depth rows below the front */
+    LBM_GROW_BAND = 4     /* occupied and within band_rows of the rear wall (App. B) */
+};
+enum { LBM_FRONT_FLAT = 0, LBM_FRONT_SINUSOIDAL = 1, LBM_FRONT_FULL = 2 };
+enum { LBM_WALL_FIXED = 0, LBM_WALL_ADVANCE = 1 };
+enum { LBM_NEGFIX_LITERAL = 0, LBM_NEGFIX_RESCALE = 1 };
+enum { LBM_FP32 = 0, LBM_FP64 = 1 };
+
+/*
+ * Model parameters (App. A parameter list; Sec. II for the model).
+ *  tau          BGK relaxation time, > 1/2 (Eq. 2)
+ *  mu           substrate friction, u* = (1 - mu) u (Sec. II, below Eq. 3)
+ *  rho_c        occupancy threshold of the two-step bounce-back (Sec. II)
+ *  rho_cell     mass of one division (Sec. II)
+ *  sigma        noise amplitude, eta~ uniform in [-sigma, sigma] (Eq. 4)
+ *  rho0         density where density-dependent growth stops (Eq. 5)
+ *  growth_rate  g: n_s = g M / rho_cell sites per step (Sec. II)
+ *  rho_init, rho_jitter   initial density rho_init (1 + jitter (2U - 1))
+ *  front_row, front_amp   initial front height and perturbation amplitude
+ *  front_kmin, front_kmax wavenumbers of the sinusoidal initial front
+ *  wall_min_gap, wall_w_factor   rear wall kept max(gap, factor w) behind hbar
+ *  edge_depth, band_rows  growth-mode extents
+ *  y_periodic   1: periodic in y too, no walls (test lattices)
+ *  seed, sim_id Philox key and counter word 3
+ *  precision    LBM_FP32 (fast path) or LBM_FP64 (debug path, bit-exact
+ *               with the CPU oracle)
+ */
+typedef struct {
+    double tau, mu, rho_c, rho_cell, sigma, rho0, growth_rate;
+    double rho_init, rho_jitter, front_row, front_amp, wall_min_gap, wall_w_factor;
+    uint64_t seed;
+    int32_t width, height, growth_mode, edge_depth, band_rows, front_kind;
+    int32_t front_kmin, front_kmax, wall_mode, negfix_mode, y_periodic;
+    uint32_t sim_id;
+    int32_t precision;
+    int32_t reserved;
+} lbm_params_t;
+
+/* Counters and observables after the latest completed step. */
+typedef struct {
+    int64_t step;          /* completed steps */
+    int64_t ns_last;       /* n_s requested by the latest step */
+    int64_t ns_total;      /* sum of n_s over all steps */
+    int64_t div_total;     /* divisions actually applied */
+    int64_t starved_steps; /* steps that accepted fewer than n_s candidates */
+    int64_t cand_last;     /* candidates drawn by the latest step */
+    int64_t events_last;   /* divisions applied by the latest step */
+    int64_t mass_fix;      /* active mass M in units of 2^-24 (exact sum of per-node rounds) */
+    int64_t quiescent_fix; /* mass frozen behind the rear wall, same unit */
+    int64_t S1, S2;        /* sum h(x), sum h(x)^2 over the columns */
+    int64_t node_updates;  /* sum over steps of the nodes updated (active window) */
+    int64_t launches;      /* kernels launched by lbm_step so far */
+    double mass, quiescent_mass, carry, hbar, w, clip_mass;
+    int32_t y_r;           /* rear wall: rows below y_r are quiescent */
+    int32_t H_top;         /* max_x h(x) */
+    int32_t hmin;          /* min_x h(x) */
+    int32_t y_hi;          /* rows >= y_hi hold no mass (window top) */
+    int32_t status;        /* LBM_STATUS_* bits */
+    int32_t reserved;
+} lbm_stats_t;
+
+typedef struct lbm_sim lbm_sim;
+
+/* Checks a parameter set without touching any GPU. LBM_OK or
+ * LBM_ERR_INVALID_ARG. Limits: 1 <= W, 3 <= H, W, H <= 32768, W*H < 2^30,
+ * tau > 1/2, rho_cell > 0, rho_c >= 0, growth_rate >= 0. */
+int lbm_validate(const lbm_params_t *params);
+
+/* Device bytes one simulation needs (for a caller-provided arena); host only. */
+int lbm_footprint(const lbm_params_t *params, uint64_t *bytes);
+
+/* Creates a simulation and initialises it on `stream` (a cudaStream_t, NULL =
+ * legacy default stream): tissue below the initial front with u = 0 and
+ * f = f^SS(rho, 0) (App. A, first paragraph), then the occupancy mask, front
+ * heights and active mass. `arena` is an optional device buffer of at least
+ * lbm_footprint() bytes, 256-byte aligned, owned by the caller and kept alive
+ * until lbm_destroy; NULL makes the library allocate (and later free) its own.
+ * On success *out holds the handle. Syncs. */
+int lbm_create(const lbm_params_t *params, void *stream, void *arena, uint64_t arena_bytes,
+               lbm_sim **out);
+
+/* Advances `nsteps` time steps (App. A steps 1-7 each, plus the front
+ * heights, Eq. 6 width, rear wall and active mass), all on the device with no
+ * host synchronisation. Returns LBM_OK or a launch error; device-side status
+ * (LBM_STATUS_*) is reported by lbm_stats. */
+int lbm_step(lbm_sim *sim, int64_t nsteps);
+
+/* Front heights h(x) = 1 + highest occupied row of column x (0 if none) into
+ * the caller's host array of W int32, and the mean height and interface width
+ * w of Eq. 6 (either pointer may be NULL). Syncs. */
+int lbm_front_heights(lbm_sim *sim, int32_t *h_host, double *hbar, double *w);
+
+/* Density rho = sum_i f_i and velocity u = sum_i f_i e_i / rho (Eq. 1; u = 0
+ * where rho = 0) of the current populations into caller host arrays of W*H
+ * doubles, row-major [y][x]. Syncs. */
+int lbm_fields(lbm_sim *sim, double *rho, double *ux, double *uy);
+
+/* Same as lbm_fields into caller device arrays of W*H doubles. Enqueues only. */
+int lbm_fields_device(lbm_sim *sim, double *rho, double *ux, double *uy);
+
+/* Current populations into a caller host array of 9*H*W doubles, [q][y][x]
+ * with the D2Q9 order 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1)
+ * 6:(-1,1) 7:(-1,-1) 8:(1,-1). Syncs. */
+int lbm_populations(lbm_sim *sim, double *f_host);
+
+/* Replaces the populations with the caller's host array (layout as above,
+ * rounded to the storage precision); recomputes the occupancy mask of the
+ * active rows, the heights and the active mass; keeps the step count, the
+ * rear wall and the carried site fraction. Every value must be finite and
+ * non-negative (as after any step), else LBM_ERR_INVALID_ARG. Syncs. */
+int lbm_set_populations(lbm_sim *sim, const double *f_host);
+
+/* Occupancy mask (1 where rho >= rho_c after the latest step) into a caller
+ * host array of H*W bytes, [y][x]. Syncs. */
+int lbm_mask(lbm_sim *sim, uint8_t *mask_host);
+
+/* Divisions applied by the latest step, sorted by (node, pair): node id
+ * y*W + x, pair p in 0..3 loading directions (1,3), (2,4), (5,7), (6,8), and
+ * the number of times the site was drawn. Writes at most `cap` entries and the
+ * total count to *n. Syncs. */
+int lbm_last_events(lbm_sim *sim, int64_t *node, int32_t *pair, int32_t *count, int64_t cap,
+                    int64_t *n);
+
+/* Counters and observables after the latest step. Syncs. */
+int lbm_stats(lbm_sim *sim, lbm_stats_t *out);
+
+/* Clears the sticky device status bits. Enqueues only. */
+int lbm_clear_status(lbm_sim *sim);
+
+/* Kernel timing for throughput measurement: while enabled, every launch of
+ * the fused update kernel is bracketed by CUDA events on the simulation's
+ * stream (at most `max_launches` of them). lbm_timing_read syncs and returns
+ * the number of timed launches, their summed device time in milliseconds and
+ * the nodes they updated. Enabling again resets the record. */
+int lbm_timing_enable(lbm_sim *sim, int64_t max_launches);
+int lbm_timing_read(lbm_sim *sim, int64_t *launches, double *total_ms, int64_t *nodes);
+
+/* Bytes of population traffic one node update moves in the fused update
+ * kernel (9 loads + 9 stores of the storage type). */
+int lbm_bytes_per_node(lbm_sim *sim, int64_t *bytes);
+
+/* Waits for the stream; returns LBM_OK or LBM_ERR_CUDA. */
+int lbm_sync(lbm_sim *sim);
+
+/* Frees the handle and (if the library allocated it) its device memory. */
+void lbm_destroy(lbm_sim *sim);
+
+/* Name of a return code; never NULL. */
+const char *lbm_strerror(int code);
+
+/* Text of the last CUDA error seen by any handle of this thread; never NULL. */
+const char *lbm_last_cuda_error(void);
+
+/* Library version string, e.g. "0.1.0 sm_103a". */
+const char *lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_LBM_H */

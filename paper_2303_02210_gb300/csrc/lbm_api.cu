@@ -1,0 +1,614 @@
+// C ABI of the library (declared in include/lbm.h): parameter checks, device
+// memory layout, initial front profile, launch sequencing and read-back.
+// All lattice arithmetic runs in the kernels of lbm_kernels.cuh; the host only
+// computes the initial front profile (App. A, first paragraph) and marshals.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_common.cuh"
+
+using namespace lbm;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "no CUDA error";
+
+int cuda_fail(cudaError_t e)
+{
+    std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return LBM_ERR_OOM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver || e == cudaErrorNoKernelImageForDevice)
+        return LBM_ERR_NO_DEVICE;
+    return LBM_ERR_CUDA;
+}
+
+// Every call on a handle makes the handle's device current first.
+#define USE_DEVICE(s)                                                                                                  \
+    do {                                                                                                               \
+        cudaError_t e_ = cudaSetDevice((s)->device);                                                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_);                                                                   \
+    } while (0)
+
+#define CK(call)                                                                                                       \
+    do {                                                                                                               \
+        cudaError_t e_ = (call);                                                                                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_);                                                                   \
+    } while (0)
+
+uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
+
+struct Layout {
+    int Wp, MW, hcap, ns_max;
+    long long P, kc_max;
+    int elem;
+    uint64_t off_f0, off_f1, off_mask, off_heights, off_rows0, off_sc, off_cflags, off_ckeys, off_gkl, off_gwpref,
+        off_hkeys, off_hcnt, off_hlist, off_evn, off_evp, off_evc, total;
+};
+
+Layout make_layout(const lbm_params_t &p)
+{
+    Layout L{};
+    L.elem = p.precision == LBM_FP64 ? 8 : 4;
+    L.Wp = (p.width + 31) / 32 * 32;
+    L.MW = L.Wp / 32;
+    L.P = (long long)L.Wp * p.height;
+    // planner capacity: divisions per step at up to four times the initial
+    // density over the whole lattice, at least 1024
+    double est = 0.0;
+    if (p.growth_mode != LBM_GROW_NONE) {
+        const double rho_hi = 4.0 * std::max(p.rho_init * (1.0 + std::fabs(p.rho_jitter)), p.rho_c);
+        est = p.growth_rate * rho_hi * (double)p.width * (double)p.height / p.rho_cell;
+    }
+    double cap = std::ceil(est) + 1024.0;
+    if (cap > 16777216.0) cap = 16777216.0;
+    L.ns_max = (int)cap;
+    L.hcap = 1;
+    while (L.hcap < 2 * L.ns_max) L.hcap <<= 1;
+    L.kc_max = ((4LL * L.ns_max + 1024) + 31) & ~31LL;
+    uint64_t o = 0;
+    const uint64_t fbytes = (uint64_t)9 * (uint64_t)L.P * (uint64_t)L.elem;
+    L.off_f0 = o; o = align256(o + fbytes);
+    L.off_f1 = o; o = align256(o + fbytes);
+    L.off_mask = o; o = align256(o + (uint64_t)p.height * L.MW * 4u);
+    L.off_heights = o; o = align256(o + (uint64_t)p.width * 4u);
+    L.off_rows0 = o; o = align256(o + (uint64_t)p.width * 4u);
+    L.off_sc = o; o = align256(o + sizeof(DevScalars));
+    L.off_cflags = o; o = align256(o + (uint64_t)(L.kc_max / 32) * 4u);
+    L.off_ckeys = o; o = align256(o + (uint64_t)L.kc_max * 4u);
+    L.off_gkl = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    L.off_gwpref = o; o = align256(o + (uint64_t)(L.kc_max / 32) * 4u);
+    L.off_hkeys = o; o = align256(o + (uint64_t)L.hcap * 4u);
+    L.off_hcnt = o; o = align256(o + (uint64_t)L.hcap * 4u);
+    L.off_hlist = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    L.off_evn = o; o = align256(o + (uint64_t)L.ns_max * 8u);
+    L.off_evp = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    L.off_evc = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    L.total = o;
+    return L;
+}
+
+// Initial front (App. A: a flat interface; here optionally perturbed): the
+// number of tissue rows of each column, node (x, y) being tissue iff y < h0(x).
+void front_rows(const lbm_params_t &p, std::vector<int32_t> &rows)
+{
+    const int W = p.width, H = p.height;
+    const PhiloxKey pk = philox_key((uint32_t)(p.seed & 0xFFFFFFFFu), (uint32_t)(p.seed >> 32));
+    rows.assign(W, H);
+    if (p.front_kind == LBM_FRONT_FULL) return;
+    std::vector<double> h0(W);
+    if (p.front_kind == LBM_FRONT_FLAT) {
+        for (int x = 0; x < W; ++x) {
+            const u32x4 r = philox4x32_10(u32x4{(uint32_t)x, 0u, STREAM_INIT, p.sim_id}, pk);
+            h0[x] = p.front_row + p.front_amp * (2.0 * u01(r.x) - 1.0);
+        }
+    } else {
+        // sum of sinusoids k = kmin..kmax with phases 2 pi U_k, scaled so that
+        // its largest excursion equals the amplitude
+        const double two_pi = 6.283185307179586;
+        std::vector<double> phi;
+        for (int k = p.front_kmin; k <= p.front_kmax; ++k) {
+            const u32x4 r = philox4x32_10(u32x4{(uint32_t)k, 1u, STREAM_INIT, p.sim_id}, pk);
+            phi.push_back(two_pi * u01(r.x));
+        }
+        double smax = 0.0;
+        for (int x = 0; x < W; ++x) {
+            double S = 0.0;
+            for (int k = p.front_kmin; k <= p.front_kmax; ++k)
+                S = S + std::sin(((two_pi * (double)k) * (double)x) / (double)W + phi[k - p.front_kmin]);
+            h0[x] = S;
+            if (std::fabs(S) > smax) smax = std::fabs(S);
+        }
+        for (int x = 0; x < W; ++x)
+            h0[x] = smax > 0.0 ? p.front_row + p.front_amp * (h0[x] / smax) : p.front_row;
+    }
+    for (int x = 0; x < W; ++x) {
+        double c = std::ceil(h0[x]);
+        if (c < 0.0) c = 0.0;
+        if (c > (double)H) c = (double)H;
+        rows[x] = (int32_t)c;
+    }
+}
+
+} // namespace
+
+struct lbm_sim {
+    lbm_params_t p;
+    int device;
+    SimDev d;
+    Layout L;
+    const KernelTable *kt;
+    cudaStream_t stream;
+    void *arena;
+    bool own_arena;
+    int cur;
+    int64_t step;
+    int64_t launches;
+    // kernel timing
+    std::vector<cudaEvent_t> ev;
+    int64_t ev_used;
+    bool timing;
+    int64_t timing_nodes0;
+};
+
+extern "C" {
+
+int lbm_validate(const lbm_params_t *p)
+{
+    if (!p) return LBM_ERR_INVALID_ARG;
+    if (p->width < 1 || p->height < 3 || p->width > 32768 || p->height > 32768) return LBM_ERR_INVALID_ARG;
+    if ((int64_t)p->width * p->height >= (int64_t)1 << 30) return LBM_ERR_INVALID_ARG;
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LBM_ERR_INVALID_ARG;
+    if (!(p->rho_cell > 0.0) || !(p->rho_c >= 0.0) || !(p->growth_rate >= 0.0) || !(p->sigma >= 0.0))
+        return LBM_ERR_INVALID_ARG;
+    if (!std::isfinite(p->mu) || !std::isfinite(p->rho_init) || !(p->rho_init >= 0.0)) return LBM_ERR_INVALID_ARG;
+    if (p->growth_mode < LBM_GROW_NONE || p->growth_mode > LBM_GROW_BAND) return LBM_ERR_INVALID_ARG;
+    if (p->growth_mode == LBM_GROW_DENSITY && !(p->rho0 > 0.0)) return LBM_ERR_INVALID_ARG;
+    if (p->growth_mode == LBM_GROW_EDGE && p->edge_depth < 0) return LBM_ERR_INVALID_ARG;
+    if (p->growth_mode == LBM_GROW_BAND && p->band_rows < 1) return LBM_ERR_INVALID_ARG;
+    if (p->front_kind < LBM_FRONT_FLAT || p->front_kind > LBM_FRONT_FULL) return LBM_ERR_INVALID_ARG;
+    if (p->front_kind == LBM_FRONT_SINUSOIDAL && (p->front_kmin < 0 || p->front_kmax < p->front_kmin))
+        return LBM_ERR_INVALID_ARG;
+    if (p->wall_mode != LBM_WALL_FIXED && p->wall_mode != LBM_WALL_ADVANCE) return LBM_ERR_INVALID_ARG;
+    if (p->negfix_mode != LBM_NEGFIX_LITERAL && p->negfix_mode != LBM_NEGFIX_RESCALE) return LBM_ERR_INVALID_ARG;
+    if (p->precision != LBM_FP32 && p->precision != LBM_FP64) return LBM_ERR_INVALID_ARG;
+    if (p->y_periodic != 0 && p->y_periodic != 1) return LBM_ERR_INVALID_ARG;
+    return LBM_OK;
+}
+
+int lbm_footprint(const lbm_params_t *p, uint64_t *bytes)
+{
+    if (!bytes) return LBM_ERR_INVALID_ARG;
+    const int v = lbm_validate(p);
+    if (v != LBM_OK) return v;
+    *bytes = make_layout(*p).total;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_sim *s)
+{
+    if (!s) return;
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->stream);
+    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    if (s->own_arena && s->arena) cudaFree(s->arena);
+    delete s;
+}
+
+int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_bytes, lbm_sim **out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    int v = lbm_validate(p);
+    if (v != LBM_OK) return v;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+
+    lbm_sim *s = new lbm_sim();
+    s->p = *p;
+    s->device = dev;
+    s->L = make_layout(*p);
+    s->kt = p->precision == LBM_FP64 ? &kTableF64 : &kTableF32;
+    s->stream = (cudaStream_t)stream;
+    s->cur = 0;
+    s->step = 0;
+    s->launches = 0;
+    s->ev_used = 0;
+    s->timing = false;
+    if (arena) {
+        if (arena_bytes < s->L.total || ((uintptr_t)arena & 255u) != 0) {
+            delete s;
+            return arena_bytes < s->L.total ? LBM_ERR_OOM : LBM_ERR_INVALID_ARG;
+        }
+        s->arena = arena;
+        s->own_arena = false;
+    } else {
+        cudaError_t e = cudaMalloc(&s->arena, s->L.total);
+        if (e != cudaSuccess) {
+            delete s;
+            return cuda_fail(e);
+        }
+        s->own_arena = true;
+    }
+    char *base = (char *)s->arena;
+    const Layout &L = s->L;
+    SimDev &d = s->d;
+    std::memset(&d, 0, sizeof(d));
+    d.f[0] = base + L.off_f0;
+    d.f[1] = base + L.off_f1;
+    d.mask = (uint32_t *)(base + L.off_mask);
+    d.heights = (int32_t *)(base + L.off_heights);
+    d.rows0 = (int32_t *)(base + L.off_rows0);
+    d.sc = (DevScalars *)(base + L.off_sc);
+    d.cflags = (uint32_t *)(base + L.off_cflags);
+    d.ckeys = (uint32_t *)(base + L.off_ckeys);
+    d.gkl = (uint32_t *)(base + L.off_gkl);
+    d.gwpref = (int32_t *)(base + L.off_gwpref);
+    d.hkeys = (uint32_t *)(base + L.off_hkeys);
+    d.hcnt = (uint32_t *)(base + L.off_hcnt);
+    d.hlist = (int32_t *)(base + L.off_hlist);
+    d.ev_node = (long long *)(base + L.off_evn);
+    d.ev_pair = (int32_t *)(base + L.off_evp);
+    d.ev_count = (int32_t *)(base + L.off_evc);
+    d.W = p->width;
+    d.H = p->height;
+    d.Wp = L.Wp;
+    d.MW = L.MW;
+    d.P = L.P;
+    d.hcap = L.hcap;
+    d.ns_max = L.ns_max;
+    d.kc_max = L.kc_max;
+    d.omega = 1.0 / p->tau;
+    d.cmu = 1.0 - p->mu;
+    d.rho_c = p->rho_c;
+    d.rho_cell = p->rho_cell;
+    d.half_cell = p->rho_cell * 0.5;
+    d.growth_rate = p->growth_rate;
+    d.rho0 = p->rho0;
+    d.sigma = p->sigma;
+    d.rho_init = p->rho_init;
+    d.rho_jitter = p->rho_jitter;
+    d.wall_min_gap = p->wall_min_gap;
+    d.wall_w_factor = p->wall_w_factor;
+    d.key0 = (uint32_t)(p->seed & 0xFFFFFFFFu);
+    d.key1 = (uint32_t)(p->seed >> 32);
+    d.pk = philox_key(d.key0, d.key1);
+    d.sim = p->sim_id;
+    d.growth_mode = p->growth_mode;
+    d.edge_depth = p->edge_depth;
+    d.band_rows = p->band_rows;
+    d.wall_mode = p->wall_mode;
+    d.negfix = p->negfix_mode;
+    d.y_periodic = p->y_periodic;
+    const int bps = s->kt->update_blocks_per_sm();
+    // persistent grid: as many blocks as fit on the SMs, rounded down to a
+    // multiple of the column tiles (each block keeps one column tile)
+    const int ncx = (p->width + s->kt->update_tile_x - 1) / s->kt->update_tile_x;
+    const int g0 = nsm * (bps > 0 ? bps : 1);
+    d.update_grid = g0 >= ncx ? (g0 / ncx) * ncx : ncx;
+    d.cand_grid = 2 * nsm;
+
+    int rc = LBM_OK;
+    do {
+        cudaError_t e = cudaMemsetAsync(s->arena, 0, L.total, s->stream);
+        if (e != cudaSuccess) { rc = cuda_fail(e); break; }
+        // the large-n_s event table starts empty (all keys 0xFFFFFFFF)
+        e = cudaMemsetAsync(d.hkeys, 0xFF, (size_t)L.hcap * 4u, s->stream);
+        if (e != cudaSuccess) { rc = cuda_fail(e); break; }
+        std::vector<int32_t> rows;
+        front_rows(*p, rows);
+        e = cudaMemcpyAsync(d.rows0, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) { rc = cuda_fail(e); break; }
+        if ((e = s->kt->fill(d, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
+        if ((e = s->kt->scan(d, 0, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
+        if ((e = s->kt->observe(d, 0, 1, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
+        e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) { rc = cuda_fail(e); break; }
+    } while (0);
+    if (rc != LBM_OK) {
+        lbm_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_sim *s, int64_t nsteps)
+{
+    if (!s || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    const bool grow = s->p.growth_mode != LBM_GROW_NONE;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        const uint32_t t = (uint32_t)s->step;
+        if (grow) {
+            CK(s->kt->cand(s->d, s->cur, t, s->stream));
+            CK(s->kt->select(s->d, s->cur, t, s->stream));
+            s->launches += 2;
+        }
+        const bool timed = s->timing && s->ev_used + 2 <= (int64_t)s->ev.size();
+        if (timed) CK(cudaEventRecord(s->ev[s->ev_used], s->stream));
+        CK(s->kt->update(s->d, s->cur, t, s->stream));
+        if (timed) {
+            CK(cudaEventRecord(s->ev[s->ev_used + 1], s->stream));
+            s->ev_used += 2;
+        }
+        CK(s->kt->observe(s->d, s->cur ^ 1, 0, s->stream));
+        s->launches += 2;
+        s->cur ^= 1;
+        ++s->step;
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_sim *s)
+{
+    if (!s) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+static int read_scalars(lbm_sim *s, DevScalars *hs)
+{
+    CK(cudaMemcpyAsync(hs, s->d.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+int lbm_stats(lbm_sim *s, lbm_stats_t *out)
+{
+    if (!s || !out) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    DevScalars hs;
+    int rc = read_scalars(s, &hs);
+    if (rc != LBM_OK) return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->step = hs.step;
+    out->ns_last = hs.ns_last;
+    out->ns_total = hs.ns_total;
+    out->div_total = hs.div_total;
+    out->starved_steps = hs.starved_steps;
+    out->cand_last = hs.cand_last;
+    out->events_last = hs.events_last;
+    out->mass_fix = hs.mass_fix;
+    out->quiescent_fix = hs.quiescent_fix;
+    out->S1 = hs.S1;
+    out->S2 = hs.S2;
+    out->node_updates = hs.node_updates;
+    out->launches = s->launches;
+    out->mass = (double)hs.mass_fix * kFixInv;
+    out->quiescent_mass = (double)hs.quiescent_fix * kFixInv;
+    out->carry = hs.carry;
+    out->hbar = hs.hbar;
+    out->w = hs.w;
+    out->clip_mass = hs.clip_mass;
+    out->y_r = hs.y_r;
+    out->H_top = hs.H_top;
+    out->hmin = hs.hmin;
+    out->y_hi = hs.y_hi;
+    out->status = hs.status;
+    return LBM_OK;
+}
+
+int lbm_clear_status(lbm_sim *s)
+{
+    if (!s) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    CK(cudaMemsetAsync(&s->d.sc->status, 0, sizeof(int), s->stream));
+    return LBM_OK;
+}
+
+int lbm_front_heights(lbm_sim *s, int32_t *h_host, double *hbar, double *w)
+{
+    if (!s) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    // only the returned values cross the bus: W int32 and two doubles
+    double hw[2];
+    if (h_host)
+        CK(cudaMemcpyAsync(h_host, s->d.heights, sizeof(int32_t) * s->p.width, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&hw[0], &s->d.sc->hbar, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&hw[1], &s->d.sc->w, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (hbar) *hbar = hw[0];
+    if (w) *w = hw[1];
+    return LBM_OK;
+}
+
+int lbm_fields_device(lbm_sim *s, double *rho, double *ux, double *uy)
+{
+    if (!s || !rho || !ux || !uy) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    CK(s->kt->fields(s->d, s->cur, rho, ux, uy, s->stream));
+    return LBM_OK;
+}
+
+int lbm_fields(lbm_sim *s, double *rho, double *ux, double *uy)
+{
+    if (!s || !rho || !ux || !uy) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    const size_t n = (size_t)s->p.width * s->p.height;
+    double *dbuf = nullptr;
+    CK(cudaMallocAsync((void **)&dbuf, 3 * n * sizeof(double), s->stream));
+    int rc = LBM_OK;
+    cudaError_t e = s->kt->fields(s->d, s->cur, dbuf, dbuf + n, dbuf + 2 * n, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rho, dbuf, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ux, dbuf + n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(uy, dbuf + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+    cudaFreeAsync(dbuf, s->stream);
+    e = cudaStreamSynchronize(s->stream);
+    if (rc == LBM_OK && e != cudaSuccess) rc = cuda_fail(e);
+    return rc;
+}
+
+int lbm_populations(lbm_sim *s, double *f_host)
+{
+    if (!s || !f_host) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    const int W = s->p.width, H = s->p.height, el = s->L.elem;
+    std::vector<char> tmp((size_t)9 * W * H * el);
+    for (int i = 0; i < 9; ++i) {
+        const char *src = (const char *)s->d.f[s->cur] + (size_t)i * s->L.P * el;
+        CK(cudaMemcpy2DAsync(tmp.data() + (size_t)i * W * H * el, (size_t)W * el, src, (size_t)s->L.Wp * el,
+                             (size_t)W * el, H, cudaMemcpyDeviceToHost, s->stream));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    const size_t n = (size_t)9 * W * H;
+    if (el == 8) {
+        std::memcpy(f_host, tmp.data(), n * 8);
+    } else {
+        const float *t = (const float *)tmp.data();
+        for (size_t k = 0; k < n; ++k) f_host[k] = (double)t[k];
+    }
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_sim *s, const double *f_host)
+{
+    if (!s || !f_host) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    const int W = s->p.width, H = s->p.height, el = s->L.elem;
+    const size_t n = (size_t)9 * W * H;
+    // every step leaves the populations non-negative; so must the caller
+    for (size_t k = 0; k < n; ++k)
+        if (!(f_host[k] >= 0.0) || !std::isfinite(f_host[k])) return LBM_ERR_INVALID_ARG;
+    std::vector<char> tmp(n * el);
+    if (el == 8) {
+        std::memcpy(tmp.data(), f_host, n * 8);
+    } else {
+        float *t = (float *)tmp.data();
+        for (size_t k = 0; k < n; ++k) t[k] = (float)f_host[k];
+    }
+    for (int b = 0; b < 2; ++b)
+        for (int i = 0; i < 9; ++i) {
+            char *dst = (char *)s->d.f[b] + (size_t)i * s->L.P * el;
+            CK(cudaMemcpy2DAsync(dst, (size_t)s->L.Wp * el, tmp.data() + (size_t)i * W * H * el, (size_t)W * el,
+                                 (size_t)W * el, H, cudaMemcpyHostToDevice, s->stream));
+        }
+    // the stored mass accumulators restart from this state
+    DevScalars *sc = s->d.sc;
+    const unsigned long long zero = 0ull;
+    const int minus1 = -1, zeroi = 0;
+    CK(cudaMemcpyAsync(&sc->mass_accum, &zero, sizeof(zero), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&sc->maxmass_accum, &minus1, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&sc->status, &zeroi, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    CK(s->kt->scan(s->d, s->cur, s->stream));
+    CK(s->kt->observe(s->d, s->cur, 1, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+int lbm_mask(lbm_sim *s, uint8_t *mask_host)
+{
+    if (!s || !mask_host) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    const int W = s->p.width, H = s->p.height, MW = s->L.MW;
+    std::vector<uint32_t> words((size_t)H * MW);
+    CK(cudaMemcpyAsync(words.data(), s->d.mask, words.size() * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) mask_host[(size_t)y * W + x] = (words[(size_t)y * MW + (x >> 5)] >> (x & 31)) & 1u;
+    return LBM_OK;
+}
+
+int lbm_last_events(lbm_sim *s, int64_t *node, int32_t *pair, int32_t *count, int64_t cap, int64_t *n)
+{
+    if (!s || !n || cap < 0) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    DevScalars hs;
+    int rc = read_scalars(s, &hs);
+    if (rc != LBM_OK) return rc;
+    const int ne = s->p.growth_mode == LBM_GROW_NONE ? 0 : hs.n_events;
+    *n = ne;
+    if (ne == 0 || cap == 0) return LBM_OK;
+    if (!node || !pair || !count) return LBM_ERR_INVALID_ARG;
+    std::vector<long long> vn(ne);
+    std::vector<int32_t> vp(ne), vc(ne);
+    CK(cudaMemcpyAsync(vn.data(), s->d.ev_node, ne * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(vp.data(), s->d.ev_pair, ne * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(vc.data(), s->d.ev_count, ne * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    std::vector<int> ord(ne);
+    for (int i = 0; i < ne; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+        return vn[a] * 4 + vp[a] < vn[b] * 4 + vp[b];
+    });
+    const int64_t m = std::min<int64_t>(cap, ne);
+    for (int64_t i = 0; i < m; ++i) {
+        node[i] = vn[ord[i]];
+        pair[i] = vp[ord[i]];
+        count[i] = vc[ord[i]];
+    }
+    return LBM_OK;
+}
+
+int lbm_timing_enable(lbm_sim *s, int64_t max_launches)
+{
+    if (!s || max_launches < 0) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    while ((int64_t)s->ev.size() < 2 * max_launches) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        s->ev.push_back(e);
+    }
+    s->ev_used = 0;
+    s->timing = max_launches > 0;
+    DevScalars hs;
+    int rc = read_scalars(s, &hs);
+    if (rc != LBM_OK) return rc;
+    s->timing_nodes0 = hs.node_updates;
+    return LBM_OK;
+}
+
+int lbm_timing_read(lbm_sim *s, int64_t *launches, double *total_ms, int64_t *nodes)
+{
+    if (!s) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    DevScalars hs;
+    int rc = read_scalars(s, &hs);
+    if (rc != LBM_OK) return rc;
+    double tot = 0.0;
+    for (int64_t k = 0; k + 1 < s->ev_used; k += 2) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, s->ev[k], s->ev[k + 1]));
+        tot += ms;
+    }
+    if (launches) *launches = s->ev_used / 2;
+    if (total_ms) *total_ms = tot;
+    if (nodes) *nodes = hs.node_updates - s->timing_nodes0;
+    s->timing = false;
+    return LBM_OK;
+}
+
+int lbm_bytes_per_node(lbm_sim *s, int64_t *bytes)
+{
+    if (!s || !bytes) return LBM_ERR_INVALID_ARG;
+    *bytes = 18 * (int64_t)s->L.elem;
+    return LBM_OK;
+}
+
+const char *lbm_strerror(int code)
+{
+    switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_INVALID_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "out of device memory (or arena too small)";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_CAPACITY: return "too many divisions in one step for the planner";
+    case LBM_ERR_NO_DEVICE: return "no usable CUDA device (compute capability 10.3 required)";
+    default: return "unknown error";
+    }
+}
+
+const char *lbm_last_cuda_error(void) { return g_cuda_err; }
+
+const char *lbm_version(void) { return "0.1.0 sm_103a"; }
+
+} // extern "C"

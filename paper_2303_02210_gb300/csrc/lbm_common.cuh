@@ -1,0 +1,159 @@
+// Shared definitions of the CUDA library: D2Q9 lattice constants, the Philox
+// generator, the device-resident scalar block and the launch descriptor.
+//
+// Lattice: D2Q9 (the paper's Sec. II lattice is D2Q7; this library implements
+// the D2Q9 analogue). Directions 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1)
+// 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1); opposite pairs 1-3, 2-4, 5-7, 6-8.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int NQ = 9;
+__host__ __device__ constexpr int ex(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
+__host__ __device__ constexpr int ey(int i) { return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0); }
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
+// Weights 4/9, 1/9, 1/36 (D2Q9, c_s^2 = 1/3).
+template <typename R>
+__host__ __device__ constexpr R wq(int i) { return i == 0 ? R(4) / R(9) : (i <= 4 ? R(1) / R(9) : R(1) / R(36)); }
+// Division pairs (Sec. II, "two opposite lattice vectors"): pair p loads
+// directions pair_a(p) and pair_b(p) = opp(pair_a(p)).
+__host__ __device__ constexpr int pair_a(int p) { return p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 6)); }
+__host__ __device__ constexpr int pair_b(int p) { return opp(pair_a(p)); }
+
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opp axis");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp diag");
+
+enum GrowthMode { GROW_NONE = 0, GROW_BULK = 1, GROW_DENSITY = 2, GROW_EDGE = 3, GROW_BAND = 4 };
+enum { STREAM_PROLIF = 1u, STREAM_INIT = 2u, STREAM_NOISE = 16u };
+enum { ST_FRONT_AT_TOP = 1, ST_STARVED = 2, ST_CAPACITY = 4 };
+
+// Fixed-point unit of the exact mass sums: 2^-24 per count.
+constexpr double kFixScale = 16777216.0;
+constexpr double kFixInv = 5.9604644775390625e-08;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the
+// 4x32 S-box, multipliers 0xD2511F53 / 0xCD9E8D57, key bumped by the Weyl
+// constants 0x9E3779B9 / 0xBB67AE85 between rounds.
+struct u32x4 {
+    uint32_t x, y, z, w;
+};
+
+// Round keys of one Philox key: k0 + r * 0x9E3779B9, k1 + r * 0xBB67AE85 for
+// r = 0..9. Precomputed once per simulation so that inside kernels they are
+// constant operands rather than per-call arithmetic.
+struct PhiloxKey {
+    uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline PhiloxKey philox_key(uint32_t k0, uint32_t k1)
+{
+    PhiloxKey k;
+    for (int r = 0; r < 10; ++r) {
+        k.k0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        k.k1[r] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    return k;
+}
+
+__host__ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const PhiloxKey &k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        // one 32 x 32 -> 64-bit product per multiplier
+        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c.z;
+        c = u32x4{(uint32_t)(p1 >> 32) ^ c.y ^ k.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.k1[r],
+                  (uint32_t)p0};
+    }
+    return c;
+}
+
+// Uniform on (0, 1): (v + 1/2) 2^-32, exact in double.
+__host__ __device__ __forceinline__ double u01(uint32_t v) { return ((double)v + 0.5) * 2.3283064365386963e-10; }
+
+// ---------------------------------------------------------------------------
+// Device-resident scalars of one simulation. Written by the kernels only
+// (besides initialisation), read back by the host on demand.
+struct DevScalars {
+    long long step;
+    long long mass_fix;       // active mass M, fixed point
+    long long quiescent_fix;  // mass behind the rear wall
+    unsigned long long mass_accum; // per-step accumulator of the update kernel
+    long long S1, S2;
+    long long ns_last, ns_total, div_total, starved_steps, cand_last, events_last;
+    long long node_updates;
+    double carry, hbar, w, clip_mass;
+    int y_r, y_copy, y_hi, H_top, hmin;
+    int maxmass_accum; // highest row holding mass, accumulated by the update kernel
+    int status;
+    int n_events;      // distinct (node, pair) events of the latest step
+    // accumulators of the multi-block observer (reset by its last block)
+    long long S1_acc, S2_acc;
+    int top_acc, low_acc;
+    unsigned int obs_done;
+    int pad0;
+    // proliferation plan for the next step, made by the observer from the
+    // state after the latest step and committed by the selector
+    long long plan_req;   // n_s = floor(g M / rho_cell + carry)
+    long long plan_ns;    // divisions to draw (0 if nothing can be drawn)
+    long long plan_kc;    // candidates evaluated by the parallel pass (multiple of 32)
+    unsigned long long plan_nwin; // candidate nodes
+    double plan_carry;    // carried fraction after this step's n_s
+    double acc_ratio;     // candidates per division seen last time
+    int plan_ylo;         // first candidate row
+    int plan_nwin_zero;   // n_s > 0 but no candidate row
+};
+
+// Everything a kernel needs to know about one simulation.
+struct SimDev {
+    void *f[2];          // population copies, [q][y][x] with row pitch Wp
+    uint32_t *mask;      // occupancy bits, [y][Wp/32]
+    int32_t *heights;    // h(x), W entries
+    DevScalars *sc;
+    // proliferation planner
+    uint32_t *cflags;    // accept bit per candidate of the parallel pass
+    uint32_t *ckeys;     // node*4 + pair per candidate of the parallel pass
+    uint32_t *gkl;       // accepted keys in draw order (large n_s)
+    int32_t *gwpref;     // accepted count before each word of cflags (large n_s)
+    uint32_t *hkeys;     // open-addressing table for large n_s, key = node*4 + pair
+    uint32_t *hcnt;
+    int32_t *hlist;      // slots in insertion order
+    long long *ev_node;  // exported events of the latest step
+    int32_t *ev_pair, *ev_count;
+    int32_t *rows0;      // initial occupied rows per column
+    int W, H, Wp, MW;
+    long long P;         // plane stride in elements (Wp * H)
+    int hcap, ns_max;
+    long long kc_max;    // capacity of cflags in candidates
+    // model constants (all derived on the host once, in double)
+    double omega, cmu, rho_c, rho_cell, half_cell, growth_rate, rho0, sigma;
+    double rho_init, rho_jitter, wall_min_gap, wall_w_factor;
+    uint32_t key0, key1, sim;
+    PhiloxKey pk;        // round keys of (key0, key1)
+    int growth_mode, edge_depth, band_rows, wall_mode, negfix, y_periodic;
+    int update_grid;     // persistent grid of the update kernel
+    int cand_grid;       // grid of the candidate pass
+};
+
+// Launchers of one precision (implemented once per storage type).
+struct KernelTable {
+    int elem_bytes;
+    cudaError_t (*fill)(const SimDev &, cudaStream_t);
+    cudaError_t (*scan)(const SimDev &, int cur, cudaStream_t);
+    cudaError_t (*observe)(const SimDev &, int cur, int init, cudaStream_t);
+    cudaError_t (*cand)(const SimDev &, int cur, uint32_t t, cudaStream_t);
+    cudaError_t (*select)(const SimDev &, int cur, uint32_t t, cudaStream_t);
+    cudaError_t (*update)(const SimDev &, int cur, uint32_t t, cudaStream_t);
+    cudaError_t (*fields)(const SimDev &, int cur, double *rho, double *ux, double *uy, cudaStream_t);
+    int (*update_blocks_per_sm)();
+    int update_tile_x; // columns per block of the update kernel
+};
+
+extern const KernelTable kTableF32;
+extern const KernelTable kTableF64;
+
+} // namespace lbm

@@ -1,0 +1,1044 @@
+// Kernels of the growing-tissue LBM hot path, templated on the population
+// storage type R (float: fast path; double: debug path, compiled without FMA
+// contraction so that it rounds exactly like the FP64 CPU oracle).
+//
+// One time step (App. A of Killeen et al., arXiv 2303.02210) is four launches:
+//   k_cand,   proliferation (Sec. II, Eq. 5): counter-based candidate draws,
+//   k_select  acceptance on the streamed density rho*, first-n_s selection in
+//             draw order, merge of repeated sites and injection of
+//             count * rho_cell/2 into the two pre-stream slots that stream into
+//             each chosen (node, pair).
+//   k_update  the fused pass over the active window: pull streaming with
+//             half-way bounce-back walls, moments (Eq. 1), friction u*, f^SS
+//             (Eq. 3), BGK relaxation or reversal below rho_c (Eq. 2 and the
+//             two-step bounce-back of Sec. II), Philox noise (Eq. 4), the
+//             negative-population fix (App. A step 7), the store, the occupancy
+//             bitmask (one warp ballot per 32 nodes) and the exact fixed-point
+//             mass / top-mass-row reductions. Persistent grid.
+//   k_observe front heights from the bitmask (warp ballots), Eq. 6 sums,
+//             the rear-wall rule (App. A, last paragraph), the active mass,
+//             the next window and the next step's proliferation plan.
+#pragma once
+
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+template <typename R>
+__device__ __forceinline__ long long fix24(R r);
+// FP32: v = r * 2^24 is exact, and v >= 0 (populations are non-negative).
+// Below 2^23 the add of 2^23 rounds v to the nearest integer (ties to even)
+// in the mantissa; from 2^23 on v is already an integer and its bits give it
+// directly. No conversion instruction (those run on a slow pipe).
+template <>
+__device__ __forceinline__ long long fix24<float>(float r)
+{
+    const float v = r * 16777216.0f;
+    if (v < 8388608.0f) return (long long)(__float_as_uint(v + 8388608.0f) - 0x4B000000u);
+    const uint32_t b = __float_as_uint(v);
+    const uint32_t e = (b >> 23) - 150u;
+    if (e < 8u) return (long long)(((b & 0x7FFFFFu) | 0x800000u) << e);
+    return __float2ll_rn(v); // rho >= 128
+}
+template <>
+__device__ __forceinline__ long long fix24<double>(double r) { return __double2ll_rn(r * 16777216.0); }
+
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_max_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_min_i(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Index of the pre-stream slot that streams into direction d of node (x, y):
+// the neighbour (x - ex_d, y - ey_d), or, across a wall, the node's own
+// opposite population (half-way bounce-back).
+__device__ __forceinline__ long long pull_slot(const SimDev &d, int y_r, int x, int y, int q)
+{
+    int ys = y - ey(q);
+    if (d.y_periodic) {
+        ys = ys < 0 ? ys + d.H : (ys >= d.H ? ys - d.H : ys);
+    } else if (ys < y_r || ys >= d.H) {
+        return (long long)opp(q) * d.P + (long long)y * d.Wp + x;
+    }
+    int xs = x - ex(q);
+    xs = xs < 0 ? xs + d.W : (xs >= d.W ? xs - d.W : xs);
+    return (long long)q * d.P + (long long)ys * d.Wp + xs;
+}
+
+// ===========================================================================
+// Initial state (App. A, first paragraph): rho = rho_init (optionally
+// jittered by U[1 - j, 1 + j]) below the front, zero above, u = 0,
+// f_i = f^SS_i(rho, 0) = w_i rho. Written into both population copies.
+template <typename R>
+__global__ void k_fill(SimDev d)
+{
+    R *f0 = (R *)d.f[0];
+    R *f1 = (R *)d.f[1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) { // scalar block (zeroed before this launch)
+        d.sc->maxmass_accum = -1;
+        d.sc->low_acc = 0x7fffffff;
+    }
+    const long long total = (long long)d.H * d.Wp;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(idx / d.Wp), x = (int)(idx % d.Wp);
+        double rho = 0.0;
+        if (x < d.W && y < d.rows0[x]) {
+            rho = d.rho_init;
+            if (d.rho_jitter != 0.0) {
+                const u32x4 r = philox4x32_10(u32x4{(uint32_t)(y * d.W + x), 2u, STREAM_INIT, d.sim}, d.pk);
+                rho = d.rho_init * (1.0 + d.rho_jitter * (2.0 * u01(r.x) - 1.0));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            const R v = (R)(wq<double>(i) * rho);
+            f0[i * d.P + idx] = v;
+            f1[i * d.P + idx] = v;
+        }
+    }
+}
+
+// Occupancy mask, exact mass and highest mass row of rows [y_r, H) of copy
+// `cur` (initial state, or populations set by the caller).
+template <typename R>
+__global__ void k_scan(SimDev d, int cur)
+{
+    const R *f = (const R *)d.f[cur];
+    const int y_r = d.sc->y_r;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long words = (long long)(d.H - y_r) * d.MW;
+    long long mass = 0;
+    int maxrow = -1;
+    for (long long wi = (((long long)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; wi < words; wi += nwarps) {
+        const int y = y_r + (int)(wi / d.MW);
+        const int m = (int)(wi % d.MW);
+        const int x = m * 32 + lane;
+        const bool ok = x < d.W;
+        R rho = R(0);
+        bool any = false;
+        if (ok) {
+            const long long n = (long long)y * d.Wp + x;
+            rho = f[n];
+            any = rho != R(0);
+#pragma unroll
+            for (int i = 1; i < NQ; ++i) {
+                const R v = f[i * d.P + n];
+                rho = rho + v;
+                any |= v != R(0);
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, ok && rho >= (R)d.rho_c);
+        if (lane == 0) d.mask[(long long)y * d.MW + m] = b;
+        if (ok) mass += fix24<R>(rho);
+        if (any) maxrow = y;
+    }
+    mass = warp_sum_ll(mass);
+    maxrow = warp_max_i(maxrow);
+    if (lane == 0) {
+        atomicAdd(&d.sc->mass_accum, (unsigned long long)mass);
+        atomicMax(&d.sc->maxmass_accum, maxrow);
+    }
+}
+
+// ===========================================================================
+// Per-node collision pieces of the update kernel.
+//
+// FP64 (debug path): every formula in the order of the CPU oracle, so the
+// results agree bit for bit. FP32 (fast path): the same quantities, regrouped
+// (algebraically identical in exact arithmetic) for fewer instructions:
+//  * u* = (1 - mu) j / rho with one reciprocal;
+//  * Eq. 3 by opposite pairs: with p = 1 - 3/2 u*.u* + 9/2 (e.u*)^2 and
+//    q = 3 e.u*, the factor is p + q for e and p - q for -e;
+//  * f_0 = rho - sum_{i>0} f_i, i.e. the BGK step's exact mass conservation
+//    (sum_i w_i (1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u) = 1), which keeps the
+//    rounding of the float weights from drifting the total mass;
+//  * the noise uniforms built from mantissa bits (no integer conversions).
+template <typename R>
+struct Consts {
+    R omega, cmu, om1, ow0, ow1, ow5, two_sigma;
+};
+
+template <typename R>
+__device__ __forceinline__ Consts<R> make_consts(const SimDev &d)
+{
+    Consts<R> c;
+    c.omega = (R)d.omega;
+    c.cmu = (R)d.cmu;
+    c.om1 = (R)(1.0 - d.omega);
+    c.ow0 = (R)(d.omega * (4.0 / 9.0));
+    c.ow1 = (R)(d.omega * (1.0 / 9.0));
+    c.ow5 = (R)(d.omega * (1.0 / 36.0));
+    c.two_sigma = (R)(2.0 * d.sigma);
+    return c;
+}
+
+template <typename R>
+__device__ __forceinline__ void collide(const R *g, R rho, R *fo, const Consts<R> &c)
+{
+    const R jx = ((((g[1] - g[3]) + g[5]) - g[6]) - g[7]) + g[8];
+    const R jy = ((((g[2] - g[4]) + g[5]) + g[6]) - g[7]) - g[8];
+    if constexpr (sizeof(R) == 8) {
+        const R ux = jx / rho, uy = jy / rho;
+        const R usx = c.cmu * ux, usy = c.cmu * uy; // u* = (1 - mu) u
+        const R uu = usx * usx + usy * usy;
+        const R eu[NQ] = {R(0), usx, usy, -usx, -usy, usx + usy, -usx + usy, -usx - usy, usx - usy};
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            R t1 = R(1) + R(3) * eu[i];
+            t1 = t1 + R(4.5) * (eu[i] * eu[i]);
+            t1 = t1 - R(1.5) * uu;
+            const R fss = (wq<R>(i) * rho) * t1;    // Eq. 3, D2Q9
+            fo[i] = g[i] - c.omega * (g[i] - fss); // Eq. 2
+        }
+    } else {
+        const float k = c.cmu * __frcp_rn(rho);
+        const float usx = jx * k, usy = jy * k;
+        const float A = fmaf(-1.5f, fmaf(usx, usx, usy * usy), 1.0f);
+        const float r1 = c.ow1 * rho, r5 = c.ow5 * rho;
+        float e, p, q;
+        e = usx;
+        p = fmaf(4.5f * e, e, A);
+        q = 3.0f * e;
+        fo[1] = fmaf(c.om1, g[1], r1 * (p + q));
+        fo[3] = fmaf(c.om1, g[3], r1 * (p - q));
+        e = usy;
+        p = fmaf(4.5f * e, e, A);
+        q = 3.0f * e;
+        fo[2] = fmaf(c.om1, g[2], r1 * (p + q));
+        fo[4] = fmaf(c.om1, g[4], r1 * (p - q));
+        e = usx + usy;
+        p = fmaf(4.5f * e, e, A);
+        q = 3.0f * e;
+        fo[5] = fmaf(c.om1, g[5], r5 * (p + q));
+        fo[7] = fmaf(c.om1, g[7], r5 * (p - q));
+        e = usy - usx;
+        p = fmaf(4.5f * e, e, A);
+        q = 3.0f * e;
+        fo[6] = fmaf(c.om1, g[6], r5 * (p + q));
+        fo[8] = fmaf(c.om1, g[8], r5 * (p - q));
+        // fo[0] is set by rest_from_mass() once the noise is added
+    }
+}
+
+// FP32: f_0 = rho - sum_{i>0} f_i. BGK (Eq. 2) and the noise (Eq. 4) both
+// conserve the node's mass exactly, so this is f_0 in exact arithmetic; in
+// floating point it keeps the rounding of constants from drifting the mass.
+template <typename R>
+__device__ __forceinline__ void rest_from_mass(R *fo, R rho)
+{
+    if constexpr (sizeof(R) == 4)
+        fo[0] = rho - ((((fo[1] + fo[2]) + (fo[3] + fo[4])) + ((fo[5] + fo[6]) + (fo[7] + fo[8]))));
+}
+
+// Eq. 4: eta_i = 2 sigma (u_i - mean u), u_i uniform with 23 random bits from
+// the Philox blocks (n, t, 16, sim) and (n, t, 17, sim).
+template <typename R>
+__device__ __forceinline__ void add_noise(R *fo, uint32_t n, uint32_t t, const SimDev &d, const Consts<R> &c)
+{
+    const u32x4 a = philox4x32_10(u32x4{n, t, STREAM_NOISE + 0u, d.sim}, d.pk);
+    const u32x4 b = philox4x32_10(u32x4{n, t, STREAM_NOISE + 1u, d.sim}, d.pk);
+    const uint32_t m[NQ] = {a.x >> 9, a.y >> 9, a.z >> 9, a.w >> 9, b.x >> 9, b.y >> 9, b.z >> 9, b.w >> 9,
+                            ((a.x & 511u) << 14) | ((a.y & 511u) << 5) | ((a.z & 511u) >> 4)};
+    if constexpr (sizeof(R) == 8) {
+        double u[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) u[i] = ((double)m[i] + 0.5) * 1.1920928955078125e-07;
+        double S = u[0];
+#pragma unroll
+        for (int i = 1; i < NQ; ++i) S = S + u[i];
+        const double ubar = S / 9.0;
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) fo[i] = fo[i] + c.two_sigma * (u[i] - ubar);
+    } else {
+        // 1 + m 2^-23 exactly; the constant offset cancels in u_i - mean u
+        float v[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) v[i] = __uint_as_float(0x3F800000u | m[i]);
+        const float S = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
+        const float nb = -c.two_sigma * (S * (1.0f / 9.0f));
+#pragma unroll
+        for (int i = 1; i < NQ; ++i) fo[i] = fo[i] + fmaf(c.two_sigma, v[i], nb);
+    }
+}
+
+// App. A step 7: negative-population correction. Returns the mass it adds.
+template <typename R>
+__device__ __forceinline__ R fix_negative(R *fo, int mode)
+{
+    R added = R(0);
+    if constexpr (sizeof(R) == 4) {
+        const float mn = fminf(fminf(fminf(fo[0], fo[1]), fminf(fo[2], fo[3])),
+                               fminf(fminf(fo[4], fo[5]), fminf(fminf(fo[6], fo[7]), fo[8])));
+        if (mn >= 0.0f) return added; // the common case
+    }
+    if (mode == 0) {
+        if (fo[0] < R(0)) {
+            R r0 = fo[0];
+#pragma unroll
+            for (int i = 1; i < NQ; ++i) r0 = r0 + fo[i];
+            fo[0] = R(0);
+            R sm = fo[0];
+#pragma unroll
+            for (int i = 1; i < NQ; ++i) sm = sm + fo[i];
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) fo[i] = (r0 * fo[i]) / sm;
+        }
+#pragma unroll
+        for (int i = 1; i < NQ; ++i) {
+            if (fo[i] < R(0)) {
+                const R a = -fo[i];
+                fo[opp(i)] = fo[opp(i)] + a;
+                fo[i] = R(0);
+                added += a + a;
+            }
+        }
+    } else {
+        bool neg = false;
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) neg |= fo[i] < R(0);
+        if (neg) {
+            R r0 = fo[0];
+#pragma unroll
+            for (int i = 1; i < NQ; ++i) r0 = r0 + fo[i];
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) fo[i] = fo[i] < R(0) ? R(0) : fo[i];
+            R sm = fo[0];
+#pragma unroll
+            for (int i = 1; i < NQ; ++i) sm = sm + fo[i];
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) fo[i] = (r0 * fo[i]) / sm;
+        }
+    }
+    return added;
+}
+
+// ===========================================================================
+// Fused update of the active window (App. A steps 1, 2, 4-7; the injection of
+// step 3 was already added to the pre-stream slots by k_select).
+template <typename R, int TPB, int NR>
+__global__ void __launch_bounds__(TPB) k_update(SimDev d, int cur, uint32_t t)
+{
+    const R *__restrict__ fin = (const R *)d.f[cur];
+    R *__restrict__ fout = (R *)d.f[cur ^ 1];
+    const int y_r = d.sc->y_r, y_copy = d.sc->y_copy, y_hi = d.sc->y_hi;
+    const int W = d.W, H = d.H, Wp = d.Wp;
+    const long long P = d.P;
+    const int lane = threadIdx.x & 31;
+
+    // Rows the rear wall has just frozen: bring this copy up to date.
+    if (y_copy < y_r) {
+        const long long n = (long long)(y_r - y_copy) * Wp;
+        for (long long k = (long long)blockIdx.x * TPB + threadIdx.x; k < n; k += (long long)gridDim.x * TPB) {
+            const long long o = (long long)y_copy * Wp + k;
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) fout[i * P + o] = fin[i * P + o];
+        }
+    }
+
+    const R rho_c = (R)d.rho_c;
+    const Consts<R> cf = make_consts<R>(d);
+    const bool noise = d.sigma != 0.0;
+    const bool periodic = d.y_periodic != 0;
+    const int ncx = (W + TPB - 1) / TPB;
+    const int nrows = y_hi - y_r;
+    long long mass = 0;
+    int maxrow = -1;
+    R clip = R(0); // mass added by the negative-population fix, this thread
+    if (nrows > 0) {
+        // the grid is a multiple of the column-tile count: each block keeps
+        // one column tile and strides over the rows
+        const int nty = (nrows + NR - 1) / NR;
+        const int tx = (int)(blockIdx.x % ncx);
+        const int ty_step = (int)(gridDim.x / ncx);
+        for (int ty = (int)(blockIdx.x / ncx); ty < nty; ty += ty_step) {
+            const int x = tx * TPB + threadIdx.x;
+            const bool colok = x < W;
+            const int xm = x == 0 ? W - 1 : x - 1;
+            const int xp = x >= W - 1 ? 0 : x + 1;
+            R fs[NR][NQ];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int y = y_r + ty * NR + r;
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) fs[r][i] = R(0);
+                if (y < y_hi && colok) {
+                    const bool bb_lo = !periodic && y - 1 < y_r;
+                    const bool bb_hi = !periodic && y + 1 >= H;
+                    const int ym = periodic ? (y == 0 ? H - 1 : y - 1) : y - 1;
+                    const int yp = periodic ? (y == H - 1 ? 0 : y + 1) : y + 1;
+                    const R *rc = fin + (long long)y * Wp;
+                    const R *rm = fin + (long long)ym * Wp;
+                    const R *rp = fin + (long long)yp * Wp;
+                    fs[r][0] = rc[x];
+                    fs[r][1] = rc[P + xm];
+                    fs[r][3] = rc[3 * P + xp];
+                    if (bb_lo) {
+                        fs[r][2] = rc[4 * P + x];
+                        fs[r][5] = rc[7 * P + x];
+                        fs[r][6] = rc[8 * P + x];
+                    } else {
+                        fs[r][2] = rm[2 * P + x];
+                        fs[r][5] = rm[5 * P + xm];
+                        fs[r][6] = rm[6 * P + xp];
+                    }
+                    if (bb_hi) {
+                        fs[r][4] = rc[2 * P + x];
+                        fs[r][7] = rc[5 * P + x];
+                        fs[r][8] = rc[6 * P + x];
+                    } else {
+                        fs[r][4] = rp[4 * P + x];
+                        fs[r][7] = rp[7 * P + xp];
+                        fs[r][8] = rp[8 * P + xm];
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int y = y_r + ty * NR + r;
+                if (y >= y_hi) break; // uniform across the block
+                const R *g = fs[r];
+                // Eq. 1 on f*: density in index order
+                R rho = g[0];
+#pragma unroll
+                for (int i = 1; i < NQ; ++i) rho = rho + g[i];
+                const bool occ = colok && rho >= rho_c;
+                R fo[NQ];
+                if (occ) {
+                    collide<R>(g, rho, fo, cf);
+                    if (noise) add_noise<R>(fo, (uint32_t)(y * W + x), t, d, cf);
+                    rest_from_mass<R>(fo, rho);
+                    clip += fix_negative<R>(fo, d.negfix);
+                } else {
+                    // rho < rho_c: reverse the directions (two-step bounce-back)
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) fo[i] = g[opp(i)];
+                }
+                const unsigned bits = __ballot_sync(0xffffffffu, occ);
+                const int wx0 = x - lane;
+                if (lane == 0 && wx0 < Wp) d.mask[(long long)y * d.MW + (wx0 >> 5)] = bits;
+                if (colok) {
+                    R *o = fout + (long long)y * Wp + x;
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) o[i * P] = fo[i];
+                    // populations are non-negative after every step, so the
+                    // node holds mass iff their sum is non-zero
+                    R ro = fo[0];
+#pragma unroll
+                    for (int i = 1; i < NQ; ++i) ro = ro + fo[i];
+                    mass += fix24<R>(ro);
+                    if (ro != R(0)) maxrow = y;
+                }
+            }
+        }
+    }
+    mass = warp_sum_ll(mass);
+    maxrow = warp_max_i(maxrow);
+    const double clipd = warp_sum_d((double)clip);
+    if (lane == 0) {
+        if (mass != 0) atomicAdd(&d.sc->mass_accum, (unsigned long long)mass);
+        if (maxrow >= 0) atomicMax(&d.sc->maxmass_accum, maxrow);
+        if (clipd != 0.0) atomicAdd(&d.sc->clip_mass, clipd);
+    }
+}
+
+// ===========================================================================
+// Proliferation (App. A step 3; Sec. II and Eq. 5), planned by the observer
+// at the end of the previous step, then two launches:
+//   k_cand   all SMs evaluate the first plan_kc candidates of the counter
+//            stream (Philox (k, t, 1, sim)): node, pair, rho* gathered from
+//            the 9 pre-stream slots, acceptance by the growth mode; one accept
+//            bit per candidate (warp ballot).
+//   k_select one block: block scan of the accept bits, the first n_s accepted
+//            candidates in draw order (more are drawn here if the parallel
+//            pass came up short), repeated (node, pair) merged in a hash table
+//            (shared memory up to SEL_SMEM_EVENTS divisions), and the
+//            injection of count * rho_cell/2 into the two pre-stream slots of
+//            each (node, pair).
+
+template <typename R>
+__device__ __forceinline__ R rho_star(const SimDev &d, const R *f, int y_r, int x, int y)
+{
+    long long o[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) o[q] = pull_slot(d, y_r, x, y, q);
+    R v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = f[o[q]];
+    R r = v[0];
+#pragma unroll
+    for (int q = 1; q < NQ; ++q) r = r + v[q];
+    return r;
+}
+
+struct Candidate {
+    int x, y, pair;
+    uint32_t u; // acceptance uniform word (density-dependent growth)
+};
+
+__device__ __forceinline__ Candidate draw_candidate(const SimDev &d, long long k, uint32_t t, int ylo,
+                                                    unsigned long long nwin)
+{
+    const u32x4 r = philox4x32_10(u32x4{(uint32_t)k, t, STREAM_PROLIF, d.sim}, d.pk);
+    const unsigned long long idx = ((unsigned long long)r.x * nwin) >> 32;
+    const long long node = (long long)ylo * d.W + (long long)idx;
+    Candidate c;
+    c.y = (int)(node / d.W);
+    c.x = (int)(node % d.W);
+    c.pair = (int)(r.y >> 30);
+    c.u = r.z;
+    return c;
+}
+
+template <typename R>
+__device__ __forceinline__ bool accept(const SimDev &d, const R *f, int y_r, const Candidate &c)
+{
+    const R rs = rho_star<R>(d, f, y_r, c.x, c.y);
+    switch (d.growth_mode) {
+    case GROW_BULK:
+    case GROW_BAND: return rs >= (R)d.rho_c;
+    case GROW_EDGE: return rs >= (R)d.rho_c && (d.heights[c.x] - c.y) <= d.edge_depth;
+    case GROW_DENSITY: return (double)rs > d.rho_c && u01(c.u) < 1.0 - (double)rs / d.rho0; // Eq. 5
+    default: return false;
+    }
+}
+
+constexpr int CAND_TPB = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(CAND_TPB) k_cand(SimDev d, int cur, uint32_t t)
+{
+    const DevScalars *sc = d.sc;
+    const long long ns = sc->plan_ns, kc = sc->plan_kc;
+    if (ns <= 0) return;
+    const R *f = (const R *)d.f[cur];
+    const int y_r = sc->y_r, ylo = sc->plan_ylo;
+    const unsigned long long nwin = sc->plan_nwin;
+    const long long stride = (long long)gridDim.x * CAND_TPB;
+    for (long long k = (long long)blockIdx.x * CAND_TPB + threadIdx.x; k < kc; k += stride) {
+        const Candidate c = draw_candidate(d, k, t, ylo, nwin);
+        const bool ok = accept<R>(d, f, y_r, c);
+        const unsigned b = __ballot_sync(0xffffffffu, ok);
+        if ((threadIdx.x & 31) == 0) d.cflags[k >> 5] = b;
+        d.ckeys[k] = (uint32_t)(((long long)c.y * d.W + c.x) * 4 + c.pair);
+    }
+}
+
+constexpr int SEL_TPB = 1024;
+constexpr int SEL_SMEM_SLOTS = 16384;  // hash slots in shared memory
+constexpr int SEL_SMEM_EVENTS = 8192;  // divisions per step handled in shared memory
+constexpr int SEL_SMEM_WORDS = 4096;   // accept-bit words handled in shared memory
+constexpr size_t SEL_SMEM_BYTES =
+    (size_t)SEL_SMEM_SLOTS * 8 + (size_t)SEL_SMEM_EVENTS * 8 + (size_t)SEL_SMEM_WORDS * 4;
+constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;
+
+struct EventTable {
+    uint32_t *keys;
+    uint32_t *cnt;
+    int32_t *list;
+    unsigned mask; // slots - 1
+};
+
+__device__ __forceinline__ void table_insert(const EventTable &tb, uint32_t key, int *nlist)
+{
+    unsigned slot = (unsigned)(((unsigned long long)key * 0x9E3779B97F4A7C15ull) >> 32) & tb.mask;
+    for (unsigned probe = 0; probe <= tb.mask; ++probe) {
+        const uint32_t old = atomicCAS(&tb.keys[slot], EMPTY_KEY, key);
+        if (old == EMPTY_KEY) {
+            atomicAdd(&tb.cnt[slot], 1u);
+            tb.list[atomicAdd(nlist, 1)] = (int)slot;
+            return;
+        }
+        if (old == key) {
+            atomicAdd(&tb.cnt[slot], 1u);
+            return;
+        }
+        slot = (slot + 1u) & tb.mask;
+    }
+}
+
+// exclusive block scan of one int per thread; returns the prefix, *total the sum
+__device__ __forceinline__ long long block_exscan(long long v, long long *total, long long *s_w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const long long a = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0;
+        long long b = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) b += u;
+        }
+        s_w[lane] = b - a;
+        if (lane == 31) s_w[32] = b;
+    }
+    __syncthreads();
+    const long long r = s_w[warp] + incl - v;
+    *total = s_w[32];
+    __syncthreads();
+    return r;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(SEL_TPB) k_select(SimDev d, int cur, uint32_t t)
+{
+    extern __shared__ unsigned char smem[];
+    __shared__ long long s_w[33];
+    __shared__ long long s_kstop, s_acc;
+    __shared__ int s_nlist;
+    R *f = (R *)d.f[cur];
+    DevScalars *sc = d.sc;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long ns = sc->plan_ns, kc = sc->plan_kc;
+    const long long cap = 64 * ns + 1024;
+    const long long nw = kc >> 5;
+    const int y_r = sc->y_r, ylo = sc->plan_ylo;
+    const unsigned long long nwin = sc->plan_nwin;
+    const bool small = ns <= SEL_SMEM_EVENTS && nw <= SEL_SMEM_WORDS;
+    EventTable tb;
+    uint32_t *kl;  // accepted keys in draw order
+    int32_t *wpref; // accepted candidates before each accept-bit word
+    if (small) {
+        tb.keys = (uint32_t *)smem;
+        tb.cnt = tb.keys + SEL_SMEM_SLOTS;
+        tb.list = (int32_t *)(tb.cnt + SEL_SMEM_SLOTS);
+        kl = (uint32_t *)(tb.list + SEL_SMEM_EVENTS);
+        wpref = (int32_t *)(kl + SEL_SMEM_EVENTS);
+        tb.mask = SEL_SMEM_SLOTS - 1;
+        for (int i = tid; i < SEL_SMEM_SLOTS; i += SEL_TPB) {
+            tb.keys[i] = EMPTY_KEY;
+            tb.cnt[i] = 0u;
+        }
+    } else {
+        tb.keys = d.hkeys;
+        tb.cnt = d.hcnt;
+        tb.list = d.hlist;
+        tb.mask = (unsigned)d.hcap - 1u;
+        kl = d.gkl;
+        wpref = d.gwpref;
+    }
+    if (tid == 0) {
+        s_kstop = 0;
+        s_acc = 0;
+        s_nlist = 0;
+    }
+    __syncthreads();
+    if (ns > 0) {
+        // (1) accepted count before each word of the parallel pass
+        const long long wpt = (nw + SEL_TPB - 1) / SEL_TPB;
+        const long long w0 = (long long)tid * wpt, w1 = w0 + wpt < nw ? w0 + wpt : nw;
+        long long cnt = 0;
+        for (long long w = w0; w < w1; ++w) cnt += __popc(d.cflags[w]);
+        long long total;
+        long long run = block_exscan(cnt, &total, s_w);
+        for (long long w = w0; w < w1; ++w) {
+            wpref[w] = (int32_t)run;
+            run += __popc(d.cflags[w]);
+        }
+        __syncthreads();
+        // (2) the first n_s accepted keys in draw order: one warp per word,
+        // one lane per candidate
+        for (long long w = warp; w < nw; w += SEL_TPB / 32) {
+            const uint32_t word = d.cflags[w];
+            if ((word >> lane) & 1u) {
+                const long long r = wpref[w] + __popc(word & ((1u << lane) - 1u));
+                if (r < ns) {
+                    kl[r] = d.ckeys[(w << 5) + lane];
+                    if (r == ns - 1) s_kstop = (w << 5) + lane + 1;
+                }
+            }
+        }
+        if (tid == 0) s_acc = total;
+        __syncthreads();
+        // (3) merge repeated (node, pair) draws
+        const long long nins = total < ns ? total : ns;
+        for (long long r = tid; r < nins; r += SEL_TPB) table_insert(tb, kl[r], &s_nlist);
+        __syncthreads();
+        // (4) more draws if the parallel pass accepted fewer than n_s
+        for (long long base = kc; s_acc < ns && base < cap; base += SEL_TPB) {
+            const long long k = base + tid;
+            bool ok = false;
+            Candidate c;
+            if (k < cap) {
+                c = draw_candidate(d, k, t, ylo, nwin);
+                ok = accept<R>(d, f, y_r, c);
+            }
+            long long tot;
+            const long long r = s_acc + block_exscan(ok ? 1 : 0, &tot, s_w);
+            if (ok && r < ns) {
+                table_insert(tb, (uint32_t)(((long long)c.y * d.W + c.x) * 4 + c.pair), &s_nlist);
+                if (r == ns - 1) s_kstop = k + 1;
+            }
+            __syncthreads();
+            if (tid == 0) s_acc += tot;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // (3) inject count * rho_cell/2 into the two pre-stream slots of each (node, pair)
+    const int nlist = s_nlist;
+    for (int e = tid; e < nlist; e += SEL_TPB) {
+        const int slot = tb.list[e];
+        const uint32_t key = tb.keys[slot];
+        const int cnt = (int)tb.cnt[slot];
+        const long long node = (long long)(key >> 2);
+        const int p = (int)(key & 3u);
+        const int y = (int)(node / d.W), x = (int)(node % d.W);
+        const R add = (R)((double)cnt * d.half_cell);
+        const long long sa = pull_slot(d, y_r, x, y, pair_a(p));
+        const long long sb = pull_slot(d, y_r, x, y, pair_b(p));
+        f[sa] = f[sa] + add;
+        f[sb] = f[sb] + add;
+        d.ev_node[e] = node;
+        d.ev_pair[e] = p;
+        d.ev_count[e] = cnt;
+        if (!small) {
+            tb.keys[slot] = EMPTY_KEY;
+            tb.cnt[slot] = 0u;
+        }
+    }
+    if (tid == 0) {
+        // commit the plan made at the end of the previous step
+        sc->ns_last = sc->plan_req;
+        sc->ns_total += sc->plan_req;
+        sc->carry = sc->plan_carry;
+        const long long acc = s_acc < ns ? s_acc : ns;
+        sc->div_total += acc;
+        sc->events_last = acc;
+        sc->n_events = nlist;
+        if (sc->plan_nwin_zero) {
+            sc->starved_steps += 1;
+            sc->status |= ST_STARVED;
+            sc->cand_last = 0;
+        } else if (ns > 0 && s_acc < ns) {
+            sc->starved_steps += 1;
+            sc->status |= ST_STARVED;
+            sc->cand_last = cap;
+        } else {
+            sc->cand_last = ns > 0 ? s_kstop : 0;
+        }
+        if (ns > 0 && s_acc >= ns) sc->acc_ratio = (double)s_kstop / (double)ns;
+    }
+}
+
+// ===========================================================================
+// Observables after an update (or of the initial state when init != 0).
+// Many blocks, one warp per 32-column word of the occupancy mask: front heights
+// h(x) = 1 + highest occupied row (32 rows per pass, one ballot per column),
+// partial Eq. 6 sums by atomics. The last block to finish then does the serial
+// part: Eq. 6 width, the rear-wall rule (App. A, last paragraph), the mass of
+// rows it freezes, the active mass, the next window, and the proliferation
+// plan of the next step (n_s from M and the carried fraction, Sec. II).
+constexpr int OBS_TPB = 256;
+constexpr int OBS_WARPS = OBS_TPB / 32;
+
+template <typename R>
+__global__ void __launch_bounds__(OBS_TPB) k_observe(SimDev d, int cur, int init)
+{
+    DevScalars *sc = d.sc;
+    const R *f = (const R *)d.f[cur];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ long long s_a[OBS_WARPS], s_b[OBS_WARPS];
+    __shared__ int s_top[OBS_WARPS], s_low[OBS_WARPS];
+    __shared__ int s_last, s_new_yr;
+    const int y_r = sc->y_r;
+    const int maxmass = sc->maxmass_accum;
+    int ytop = maxmass > y_r - 1 ? maxmass : y_r - 1;
+    if (ytop > d.H - 1) ytop = d.H - 1;
+
+    long long S1 = 0, S2 = 0;
+    int top = 0, low = 0x7fffffff;
+    for (int m = blockIdx.x * OBS_WARPS + warp; m < d.MW; m += gridDim.x * OBS_WARPS) {
+        const int x = m * 32 + lane;
+        unsigned pending = __ballot_sync(0xffffffffu, x < d.W);
+        int h = 0;
+        for (int yb = ytop; yb >= 0 && pending; yb -= 32) {
+            const int y = yb - lane;
+            const unsigned word = y >= 0 ? d.mask[(long long)y * d.MW + m] : 0u;
+            unsigned any = word;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(0xffffffffu, any, o);
+            unsigned todo = pending & any;
+            while (todo) {
+                const int c = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const unsigned b = __ballot_sync(0xffffffffu, (word >> c) & 1u);
+                if (lane == c) h = yb - (__ffs(b) - 1) + 1;
+                pending &= ~(1u << c);
+            }
+        }
+        if (x < d.W) {
+            d.heights[x] = h;
+            S1 += h;
+            S2 += (long long)h * h;
+            top = max(top, h);
+            low = min(low, h);
+        }
+    }
+    S1 = warp_sum_ll(S1);
+    S2 = warp_sum_ll(S2);
+    top = warp_max_i(top);
+    low = warp_min_i(low);
+    if (lane == 0) {
+        s_a[warp] = S1;
+        s_b[warp] = S2;
+        s_top[warp] = top;
+        s_low[warp] = low;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long a = 0, b = 0;
+        int tp = 0, lw = 0x7fffffff;
+        for (int i = 0; i < OBS_WARPS; ++i) {
+            a += s_a[i];
+            b += s_b[i];
+            tp = max(tp, s_top[i]);
+            lw = min(lw, s_low[i]);
+        }
+        atomicAdd((unsigned long long *)&sc->S1_acc, (unsigned long long)a);
+        atomicAdd((unsigned long long *)&sc->S2_acc, (unsigned long long)b);
+        atomicMax(&sc->top_acc, tp);
+        atomicMin(&sc->low_acc, lw);
+        __threadfence();
+        const unsigned ticket = atomicAdd(&sc->obs_done, 1u);
+        s_last = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    volatile DevScalars *vs = sc;
+    if (tid == 0) {
+        const long long a = vs->S1_acc, b = vs->S2_acc;
+        sc->S1 = a;
+        sc->S2 = b;
+        sc->H_top = vs->top_acc;
+        sc->hmin = vs->low_acc;
+        // Eq. 6: w = sqrt(W S2 - S1^2) / W
+        sc->hbar = (double)a / (double)d.W;
+        sc->w = sqrt((double)((long long)d.W * b - a * a)) / (double)d.W;
+        // the rear wall is kept behind the front at all times, the initial
+        // state included
+        int nyr = y_r;
+        if (d.wall_mode == 1 && !d.y_periodic) {
+            double gap = d.wall_min_gap;
+            const double wg = d.wall_w_factor * sc->w;
+            if (wg > gap) gap = wg;
+            double c = floor(sc->hbar - gap);
+            if (c > (double)(d.H - 1)) c = (double)(d.H - 1);
+            const int cand = (int)c;
+            if (cand > nyr) nyr = cand;
+        }
+        s_new_yr = nyr;
+    }
+    __syncthreads();
+    const int nyr = s_new_yr;
+    // mass of the rows the wall freezes now
+    long long fm = 0;
+    if (nyr > y_r) {
+        const long long n = (long long)(nyr - y_r) * d.W;
+        for (long long k = tid; k < n; k += OBS_TPB) {
+            const int y = y_r + (int)(k / d.W), x = (int)(k % d.W);
+            const long long o = (long long)y * d.Wp + x;
+            R r = f[o];
+#pragma unroll
+            for (int i = 1; i < NQ; ++i) r = r + f[i * d.P + o];
+            fm += fix24<R>(r);
+        }
+    }
+    fm = warp_sum_ll(fm);
+    if (lane == 0) s_a[warp] = fm;
+    __syncthreads();
+    if (tid == 0) {
+        long long frozen = 0;
+        for (int i = 0; i < OBS_WARPS; ++i) frozen += s_a[i];
+        const long long acc = (long long)sc->mass_accum;
+        sc->mass_fix = acc - frozen;
+        sc->quiescent_fix += frozen;
+        int yhi;
+        if (d.y_periodic) {
+            yhi = d.H;
+        } else {
+            yhi = maxmass + 2 < d.H ? maxmass + 2 : d.H;
+            if (!init && sc->y_hi > yhi) yhi = sc->y_hi; // the window never shrinks
+        }
+        if (!init) {
+            sc->node_updates += (long long)d.W * (long long)(sc->y_hi > y_r ? sc->y_hi - y_r : 0);
+            sc->step += 1;
+        }
+        sc->y_copy = y_r;
+        sc->y_r = nyr;
+        sc->y_hi = yhi;
+        if (maxmass >= d.H - 1) sc->status |= ST_FRONT_AT_TOP;
+        sc->mass_accum = 0ull;
+        sc->maxmass_accum = -1;
+        sc->S1_acc = 0;
+        sc->S2_acc = 0;
+        sc->top_acc = 0;
+        sc->low_acc = 0x7fffffff;
+        sc->obs_done = 0u;
+        // proliferation plan of the next step (Sec. II): n_s sites from the
+        // active mass and the carried fraction, drawn from the active portion
+        // restricted by the growth mode
+        if (d.growth_mode != GROW_NONE) {
+            const double mass = (double)sc->mass_fix * kFixInv;
+            const double xns = d.growth_rate * mass / d.rho_cell + sc->carry;
+            const double fl = floor(xns);
+            long long ns = (long long)fl;
+            sc->plan_req = ns;
+            sc->plan_carry = xns - fl;
+            int ylo = nyr, yhi_c = sc->H_top;
+            if (d.growth_mode == GROW_EDGE) {
+                const int e = sc->hmin - d.edge_depth;
+                if (e > ylo) ylo = e;
+            } else if (d.growth_mode == GROW_BAND) {
+                if (nyr + d.band_rows < yhi_c) yhi_c = nyr + d.band_rows;
+            }
+            const unsigned long long nwin =
+                yhi_c > ylo ? (unsigned long long)(yhi_c - ylo) * (unsigned long long)d.W : 0ull;
+            if (ns > d.ns_max) {
+                sc->status |= ST_CAPACITY;
+                ns = 0;
+            }
+            sc->plan_nwin_zero = (ns > 0 && nwin == 0) ? 1 : 0;
+            if (nwin == 0) ns = 0;
+            sc->plan_ns = ns;
+            sc->plan_ylo = ylo;
+            sc->plan_nwin = nwin;
+            // candidates for the parallel pass: n_s times the ratio seen last
+            // step, with a margin; the selector draws more if it falls short
+            double ratio = sc->acc_ratio > 1.0 ? sc->acc_ratio : 1.0;
+            long long kc = (long long)ceil((double)ns * ratio * 1.15) + 64;
+            const long long cap = 64 * ns + 1024;
+            if (kc > cap) kc = cap;
+            kc = (kc + 31) & ~31ll;
+            if (kc > d.kc_max) kc = d.kc_max;
+            sc->plan_kc = ns > 0 ? kc : 0;
+        }
+    }
+}
+
+// rho and u of copy `cur` into device arrays of W*H doubles (Eq. 1).
+template <typename R>
+__global__ void k_fields(SimDev d, int cur, double *rho, double *ux, double *uy)
+{
+    const R *f = (const R *)d.f[cur];
+    const long long total = (long long)d.W * d.H;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / d.W), x = (int)(k % d.W);
+        const long long o = (long long)y * d.Wp + x;
+        double g[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) g[i] = (double)f[i * d.P + o];
+        double r = g[0];
+#pragma unroll
+        for (int i = 1; i < NQ; ++i) r = r + g[i];
+        const double jx = ((((g[1] - g[3]) + g[5]) - g[6]) - g[7]) + g[8];
+        const double jy = ((((g[2] - g[4]) + g[5]) + g[6]) - g[7]) - g[8];
+        rho[k] = r;
+        ux[k] = r != 0.0 ? jx / r : 0.0;
+        uy[k] = r != 0.0 ? jy / r : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers of one storage type.
+template <typename R>
+struct Launch {
+    static constexpr int UPD_TPB = 128;
+    static constexpr int UPD_NR = sizeof(R) == 4 ? 2 : 1;
+
+    static cudaError_t fill(const SimDev &d, cudaStream_t s)
+    {
+        k_fill<R><<<4 * 152, 256, 0, s>>>(d);
+        return cudaGetLastError();
+    }
+    static cudaError_t scan(const SimDev &d, int cur, cudaStream_t s)
+    {
+        k_scan<R><<<4 * 152, 256, 0, s>>>(d, cur);
+        return cudaGetLastError();
+    }
+    static cudaError_t observe(const SimDev &d, int cur, int init, cudaStream_t s)
+    {
+        int g = (d.MW + OBS_WARPS - 1) / OBS_WARPS;
+        if (g > 4 * 152) g = 4 * 152;
+        k_observe<R><<<g, OBS_TPB, 0, s>>>(d, cur, init);
+        return cudaGetLastError();
+    }
+    static cudaError_t cand(const SimDev &d, int cur, uint32_t t, cudaStream_t s)
+    {
+        k_cand<R><<<d.cand_grid, CAND_TPB, 0, s>>>(d, cur, t);
+        return cudaGetLastError();
+    }
+    static cudaError_t select(const SimDev &d, int cur, uint32_t t, cudaStream_t s)
+    {
+        // the shared-memory opt-in is per device
+        static bool attr[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev >= 64 || !attr[dev]) {
+            e = cudaFuncSetAttribute(k_select<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEL_SMEM_BYTES);
+            if (e != cudaSuccess) return e;
+            if (dev < 64) attr[dev] = true;
+        }
+        k_select<R><<<1, SEL_TPB, SEL_SMEM_BYTES, s>>>(d, cur, t);
+        return cudaGetLastError();
+    }
+    static cudaError_t update(const SimDev &d, int cur, uint32_t t, cudaStream_t s)
+    {
+        k_update<R, UPD_TPB, UPD_NR><<<d.update_grid, UPD_TPB, 0, s>>>(d, cur, t);
+        return cudaGetLastError();
+    }
+    static cudaError_t fields(const SimDev &d, int cur, double *rho, double *ux, double *uy, cudaStream_t s)
+    {
+        k_fields<R><<<4 * 152, 256, 0, s>>>(d, cur, rho, ux, uy);
+        return cudaGetLastError();
+    }
+    static int update_blocks_per_sm()
+    {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<R, UPD_TPB, UPD_NR>, UPD_TPB, 0) != cudaSuccess)
+            return 0;
+        return n;
+    }
+};
+
+template <typename R>
+constexpr KernelTable make_table()
+{
+    return KernelTable{(int)sizeof(R),        &Launch<R>::fill,   &Launch<R>::scan,
+                       &Launch<R>::observe,   &Launch<R>::cand,   &Launch<R>::select,
+                       &Launch<R>::update,    &Launch<R>::fields, &Launch<R>::update_blocks_per_sm,
+                       Launch<R>::UPD_TPB};
+}
+
+} // namespace lbm

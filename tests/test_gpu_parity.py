@@ -180,3 +180,12 @@ def test_full_size_edge_workload_fp64_exact_and_fp32_close():
     assert flips == 0
     assert e_rho <= RTOL_FP32 and e_u <= RTOL_FP32
     assert g32.stats()["ns_total"] == o.stats()["ns_total"]
+
+
+def test_set_populations_rejects_negative_values():
+    p = wl.lattice_small(seed=1)
+    g = gpu_sim(p, "fp32")
+    f = g.pops()
+    f[3, 5, 5] = -1e-3
+    with pytest.raises(Exception):
+        g.set_pops(f)
