@@ -201,6 +201,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--update-kernel", default="auto", choices=["auto", "plain", "tma", "tma1"])
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -222,8 +223,9 @@ def main():
     from paper_2303_02210_gb300.lbm import Simulation
 
     params = workload_params(rank)
-    sim = Simulation(params, precision=args.precision)
+    sim = Simulation(params, precision=args.precision, update_kernel=args.update_kernel)
     stream = sim.stream
+    kernel_used = {1: "k_update (plain loads)", 2: "k_update_tma (bulk tensor copies)"}[sim.stats()["update_kernel"]]
 
     def barrier():
         if dist is not None:
@@ -272,7 +274,7 @@ def main():
     torch.cuda.synchronize()
     h = np.empty(params["width"], dtype=np.int32)
     t0 = time.perf_counter()
-    sim2 = Simulation(params, precision=args.precision)
+    sim2 = Simulation(params, precision=args.precision, update_kernel=args.update_kernel)
     for _ in range(e2e_steps):
         sim2.step(1)
         h, hbar, w = sim2.front_heights()
@@ -307,7 +309,7 @@ def main():
         "data": "synthetic", "config": workload_config(args.precision),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_update (fused stream/collide/front/noise)",
+                     "kernel": kernel_used + ": fused stream/collide/front/noise",
                      "algorithmic_bytes_per_launch": bpn * nodes_per_launch,
                      "avg_launch_ms": k_ms / max(k_launches, 1), "peak_source": peak_kind},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -38,6 +38,7 @@ extern "C" {
 #define LBM_STATUS_FRONT_AT_TOP 1   /* mass reached row H-1 (the top wall) */
 #define LBM_STATUS_GROWTH_STARVED 2 /* a step accepted fewer than n_s divisions */
 #define LBM_STATUS_CAPACITY 4       /* n_s exceeded the planner capacity; growth skipped */
+#define LBM_STATUS_TIMEOUT 8        /* a bulk copy did not complete in time; the step was abandoned */
 
 /* ---- enumerations used in lbm_params_t ---- */
 enum {
@@ -70,6 +71,9 @@ enum { LBM_FP32 = 0, LBM_FP64 = 1 };
  *  seed, sim_id Philox key and counter word 3
  *  precision    LBM_FP32 (fast path) or LBM_FP64 (debug path, bit-exact
  *               with the CPU oracle)
+ *  update_kernel 0: choose (the TMA-staged kernel for FP32 with walls in y,
+ *               else the plain-load kernel); 1: plain-load kernel; 2: TMA-staged
+ *               kernel (FP32 and y_periodic = 0 only)
  */
 typedef struct {
     double tau, mu, rho_c, rho_cell, sigma, rho0, growth_rate;
@@ -79,7 +83,7 @@ typedef struct {
     int32_t front_kmin, front_kmax, wall_mode, negfix_mode, y_periodic;
     uint32_t sim_id;
     int32_t precision;
-    int32_t reserved;
+    int32_t update_kernel;
 } lbm_params_t;
 
 /* Counters and observables after the latest completed step. */
@@ -102,7 +106,7 @@ typedef struct {
     int32_t hmin;          /* min_x h(x) */
     int32_t y_hi;          /* rows >= y_hi hold no mass (window top) */
     int32_t status;        /* LBM_STATUS_* bits */
-    int32_t reserved;
+    int32_t update_kernel; /* kernel used for the fused update: 1 plain loads, 2 TMA-staged */
 } lbm_stats_t;
 
 typedef struct lbm_sim lbm_sim;

@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/lbm.h"
 #include "lbm_common.cuh"
 
@@ -134,6 +136,37 @@ void front_rows(const lbm_params_t &p, std::vector<int32_t> &rows)
     }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// Population copy as a 3-D FP32 tensor {W, H, 9} with row pitch Wp and plane
+// pitch P elements; `bx` x `by` x 9 boxes. Out-of-range loads read zeros.
+bool encode_population_map(CUtensorMap *m, void *base, int W, int H, int Wp, long long P, int bx, int by)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)Wp * 4u, (cuuint64_t)P * 4u};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 9};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 } // namespace
 
 struct lbm_sim {
@@ -148,6 +181,10 @@ struct lbm_sim {
     int cur;
     int64_t step;
     int64_t launches;
+    // TMA-staged update (FP32, walls in y)
+    bool use_tma;
+    int tma_grid, tma_variant;
+    CUtensorMap maps[2];
     // kernel timing
     std::vector<cudaEvent_t> ev;
     int64_t ev_used;
@@ -177,6 +214,8 @@ int lbm_validate(const lbm_params_t *p)
     if (p->negfix_mode != LBM_NEGFIX_LITERAL && p->negfix_mode != LBM_NEGFIX_RESCALE) return LBM_ERR_INVALID_ARG;
     if (p->precision != LBM_FP32 && p->precision != LBM_FP64) return LBM_ERR_INVALID_ARG;
     if (p->y_periodic != 0 && p->y_periodic != 1) return LBM_ERR_INVALID_ARG;
+    if (p->update_kernel < 0 || p->update_kernel > 3) return LBM_ERR_INVALID_ARG;
+    if (p->update_kernel >= 2 && (p->precision != LBM_FP32 || p->y_periodic)) return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
 
@@ -286,6 +325,15 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     d.wall_mode = p->wall_mode;
     d.negfix = p->negfix_mode;
     d.y_periodic = p->y_periodic;
+    d.noise_on = p->sigma != 0.0;
+    d.f_rho_c = (float)d.rho_c;
+    d.f_omega = (float)d.omega;
+    d.f_cmu = (float)d.cmu;
+    d.f_om1 = (float)(1.0 - d.omega);
+    d.f_ow0 = (float)(d.omega * (4.0 / 9.0));
+    d.f_ow1 = (float)(d.omega * (1.0 / 9.0));
+    d.f_ow5 = (float)(d.omega * (1.0 / 36.0));
+    d.f_two_sigma = (float)(2.0 * p->sigma);
     const int bps = s->kt->update_blocks_per_sm();
     // persistent grid: as many blocks as fit on the SMs, rounded down to a
     // multiple of the column tiles (each block keeps one column tile)
@@ -293,6 +341,20 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     const int g0 = nsm * (bps > 0 ? bps : 1);
     d.update_grid = g0 >= ncx ? (g0 / ncx) * ncx : ncx;
     d.cand_grid = 2 * nsm;
+    s->use_tma = false;
+    s->tma_grid = nsm;
+    s->tma_variant = p->update_kernel == 3 ? 1 : 0;
+    if (p->precision == LBM_FP32 && !p->y_periodic && p->update_kernel != 1) {
+        bool ok = true;
+        for (int b = 0; b < 2 && ok; ++b)
+            ok = encode_population_map(&s->maps[b], d.f[b], d.W, d.H, d.Wp, d.P, kTmaBoxX + 8, kTmaBoxY + 2);
+        s->use_tma = ok;
+        if (!ok && p->update_kernel >= 2) {
+            if (s->own_arena) cudaFree(s->arena);
+            delete s;
+            return LBM_ERR_CUDA;
+        }
+    }
 
     int rc = LBM_OK;
     do {
@@ -333,7 +395,10 @@ int lbm_step(lbm_sim *s, int64_t nsteps)
         }
         const bool timed = s->timing && s->ev_used + 2 <= (int64_t)s->ev.size();
         if (timed) CK(cudaEventRecord(s->ev[s->ev_used], s->stream));
-        CK(s->kt->update(s->d, s->cur, t, s->stream));
+        if (s->use_tma)
+            CK(launch_update_tma_f32(s->d, s->cur, t, s->maps, s->tma_grid, s->tma_variant, s->stream));
+        else
+            CK(s->kt->update(s->d, s->cur, t, s->stream));
         if (timed) {
             CK(cudaEventRecord(s->ev[s->ev_used + 1], s->stream));
             s->ev_used += 2;
@@ -394,6 +459,7 @@ int lbm_stats(lbm_sim *s, lbm_stats_t *out)
     out->hmin = hs.hmin;
     out->y_hi = hs.y_hi;
     out->status = hs.status;
+    out->update_kernel = s->use_tma ? 2 : 1;
     return LBM_OK;
 }
 

@@ -6,6 +6,7 @@
 // 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1); opposite pairs 1-3, 2-4, 5-7, 6-8.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,7 +29,7 @@ static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp dia
 
 enum GrowthMode { GROW_NONE = 0, GROW_BULK = 1, GROW_DENSITY = 2, GROW_EDGE = 3, GROW_BAND = 4 };
 enum { STREAM_PROLIF = 1u, STREAM_INIT = 2u, STREAM_NOISE = 16u };
-enum { ST_FRONT_AT_TOP = 1, ST_STARVED = 2, ST_CAPACITY = 4 };
+enum { ST_FRONT_AT_TOP = 1, ST_STARVED = 2, ST_CAPACITY = 4, ST_TIMEOUT = 8 };
 
 // Fixed-point unit of the exact mass sums: 2^-24 per count.
 constexpr double kFixScale = 16777216.0;
@@ -135,6 +136,10 @@ struct SimDev {
     uint32_t key0, key1, sim;
     PhiloxKey pk;        // round keys of (key0, key1)
     int growth_mode, edge_depth, band_rows, wall_mode, negfix, y_periodic;
+    int noise_on;        // sigma != 0
+    // the same constants rounded to float once on the host, so that no kernel
+    // evaluates double arithmetic per node (the FP64 pipe is narrow)
+    float f_rho_c, f_omega, f_cmu, f_om1, f_ow0, f_ow1, f_ow5, f_two_sigma;
     int update_grid;     // persistent grid of the update kernel
     int cand_grid;       // grid of the candidate pass
 };
@@ -155,5 +160,11 @@ struct KernelTable {
 
 extern const KernelTable kTableF32;
 extern const KernelTable kTableF64;
+
+// TMA-staged FP32 update (lbm_update_tma.cuh). maps[b] loads from copy b
+// (box (128 + 8) x (8 + 2) x 9).
+cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
+                                  int variant, cudaStream_t s);
+constexpr int kTmaBoxX = 128, kTmaBoxY = 8;
 
 } // namespace lbm

@@ -1,6 +1,15 @@
 // FP32 storage and arithmetic: the fast path.
 #include "lbm_kernels.cuh"
+#include "lbm_update_tma.cuh"
 
 namespace lbm {
 const KernelTable kTableF32 = make_table<float>();
+
+static_assert(kTmaBoxX == TMA_TX && kTmaBoxY == TMA_TY, "tensor-map boxes match the kernel tile");
+
+cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
+                                  int variant, cudaStream_t s)
+{
+    return launch_update_tma(d, cur, t, maps, nsm, variant, s);
+}
 } // namespace lbm

@@ -34,14 +34,23 @@ template <>
 __device__ __forceinline__ long long fix24<float>(float r)
 {
     const float v = r * 16777216.0f;
-    if (v < 8388608.0f) return (long long)(__float_as_uint(v + 8388608.0f) - 0x4B000000u);
+    const long long lo = (long long)(__float_as_uint(v + 8388608.0f) - 0x4B000000u);
     const uint32_t b = __float_as_uint(v);
-    const uint32_t e = (b >> 23) - 150u;
-    if (e < 8u) return (long long)(((b & 0x7FFFFFu) | 0x800000u) << e);
-    return __float2ll_rn(v); // rho >= 128
+    const long long hi = (long long)((unsigned long long)((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 150u));
+    return v < 8388608.0f ? lo : hi; // v < 2^63 always (rho < 2^39)
 }
 template <>
 __device__ __forceinline__ long long fix24<double>(double r) { return __double2ll_rn(r * 16777216.0); }
+
+// Occupancy threshold in the storage type (the FP32 copy is rounded on the host).
+template <typename R>
+__device__ __forceinline__ R rho_c_of(const SimDev &d)
+{
+    if constexpr (sizeof(R) == 8)
+        return d.rho_c;
+    else
+        return d.f_rho_c;
+}
 
 __device__ __forceinline__ long long warp_sum_ll(long long v)
 {
@@ -148,7 +157,7 @@ __global__ void k_scan(SimDev d, int cur)
                 any |= v != R(0);
             }
         }
-        const unsigned b = __ballot_sync(0xffffffffu, ok && rho >= (R)d.rho_c);
+        const unsigned b = __ballot_sync(0xffffffffu, ok && rho >= rho_c_of<R>(d));
         if (lane == 0) d.mask[(long long)y * d.MW + m] = b;
         if (ok) mass += fix24<R>(rho);
         if (any) maxrow = y;
@@ -168,8 +177,8 @@ __global__ void k_scan(SimDev d, int cur)
 // results agree bit for bit. FP32 (fast path): the same quantities, regrouped
 // (algebraically identical in exact arithmetic) for fewer instructions:
 //  * u* = (1 - mu) j / rho with one reciprocal;
-//  * Eq. 3 by opposite pairs: with p = 1 - 3/2 u*.u* + 9/2 (e.u*)^2 and
-//    q = 3 e.u*, the factor is p + q for e and p - q for -e;
+//  * Eq. 3 by opposite pairs: with p = 1 - 3/2 u*.u* + 9/2 (e.u*)^2, the
+//    factor is p + 3 e.u* for e and p - 3 e.u* for -e;
 //  * f_0 = rho - sum_{i>0} f_i, i.e. the BGK step's exact mass conservation
 //    (sum_i w_i (1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u) = 1), which keeps the
 //    rounding of the float weights from drifting the total mass;
@@ -183,18 +192,28 @@ template <typename R>
 __device__ __forceinline__ Consts<R> make_consts(const SimDev &d)
 {
     Consts<R> c;
-    c.omega = (R)d.omega;
-    c.cmu = (R)d.cmu;
-    c.om1 = (R)(1.0 - d.omega);
-    c.ow0 = (R)(d.omega * (4.0 / 9.0));
-    c.ow1 = (R)(d.omega * (1.0 / 9.0));
-    c.ow5 = (R)(d.omega * (1.0 / 36.0));
-    c.two_sigma = (R)(2.0 * d.sigma);
+    if constexpr (sizeof(R) == 8) {
+        c.omega = d.omega;
+        c.cmu = d.cmu;
+        c.om1 = 1.0 - d.omega;
+        c.ow0 = d.omega * (4.0 / 9.0);
+        c.ow1 = d.omega * (1.0 / 9.0);
+        c.ow5 = d.omega * (1.0 / 36.0);
+        c.two_sigma = 2.0 * d.sigma;
+    } else {
+        c.omega = d.f_omega;
+        c.cmu = d.f_cmu;
+        c.om1 = d.f_om1;
+        c.ow0 = d.f_ow0;
+        c.ow1 = d.f_ow1;
+        c.ow5 = d.f_ow5;
+        c.two_sigma = d.f_two_sigma;
+    }
     return c;
 }
 
 template <typename R>
-__device__ __forceinline__ void collide(const R *g, R rho, R *fo, const Consts<R> &c)
+__device__ __forceinline__ void collide(const R *g, R rho, R *fo, const Consts<R> &c, const R *eta)
 {
     const R jx = ((((g[1] - g[3]) + g[5]) - g[6]) - g[7]) + g[8];
     const R jy = ((((g[2] - g[4]) + g[5]) + g[6]) - g[7]) - g[8];
@@ -211,50 +230,49 @@ __device__ __forceinline__ void collide(const R *g, R rho, R *fo, const Consts<R
             const R fss = (wq<R>(i) * rho) * t1;    // Eq. 3, D2Q9
             fo[i] = g[i] - c.omega * (g[i] - fss); // Eq. 2
         }
+        if (eta) {
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) fo[i] = fo[i] + eta[i]; // Eq. 4
+        }
     } else {
-        const float k = c.cmu * __frcp_rn(rho);
+        float rr;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rr) : "f"(rho));
+        const float k = c.cmu * rr;
         const float usx = jx * k, usy = jy * k;
         const float A = fmaf(-1.5f, fmaf(usx, usx, usy * usy), 1.0f);
         const float r1 = c.ow1 * rho, r5 = c.ow5 * rho;
-        float e, p, q;
+        // every multiply-add is an explicit fmaf, so the rounding does not
+        // depend on the compiler's contraction choices; the noise rides in
+        // the innermost one
+        float e, p;
         e = usx;
         p = fmaf(4.5f * e, e, A);
-        q = 3.0f * e;
-        fo[1] = fmaf(c.om1, g[1], r1 * (p + q));
-        fo[3] = fmaf(c.om1, g[3], r1 * (p - q));
+        fo[1] = fmaf(c.om1, g[1], fmaf(r1, fmaf(3.0f, e, p), eta[1]));
+        fo[3] = fmaf(c.om1, g[3], fmaf(r1, fmaf(-3.0f, e, p), eta[3]));
         e = usy;
         p = fmaf(4.5f * e, e, A);
-        q = 3.0f * e;
-        fo[2] = fmaf(c.om1, g[2], r1 * (p + q));
-        fo[4] = fmaf(c.om1, g[4], r1 * (p - q));
+        fo[2] = fmaf(c.om1, g[2], fmaf(r1, fmaf(3.0f, e, p), eta[2]));
+        fo[4] = fmaf(c.om1, g[4], fmaf(r1, fmaf(-3.0f, e, p), eta[4]));
         e = usx + usy;
         p = fmaf(4.5f * e, e, A);
-        q = 3.0f * e;
-        fo[5] = fmaf(c.om1, g[5], r5 * (p + q));
-        fo[7] = fmaf(c.om1, g[7], r5 * (p - q));
+        fo[5] = fmaf(c.om1, g[5], fmaf(r5, fmaf(3.0f, e, p), eta[5]));
+        fo[7] = fmaf(c.om1, g[7], fmaf(r5, fmaf(-3.0f, e, p), eta[7]));
         e = usy - usx;
         p = fmaf(4.5f * e, e, A);
-        q = 3.0f * e;
-        fo[6] = fmaf(c.om1, g[6], r5 * (p + q));
-        fo[8] = fmaf(c.om1, g[8], r5 * (p - q));
-        // fo[0] is set by rest_from_mass() once the noise is added
-    }
-}
-
-// FP32: f_0 = rho - sum_{i>0} f_i. BGK (Eq. 2) and the noise (Eq. 4) both
-// conserve the node's mass exactly, so this is f_0 in exact arithmetic; in
-// floating point it keeps the rounding of constants from drifting the mass.
-template <typename R>
-__device__ __forceinline__ void rest_from_mass(R *fo, R rho)
-{
-    if constexpr (sizeof(R) == 4)
+        fo[6] = fmaf(c.om1, g[6], fmaf(r5, fmaf(3.0f, e, p), eta[6]));
+        fo[8] = fmaf(c.om1, g[8], fmaf(r5, fmaf(-3.0f, e, p), eta[8]));
+        // f_0 = rho - sum_{i>0} f_i: BGK (Eq. 2) and the noise (Eq. 4) both
+        // conserve the node's mass exactly, so this is f_0 in exact
+        // arithmetic, and it keeps the rounding of the float weights and of
+        // 1/9 from drifting the total mass
         fo[0] = rho - ((((fo[1] + fo[2]) + (fo[3] + fo[4])) + ((fo[5] + fo[6]) + (fo[7] + fo[8]))));
+    }
 }
 
 // Eq. 4: eta_i = 2 sigma (u_i - mean u), u_i uniform with 23 random bits from
 // the Philox blocks (n, t, 16, sim) and (n, t, 17, sim).
 template <typename R>
-__device__ __forceinline__ void add_noise(R *fo, uint32_t n, uint32_t t, const SimDev &d, const Consts<R> &c)
+__device__ __forceinline__ void noise_eta(R *eta, uint32_t n, uint32_t t, const SimDev &d, const Consts<R> &c)
 {
     const u32x4 a = philox4x32_10(u32x4{n, t, STREAM_NOISE + 0u, d.sim}, d.pk);
     const u32x4 b = philox4x32_10(u32x4{n, t, STREAM_NOISE + 1u, d.sim}, d.pk);
@@ -269,7 +287,7 @@ __device__ __forceinline__ void add_noise(R *fo, uint32_t n, uint32_t t, const S
         for (int i = 1; i < NQ; ++i) S = S + u[i];
         const double ubar = S / 9.0;
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) fo[i] = fo[i] + c.two_sigma * (u[i] - ubar);
+        for (int i = 0; i < NQ; ++i) eta[i] = c.two_sigma * (u[i] - ubar);
     } else {
         // 1 + m 2^-23 exactly; the constant offset cancels in u_i - mean u
         float v[NQ];
@@ -277,8 +295,61 @@ __device__ __forceinline__ void add_noise(R *fo, uint32_t n, uint32_t t, const S
         for (int i = 0; i < NQ; ++i) v[i] = __uint_as_float(0x3F800000u | m[i]);
         const float S = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
         const float nb = -c.two_sigma * (S * (1.0f / 9.0f));
+        eta[0] = 0.0f; // f_0 follows from mass conservation
 #pragma unroll
-        for (int i = 1; i < NQ; ++i) fo[i] = fo[i] + fmaf(c.two_sigma, v[i], nb);
+        for (int i = 1; i < NQ; ++i) eta[i] = fmaf(c.two_sigma, v[i], nb);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R fix_negative(R *fo, int mode);
+
+// One occupied node: Eq. 3 / Eq. 2 relaxation with (NOISE) the Eq. 4 noise,
+// before the negative-population fix.
+template <typename R, bool NOISE>
+__device__ __forceinline__ void relax_core(const R *g, R rho, R *fo, uint32_t n, uint32_t t, const SimDev &d,
+                                           const Consts<R> &c)
+{
+    R eta[NQ];
+    if constexpr (NOISE) {
+        noise_eta<R>(eta, n, t, d, c);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) eta[i] = R(0);
+    }
+    if constexpr (sizeof(R) == 8)
+        collide<R>(g, rho, fo, c, NOISE ? eta : nullptr);
+    else
+        collide<R>(g, rho, fo, c, eta);
+}
+
+// relax_core followed by the negative-population fix. Returns the mass the
+// fix added.
+template <typename R>
+__device__ __forceinline__ R relax_node(const R *g, R rho, R *fo, uint32_t n, uint32_t t, const SimDev &d,
+                                        const Consts<R> &c)
+{
+    if (d.noise_on)
+        relax_core<R, true>(g, rho, fo, n, t, d, c);
+    else
+        relax_core<R, false>(g, rho, fo, n, t, d, c);
+    return fix_negative<R>(fo, d.negfix);
+}
+
+// Mass of the stored populations of a node. FP64 (as the oracle): their sum
+// in index order. FP32: the node's density before the update plus what the
+// negative-population fix added, which is that sum in exact arithmetic (the
+// update and the reversal conserve mass).
+template <typename R>
+__device__ __forceinline__ R node_mass(const R *fo, R rho, R added)
+{
+    if constexpr (sizeof(R) == 8) {
+        R r = fo[0];
+#pragma unroll
+        for (int i = 1; i < NQ; ++i) r = r + fo[i];
+        return r;
+    } else {
+        return rho + added;
     }
 }
 
@@ -356,9 +427,8 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d, int cur, uint32_t t)
         }
     }
 
-    const R rho_c = (R)d.rho_c;
+    const R rho_c = rho_c_of<R>(d);
     const Consts<R> cf = make_consts<R>(d);
-    const bool noise = d.sigma != 0.0;
     const bool periodic = d.y_periodic != 0;
     const int ncx = (W + TPB - 1) / TPB;
     const int nrows = y_hi - y_r;
@@ -424,11 +494,10 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d, int cur, uint32_t t)
                 for (int i = 1; i < NQ; ++i) rho = rho + g[i];
                 const bool occ = colok && rho >= rho_c;
                 R fo[NQ];
+                R added = R(0);
                 if (occ) {
-                    collide<R>(g, rho, fo, cf);
-                    if (noise) add_noise<R>(fo, (uint32_t)(y * W + x), t, d, cf);
-                    rest_from_mass<R>(fo, rho);
-                    clip += fix_negative<R>(fo, d.negfix);
+                    added = relax_node<R>(g, rho, fo, (uint32_t)(y * W + x), t, d, cf);
+                    clip += added;
                 } else {
                     // rho < rho_c: reverse the directions (two-step bounce-back)
 #pragma unroll
@@ -443,9 +512,7 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d, int cur, uint32_t t)
                     for (int i = 0; i < NQ; ++i) o[i * P] = fo[i];
                     // populations are non-negative after every step, so the
                     // node holds mass iff their sum is non-zero
-                    R ro = fo[0];
-#pragma unroll
-                    for (int i = 1; i < NQ; ++i) ro = ro + fo[i];
+                    const R ro = node_mass<R>(fo, rho, added);
                     mass += fix24<R>(ro);
                     if (ro != R(0)) maxrow = y;
                 }
@@ -516,8 +583,8 @@ __device__ __forceinline__ bool accept(const SimDev &d, const R *f, int y_r, con
     const R rs = rho_star<R>(d, f, y_r, c.x, c.y);
     switch (d.growth_mode) {
     case GROW_BULK:
-    case GROW_BAND: return rs >= (R)d.rho_c;
-    case GROW_EDGE: return rs >= (R)d.rho_c && (d.heights[c.x] - c.y) <= d.edge_depth;
+    case GROW_BAND: return rs >= rho_c_of<R>(d);
+    case GROW_EDGE: return rs >= rho_c_of<R>(d) && (d.heights[c.x] - c.y) <= d.edge_depth;
     case GROW_DENSITY: return (double)rs > d.rho_c && u01(c.u) < 1.0 - (double)rs / d.rho0; // Eq. 5
     default: return false;
     }
@@ -551,6 +618,7 @@ constexpr int SEL_SMEM_WORDS = 4096;   // accept-bit words handled in shared mem
 constexpr size_t SEL_SMEM_BYTES =
     (size_t)SEL_SMEM_SLOTS * 8 + (size_t)SEL_SMEM_EVENTS * 8 + (size_t)SEL_SMEM_WORDS * 4;
 constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;
+constexpr int SEL_BATCH = 4; // independent memory accesses a selector thread keeps in flight
 
 struct EventTable {
     uint32_t *keys;
@@ -665,14 +733,27 @@ __global__ void __launch_bounds__(SEL_TPB) k_select(SimDev d, int cur, uint32_t 
         }
         __syncthreads();
         // (2) the first n_s accepted keys in draw order: one warp per word,
-        // one lane per candidate
-        for (long long w = warp; w < nw; w += SEL_TPB / 32) {
-            const uint32_t word = d.cflags[w];
-            if ((word >> lane) & 1u) {
-                const long long r = wpref[w] + __popc(word & ((1u << lane) - 1u));
-                if (r < ns) {
-                    kl[r] = d.ckeys[(w << 5) + lane];
-                    if (r == ns - 1) s_kstop = (w << 5) + lane + 1;
+        // one lane per candidate; each warp loads SEL_BATCH words and their
+        // keys before using any of them
+        const uint32_t *__restrict__ cfl = d.cflags;
+        const uint32_t *__restrict__ ckk = d.ckeys;
+        for (long long w0b = warp; w0b < nw; w0b += (long long)(SEL_TPB / 32) * SEL_BATCH) {
+            uint32_t word[SEL_BATCH], key[SEL_BATCH];
+#pragma unroll
+            for (int j = 0; j < SEL_BATCH; ++j) {
+                const long long w = w0b + (long long)j * (SEL_TPB / 32);
+                word[j] = w < nw ? cfl[w] : 0u;
+                key[j] = ((word[j] >> lane) & 1u) ? ckk[(w << 5) + lane] : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < SEL_BATCH; ++j) {
+                const long long w = w0b + (long long)j * (SEL_TPB / 32);
+                if ((word[j] >> lane) & 1u) {
+                    const long long r = wpref[w] + __popc(word[j] & ((1u << lane) - 1u));
+                    if (r < ns) {
+                        kl[r] = key[j];
+                        if (r == ns - 1) s_kstop = (w << 5) + lane + 1;
+                    }
                 }
             }
         }
@@ -703,26 +784,44 @@ __global__ void __launch_bounds__(SEL_TPB) k_select(SimDev d, int cur, uint32_t 
         }
     }
     __syncthreads();
-    // (3) inject count * rho_cell/2 into the two pre-stream slots of each (node, pair)
+    // (3) inject count * rho_cell/2 into the two pre-stream slots of each
+    // (node, pair). Distinct (node, pair) never share a slot (each slot streams
+    // into exactly one direction of one node), so a thread gathers all the
+    // slots of its batch before it stores any.
     const int nlist = s_nlist;
-    for (int e = tid; e < nlist; e += SEL_TPB) {
-        const int slot = tb.list[e];
-        const uint32_t key = tb.keys[slot];
-        const int cnt = (int)tb.cnt[slot];
-        const long long node = (long long)(key >> 2);
-        const int p = (int)(key & 3u);
-        const int y = (int)(node / d.W), x = (int)(node % d.W);
-        const R add = (R)((double)cnt * d.half_cell);
-        const long long sa = pull_slot(d, y_r, x, y, pair_a(p));
-        const long long sb = pull_slot(d, y_r, x, y, pair_b(p));
-        f[sa] = f[sa] + add;
-        f[sb] = f[sb] + add;
-        d.ev_node[e] = node;
-        d.ev_pair[e] = p;
-        d.ev_count[e] = cnt;
-        if (!small) {
-            tb.keys[slot] = EMPTY_KEY;
-            tb.cnt[slot] = 0u;
+    for (int e0 = tid; e0 < nlist; e0 += SEL_TPB * SEL_BATCH) {
+        long long sl[2 * SEL_BATCH];
+        R val[2 * SEL_BATCH], add[SEL_BATCH];
+#pragma unroll
+        for (int j = 0; j < SEL_BATCH; ++j) {
+            const int e = e0 + j * SEL_TPB;
+            if (e < nlist) {
+                const int slot = tb.list[e];
+                const uint32_t key = tb.keys[slot];
+                const int cnt = (int)tb.cnt[slot];
+                const long long node = (long long)(key >> 2);
+                const int p = (int)(key & 3u);
+                const int y = (int)(node / d.W), x = (int)(node % d.W);
+                add[j] = (R)((double)cnt * d.half_cell);
+                sl[2 * j] = pull_slot(d, y_r, x, y, pair_a(p));
+                sl[2 * j + 1] = pull_slot(d, y_r, x, y, pair_b(p));
+                val[2 * j] = f[sl[2 * j]];
+                val[2 * j + 1] = f[sl[2 * j + 1]];
+                d.ev_node[e] = node;
+                d.ev_pair[e] = p;
+                d.ev_count[e] = cnt;
+                if (!small) {
+                    tb.keys[slot] = EMPTY_KEY;
+                    tb.cnt[slot] = 0u;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < SEL_BATCH; ++j) {
+            if (e0 + j * SEL_TPB < nlist) {
+                f[sl[2 * j]] = val[2 * j] + add[j];
+                f[sl[2 * j + 1]] = val[2 * j + 1] + add[j];
+            }
         }
     }
     if (tid == 0) {

@@ -31,6 +31,8 @@ LBM_OK = 0
 STATUS_FRONT_AT_TOP = 1
 STATUS_GROWTH_STARVED = 2
 STATUS_CAPACITY = 4
+STATUS_TIMEOUT = 8
+UPDATE_KERNELS = {"auto": 0, "plain": 1, "tma": 2, "tma1": 3}
 
 
 class LbmError(RuntimeError):
@@ -51,7 +53,7 @@ class lbm_params_t(ctypes.Structure):
         ("front_kind", ctypes.c_int32), ("front_kmin", ctypes.c_int32),
         ("front_kmax", ctypes.c_int32), ("wall_mode", ctypes.c_int32),
         ("negfix_mode", ctypes.c_int32), ("y_periodic", ctypes.c_int32),
-        ("sim_id", ctypes.c_uint32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("sim_id", ctypes.c_uint32), ("precision", ctypes.c_int32), ("update_kernel", ctypes.c_int32),
     ]
 
 
@@ -67,7 +69,7 @@ class lbm_stats_t(ctypes.Structure):
         ("carry", ctypes.c_double), ("hbar", ctypes.c_double), ("w", ctypes.c_double),
         ("clip_mass", ctypes.c_double),
         ("y_r", ctypes.c_int32), ("H_top", ctypes.c_int32), ("hmin", ctypes.c_int32),
-        ("y_hi", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("y_hi", ctypes.c_int32), ("status", ctypes.c_int32), ("update_kernel", ctypes.c_int32),
     ]
 
 
@@ -133,13 +135,13 @@ def _check(rc: int, what: str):
         raise LbmError(f"{what}: {msg} [{rc}]")
 
 
-def make_params(d: dict, precision: str = "fp32") -> lbm_params_t:
+def make_params(d: dict, precision: str = "fp32", update_kernel: str = "auto") -> lbm_params_t:
     p = lbm_params_t()
     for name, _ in lbm_params_t._fields_:
         if name == "precision":
             v = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        elif name == "reserved":
-            v = 0
+        elif name == "update_kernel":
+            v = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
         else:
             v = d[name]
             if name == "growth_mode" and isinstance(v, str):
@@ -169,7 +171,8 @@ def lbm_footprint(params: dict, precision: str = "fp32") -> int:
 class Simulation:
     """One resident simulation (``lbm_create`` ... ``lbm_destroy``)."""
 
-    def __init__(self, params: dict, precision: str = "fp32", device=None, stream=None):
+    def __init__(self, params: dict, precision: str = "fp32", device=None, stream=None,
+                 update_kernel: str = "auto"):
         import torch
         lib = load_library()
         if not torch.cuda.is_available():
@@ -179,7 +182,7 @@ class Simulation:
         self.W = int(params["width"])
         self.H = int(params["height"])
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
-        self._p = make_params(params, precision)
+        self._p = make_params(params, precision, update_kernel)
         nbytes = lbm_footprint(params, precision)
         with torch.cuda.device(self.device):
             self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
@@ -282,7 +285,7 @@ class Simulation:
     def lbm_stats(self) -> dict:
         s = lbm_stats_t()
         _check(self._lib.lbm_stats(self._h, ctypes.byref(s)), "lbm_stats")
-        return {name: getattr(s, name) for name, _ in lbm_stats_t._fields_ if name != "reserved"}
+        return {name: getattr(s, name) for name, _ in lbm_stats_t._fields_}
 
     stats = lbm_stats
 
