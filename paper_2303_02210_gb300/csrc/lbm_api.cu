@@ -49,7 +49,7 @@ struct Layout {
     long long P, kc_max;
     int elem;
     uint64_t off_f0, off_f1, off_mask, off_heights, off_rows0, off_sc, off_cflags, off_ckeys, off_gkl, off_gwpref,
-        off_hkeys, off_hcnt, off_hlist, off_evn, off_evp, off_evc, total;
+        off_hkeys, off_hcnt, off_hlist, off_evk, off_evc, off_rown, off_rk, off_roff, off_radd, total;
 };
 
 Layout make_layout(const lbm_params_t &p)
@@ -87,9 +87,12 @@ Layout make_layout(const lbm_params_t &p)
     L.off_hkeys = o; o = align256(o + (uint64_t)L.hcap * 4u);
     L.off_hcnt = o; o = align256(o + (uint64_t)L.hcap * 4u);
     L.off_hlist = o; o = align256(o + (uint64_t)L.ns_max * 4u);
-    L.off_evn = o; o = align256(o + (uint64_t)L.ns_max * 8u);
-    L.off_evp = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    L.off_evk = o; o = align256(o + (uint64_t)L.ns_max * 4u);
     L.off_evc = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    L.off_rown = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    L.off_rk = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    L.off_roff = o; o = align256(o + (uint64_t)L.ns_max * 8u);
+    L.off_radd = o; o = align256(o + (uint64_t)L.ns_max * 4u);
     L.total = o;
     return L;
 }
@@ -214,7 +217,7 @@ int lbm_validate(const lbm_params_t *p)
     if (p->negfix_mode != LBM_NEGFIX_LITERAL && p->negfix_mode != LBM_NEGFIX_RESCALE) return LBM_ERR_INVALID_ARG;
     if (p->precision != LBM_FP32 && p->precision != LBM_FP64) return LBM_ERR_INVALID_ARG;
     if (p->y_periodic != 0 && p->y_periodic != 1) return LBM_ERR_INVALID_ARG;
-    if (p->update_kernel < 0 || p->update_kernel > 3) return LBM_ERR_INVALID_ARG;
+    if (p->update_kernel < 0 || p->update_kernel > 4) return LBM_ERR_INVALID_ARG;
     if (p->update_kernel >= 2 && (p->precision != LBM_FP32 || p->y_periodic)) return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
@@ -292,9 +295,12 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     d.hkeys = (uint32_t *)(base + L.off_hkeys);
     d.hcnt = (uint32_t *)(base + L.off_hcnt);
     d.hlist = (int32_t *)(base + L.off_hlist);
-    d.ev_node = (long long *)(base + L.off_evn);
-    d.ev_pair = (int32_t *)(base + L.off_evp);
+    d.ev_key = (uint32_t *)(base + L.off_evk);
     d.ev_count = (int32_t *)(base + L.off_evc);
+    d.rec_owner = (int *)(base + L.off_rown);
+    d.rec_k = (int *)(base + L.off_rk);
+    d.rec_off = (int *)(base + L.off_roff);
+    d.rec_add = (float *)(base + L.off_radd);
     d.W = p->width;
     d.H = p->height;
     d.Wp = L.Wp;
@@ -344,11 +350,20 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     s->use_tma = false;
     s->tma_grid = nsm;
     s->tma_variant = p->update_kernel == 3 ? 1 : 0;
+    const bool tma_inject = p->update_kernel != 4; // 4: the selector injects into global memory
     if (p->precision == LBM_FP32 && !p->y_periodic && p->update_kernel != 1) {
         bool ok = true;
         for (int b = 0; b < 2 && ok; ++b)
             ok = encode_population_map(&s->maps[b], d.f[b], d.W, d.H, d.Wp, d.P, kTmaBoxX + 8, kTmaBoxY + 2);
         s->use_tma = ok;
+        d.inject_in_update = ok && tma_inject ? 1 : 0;
+        d.upd_ctas = launch_update_tma_ctas(nsm, s->tma_variant);
+        d.upd_magic = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d.upd_ctas - 1) / (uint64_t)d.upd_ctas);
+        if (d.upd_ctas > kTmaMaxCtas || (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) *
+                                                ((p->height + kTmaBoxY - 1) / kTmaBoxY) >= (1LL << 22)) {
+            s->use_tma = false;
+            d.inject_in_update = 0;
+        }
         if (!ok && p->update_kernel >= 2) {
             if (s->own_arena) cudaFree(s->arena);
             delete s;
@@ -595,12 +610,17 @@ int lbm_last_events(lbm_sim *s, int64_t *node, int32_t *pair, int32_t *count, in
     *n = ne;
     if (ne == 0 || cap == 0) return LBM_OK;
     if (!node || !pair || !count) return LBM_ERR_INVALID_ARG;
-    std::vector<long long> vn(ne);
-    std::vector<int32_t> vp(ne), vc(ne);
-    CK(cudaMemcpyAsync(vn.data(), s->d.ev_node, ne * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(vp.data(), s->d.ev_pair, ne * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    std::vector<uint32_t> vk(ne);
+    std::vector<int32_t> vc(ne);
+    CK(cudaMemcpyAsync(vk.data(), s->d.ev_key, ne * sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(vc.data(), s->d.ev_count, ne * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    std::vector<long long> vn(ne);
+    std::vector<int32_t> vp(ne);
+    for (int i = 0; i < ne; ++i) {
+        vn[i] = (long long)key_y(vk[i]) * s->p.width + key_x(vk[i]);
+        vp[i] = key_pair(vk[i]);
+    }
     std::vector<int> ord(ne);
     for (int i = 0; i < ne; ++i) ord[i] = i;
     std::sort(ord.begin(), ord.end(), [&](int a, int b) {

@@ -31,6 +31,17 @@ enum GrowthMode { GROW_NONE = 0, GROW_BULK = 1, GROW_DENSITY = 2, GROW_EDGE = 3,
 enum { STREAM_PROLIF = 1u, STREAM_INIT = 2u, STREAM_NOISE = 16u };
 enum { ST_FRONT_AT_TOP = 1, ST_STARVED = 2, ST_CAPACITY = 4, ST_TIMEOUT = 8 };
 
+// A division site (node (x, y), opposite pair p) packed into 32 bits:
+// y << 17 | x << 2 | p (W, H <= 32768 and W H < 2^30 keep every key below
+// 0xFFFFFFFF, the empty marker of the merge tables).
+__host__ __device__ __forceinline__ uint32_t pack_key(int x, int y, int p)
+{
+    return ((uint32_t)y << 17) | ((uint32_t)x << 2) | (uint32_t)p;
+}
+__host__ __device__ __forceinline__ int key_x(uint32_t k) { return (int)((k >> 2) & 0x7FFFu); }
+__host__ __device__ __forceinline__ int key_y(uint32_t k) { return (int)(k >> 17); }
+__host__ __device__ __forceinline__ int key_pair(uint32_t k) { return (int)(k & 3u); }
+
 // Fixed-point unit of the exact mass sums: 2^-24 per count.
 constexpr double kFixScale = 16777216.0;
 constexpr double kFixInv = 5.9604644775390625e-08;
@@ -123,8 +134,8 @@ struct SimDev {
     uint32_t *hkeys;     // open-addressing table for large n_s, key = node*4 + pair
     uint32_t *hcnt;
     int32_t *hlist;      // slots in insertion order
-    long long *ev_node;  // exported events of the latest step
-    int32_t *ev_pair, *ev_count;
+    uint32_t *ev_key;    // divisions of the latest step: packed (node, pair) keys
+    int32_t *ev_count;   // and how often each was drawn
     int32_t *rows0;      // initial occupied rows per column
     int W, H, Wp, MW;
     long long P;         // plane stride in elements (Wp * H)
@@ -137,6 +148,13 @@ struct SimDev {
     PhiloxKey pk;        // round keys of (key0, key1)
     int growth_mode, edge_depth, band_rows, wall_mode, negfix, y_periodic;
     int noise_on;        // sigma != 0
+    int inject_in_update; // the selector only lists the divisions; the update kernel adds them
+    int upd_ctas;         // CTAs of the TMA-staged update kernel (tiles dealt round-robin)
+    uint32_t upd_magic;   // ceil(2^32 / upd_ctas): tile / upd_ctas = umulhi(tile, magic)
+    int *rec_owner;       // per division (selector order): owning CTA of its tile,
+    int *rec_k;           // the tile's index among that CTA's tiles,
+    int *rec_off;         // the two pre-stream slots' offsets in the staged box,
+    float *rec_add;       // and count * rho_cell / 2
     // the same constants rounded to float once on the host, so that no kernel
     // evaluates double arithmetic per node (the FP64 pipe is narrow)
     float f_rho_c, f_omega, f_cmu, f_om1, f_ow0, f_ow1, f_ow5, f_two_sigma;
@@ -165,6 +183,9 @@ extern const KernelTable kTableF64;
 // (box (128 + 8) x (8 + 2) x 9).
 cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
                                   int variant, cudaStream_t s);
+// CTAs the TMA-staged update kernel runs on this many SMs.
+int launch_update_tma_ctas(int nsm, int variant);
 constexpr int kTmaBoxX = 128, kTmaBoxY = 8;
+constexpr int kTmaMaxCtas = 1024; // the reciprocal above is exact for tile < 2^22
 
 } // namespace lbm

@@ -12,4 +12,6 @@ cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CU
 {
     return launch_update_tma(d, cur, t, maps, nsm, variant, s);
 }
+
+int launch_update_tma_ctas(int nsm, int variant) { return (variant == 1 ? 3 : 2) * nsm; }
 } // namespace lbm

@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(CAND_TPB) k_cand(SimDev d, int cur, uint32_t t
         const bool ok = accept<R>(d, f, y_r, c);
         const unsigned b = __ballot_sync(0xffffffffu, ok);
         if ((threadIdx.x & 31) == 0) d.cflags[k >> 5] = b;
-        d.ckeys[k] = (uint32_t)(((long long)c.y * d.W + c.x) * 4 + c.pair);
+        d.ckeys[k] = pack_key(c.x, c.y, c.pair);
     }
 }
 
@@ -627,22 +627,32 @@ struct EventTable {
     unsigned mask; // slots - 1
 };
 
-__device__ __forceinline__ void table_insert(const EventTable &tb, uint32_t key, int *nlist)
+// Counts one draw of `key`; returns the slot if the key is new, else -1.
+__device__ __forceinline__ int table_insert(const EventTable &tb, uint32_t key)
 {
     unsigned slot = (unsigned)(((unsigned long long)key * 0x9E3779B97F4A7C15ull) >> 32) & tb.mask;
     for (unsigned probe = 0; probe <= tb.mask; ++probe) {
         const uint32_t old = atomicCAS(&tb.keys[slot], EMPTY_KEY, key);
-        if (old == EMPTY_KEY) {
+        if (old == EMPTY_KEY || old == key) {
             atomicAdd(&tb.cnt[slot], 1u);
-            tb.list[atomicAdd(nlist, 1)] = (int)slot;
-            return;
-        }
-        if (old == key) {
-            atomicAdd(&tb.cnt[slot], 1u);
-            return;
+            return old == EMPTY_KEY ? (int)slot : -1;
         }
         slot = (slot + 1u) & tb.mask;
     }
+    return -1;
+}
+
+// Appends the new slots of a warp to the table's list with one atomic per
+// warp. Every lane of the warp calls it (newslot < 0: nothing to append).
+__device__ __forceinline__ void table_append(const EventTable &tb, int newslot, int *nlist)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, newslot >= 0);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(nlist, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (newslot >= 0) tb.list[base + __popc(m & ((1u << lane) - 1u))] = newslot;
 }
 
 // exclusive block scan of one int per thread; returns the prefix, *total the sum
@@ -673,6 +683,35 @@ __device__ __forceinline__ long long block_exscan(long long v, long long *total,
     *total = s_w[32];
     __syncthreads();
     return r;
+}
+
+// For the TMA-staged update: where division e goes. Its node's tile (of
+// kTmaBoxX x kTmaBoxY nodes of the active window; tiles are dealt
+// round-robin over upd_ctas CTAs), that tile's index among the owner's tiles,
+// and the offsets of the two pre-stream slots in the tile's staged box
+// ((kTmaBoxX + 8) x (kTmaBoxY + 2) x 9 with the tile at column 4, row 1):
+// the source (x - ex_q, y - ey_q) unwrapped in x, or across a wall the
+// node's own population opp(q).
+template <typename R>
+__device__ __forceinline__ void division_record(const SimDev &d, int e, uint32_t key, int cnt, int y_r)
+{
+    constexpr int LX = kTmaBoxX + 8, PL = (kTmaBoxY + 2) * LX;
+    const int x = key_x(key), y = key_y(key), p = key_pair(key);
+    const int ncx = (d.W + kTmaBoxX - 1) / kTmaBoxX;
+    const int ty = (y - y_r) / kTmaBoxY, tx = x / kTmaBoxX;
+    const uint32_t tile = (uint32_t)(ty * ncx + tx);
+    const uint32_t q = __umulhi(tile, d.upd_magic);
+    const int x0 = tx * kTmaBoxX, y0 = y_r + ty * kTmaBoxY;
+    d.rec_owner[e] = (int)(tile - q * (uint32_t)d.upd_ctas);
+    d.rec_k[e] = (int)q;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int qd = h == 0 ? pair_a(p) : pair_b(p);
+        const int ys = y - ey(qd);
+        d.rec_off[2 * e + h] = (ys < y_r || ys >= d.H) ? opp(qd) * PL + (y - y0 + 1) * LX + (x - x0 + 4)
+                                                       : qd * PL + (ys - y0 + 1) * LX + (x - ex(qd) - x0 + 4);
+    }
+    d.rec_add[e] = (float)((double)cnt * d.half_cell);
 }
 
 template <typename R>
@@ -761,7 +800,10 @@ __global__ void __launch_bounds__(SEL_TPB) k_select(SimDev d, int cur, uint32_t 
         __syncthreads();
         // (3) merge repeated (node, pair) draws
         const long long nins = total < ns ? total : ns;
-        for (long long r = tid; r < nins; r += SEL_TPB) table_insert(tb, kl[r], &s_nlist);
+        for (long long r0 = 0; r0 < nins; r0 += SEL_TPB) {
+            const long long r = r0 + tid;
+            table_append(tb, r < nins ? table_insert(tb, kl[r]) : -1, &s_nlist);
+        }
         __syncthreads();
         // (4) more draws if the parallel pass accepted fewer than n_s
         for (long long base = kc; s_acc < ns && base < cap; base += SEL_TPB) {
@@ -774,10 +816,12 @@ __global__ void __launch_bounds__(SEL_TPB) k_select(SimDev d, int cur, uint32_t 
             }
             long long tot;
             const long long r = s_acc + block_exscan(ok ? 1 : 0, &tot, s_w);
+            int ins = -1;
             if (ok && r < ns) {
-                table_insert(tb, (uint32_t)(((long long)c.y * d.W + c.x) * 4 + c.pair), &s_nlist);
+                ins = table_insert(tb, pack_key(c.x, c.y, c.pair));
                 if (r == ns - 1) s_kstop = k + 1;
             }
+            table_append(tb, ins, &s_nlist);
             __syncthreads();
             if (tid == 0) s_acc += tot;
             __syncthreads();
@@ -785,9 +829,10 @@ __global__ void __launch_bounds__(SEL_TPB) k_select(SimDev d, int cur, uint32_t 
     }
     __syncthreads();
     // (3) inject count * rho_cell/2 into the two pre-stream slots of each
-    // (node, pair). Distinct (node, pair) never share a slot (each slot streams
-    // into exactly one direction of one node), so a thread gathers all the
-    // slots of its batch before it stores any.
+    // (node, pair), or leave that to the update kernel (the TMA-staged one adds
+    // them to its staged tiles). Distinct (node, pair) never share a slot (each
+    // slot streams into exactly one direction of one node), so a thread gathers
+    // all the slots of its batch before it stores any.
     const int nlist = s_nlist;
     for (int e0 = tid; e0 < nlist; e0 += SEL_TPB * SEL_BATCH) {
         long long sl[2 * SEL_BATCH];
@@ -799,28 +844,30 @@ __global__ void __launch_bounds__(SEL_TPB) k_select(SimDev d, int cur, uint32_t 
                 const int slot = tb.list[e];
                 const uint32_t key = tb.keys[slot];
                 const int cnt = (int)tb.cnt[slot];
-                const long long node = (long long)(key >> 2);
-                const int p = (int)(key & 3u);
-                const int y = (int)(node / d.W), x = (int)(node % d.W);
-                add[j] = (R)((double)cnt * d.half_cell);
-                sl[2 * j] = pull_slot(d, y_r, x, y, pair_a(p));
-                sl[2 * j + 1] = pull_slot(d, y_r, x, y, pair_b(p));
-                val[2 * j] = f[sl[2 * j]];
-                val[2 * j + 1] = f[sl[2 * j + 1]];
-                d.ev_node[e] = node;
-                d.ev_pair[e] = p;
+                if (!d.inject_in_update) {
+                    const int x = key_x(key), y = key_y(key), p = key_pair(key);
+                    add[j] = (R)((double)cnt * d.half_cell);
+                    sl[2 * j] = pull_slot(d, y_r, x, y, pair_a(p));
+                    sl[2 * j + 1] = pull_slot(d, y_r, x, y, pair_b(p));
+                    val[2 * j] = f[sl[2 * j]];
+                    val[2 * j + 1] = f[sl[2 * j + 1]];
+                }
+                d.ev_key[e] = key;
                 d.ev_count[e] = cnt;
+                if (d.inject_in_update) division_record<R>(d, e, key, cnt, y_r);
                 if (!small) {
                     tb.keys[slot] = EMPTY_KEY;
                     tb.cnt[slot] = 0u;
                 }
             }
         }
+        if (!d.inject_in_update) {
 #pragma unroll
-        for (int j = 0; j < SEL_BATCH; ++j) {
-            if (e0 + j * SEL_TPB < nlist) {
-                f[sl[2 * j]] = val[2 * j] + add[j];
-                f[sl[2 * j + 1]] = val[2 * j + 1] + add[j];
+            for (int j = 0; j < SEL_BATCH; ++j) {
+                if (e0 + j * SEL_TPB < nlist) {
+                    f[sl[2 * j]] = val[2 * j] + add[j];
+                    f[sl[2 * j + 1]] = val[2 * j + 1] + add[j];
+                }
             }
         }
     }

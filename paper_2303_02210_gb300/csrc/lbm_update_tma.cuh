@@ -32,13 +32,20 @@ constexpr int TMA_LY = TMA_TY + 2;
 constexpr int TMA_IN_FLOATS = 9 * TMA_LY * TMA_LX;             // one box
 constexpr int TMA_IN_STRIDE = (TMA_IN_FLOATS + 31) / 32 * 32;   // stage pitch, 128-byte multiple
 constexpr uint32_t TMA_IN_BYTES = (uint32_t)TMA_IN_FLOATS * 4u; // bytes one box copy delivers
+// Slot additions (two per division) a CTA keeps in shared memory for its
+// staged tiles (more are read from global memory per tile); tiles flagged
+// per CTA.
+constexpr int TMA_EV_CAP = 1024;
+constexpr int TMA_KFLAG_WORDS = 32;
 template <int STAGES>
-constexpr size_t tma_smem_bytes() { return (size_t)STAGES * TMA_IN_STRIDE * 4 + 8 * STAGES + 128; }
+constexpr size_t tma_smem_bytes()
+{
+    return (size_t)STAGES * TMA_IN_STRIDE * 4 + 8 * STAGES + (size_t)TMA_EV_CAP * 12 + TMA_KFLAG_WORDS * 4 + 128;
+}
 // a stalled copy is given up after about two seconds at 2 GHz
 constexpr long long TMA_WAIT_BUDGET = 4000000000ll;
 static_assert(((TMA_IN_STRIDE * 4) % 128) == 0 && ((TMA_LX * 4) % 16) == 0, "smem alignment");
-static_assert(3 * (tma_smem_bytes<1>() + 1024) <= 228 * 1024 && 2 * (tma_smem_bytes<2>() + 1024) <= 228 * 1024,
-              "CTAs per SM by shared memory");
+static_assert(2 * (tma_smem_bytes<2>() + 1024) <= 227 * 1024, "two CTAs per SM by shared memory");
 
 constexpr int PLANE = TMA_LY * TMA_LX; // floats per staged plane
 
@@ -79,7 +86,12 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *s_in = (float *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint64_t *full = (uint64_t *)(s_in + STAGES * TMA_IN_STRIDE);
-    __shared__ int s_abort;
+    // divisions of this CTA's tiles: local tile index, two staged offsets, amount
+    int *ev_k = (int *)(full + STAGES);
+    int *ev_off = ev_k + TMA_EV_CAP / 2;
+    float *ev_add = (float *)(ev_off + TMA_EV_CAP);
+    unsigned *kflag = (unsigned *)(ev_add + TMA_EV_CAP); // tiles with divisions
+    __shared__ int s_abort, s_nev;
 
     const float *__restrict__ fin = (const float *)d.f[cur];
     float *__restrict__ fout = (float *)d.f[cur ^ 1];
@@ -109,10 +121,12 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
 
     if (tid == 0) {
         s_abort = 0;
+        s_nev = 0;
         prefetch_tensormap(&tm_in);
         for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
         fence_mbar_init();
     }
+    if (tid < TMA_KFLAG_WORDS) kflag[tid] = 0u;
     __syncthreads();
     int itx = (int)blockIdx.x % ncx, ity = (int)blockIdx.x / ncx; // next tile to load (thread 0)
     auto issue = [&](int k) {
@@ -126,8 +140,41 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
             ++ity;
         }
     };
+    // the first tiles' copies run while the divisions are sorted out below
     if (tid == 0)
         for (int k = 0; k < STAGES && k < count; ++k) issue(k);
+
+    // App. A step 3 for this CTA: the selector listed, per division, the CTA
+    // that owns its node's tile, the tile's local index, the offsets of the
+    // two pre-stream slots in the staged box and the amount; keep ours.
+    const int nev_all = d.inject_in_update ? d.sc->n_events : 0;
+    constexpr int EV_BATCH = 16; // owner words a thread loads before it looks at any
+    for (int eb = 0; eb < nev_all; eb += TMA_NT * EV_BATCH) {
+        int own[EV_BATCH];
+#pragma unroll
+        for (int j = 0; j < EV_BATCH; ++j) {
+            const int e = eb + j * TMA_NT + tid;
+            own[j] = e < nev_all ? d.rec_owner[e] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < EV_BATCH; ++j) {
+            const int e = eb + j * TMA_NT + tid;
+            if (own[j] == (int)blockIdx.x) {
+                const int at = atomicAdd(&s_nev, 1);
+                const int k = d.rec_k[e];
+                if (at < TMA_EV_CAP / 2) {
+                    ev_k[at] = k;
+                    ev_off[2 * at] = d.rec_off[2 * e];
+                    ev_off[2 * at + 1] = d.rec_off[2 * e + 1];
+                    ev_add[at] = d.rec_add[e];
+                }
+                if (k < 32 * TMA_KFLAG_WORDS) atomicOr(&kflag[k >> 5], 1u << (k & 31));
+            }
+        }
+    }
+    __syncthreads();
+    const int nev = s_nev;                            // divisions of this CTA
+    const bool ev_overflow = nev > TMA_EV_CAP / 2;    // then scan the global list per tile
 
     const Consts<float> cf = make_consts<float>(d);
     const float rho_c = d.f_rho_c;
@@ -164,6 +211,25 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
                 if (right) sp[(W - x0) + 4] = pr;
                 fence_proxy_async_smem(); // before the next bulk copy overwrites them
             }
+            __syncthreads();
+        }
+        // divisions of this tile, added to the staged pre-stream slots
+        const bool has_ev = nev > 0 && (ev_overflow || k >= 32 * TMA_KFLAG_WORDS || ((kflag[k >> 5] >> (k & 31)) & 1u));
+        if (has_ev) { // uniform across the CTA
+            if (!ev_overflow) {
+                for (int i = tid; i < nev; i += TMA_NT)
+                    if (ev_k[i] == k) {
+                        stage[ev_off[2 * i]] += ev_add[i];
+                        stage[ev_off[2 * i + 1]] += ev_add[i];
+                    }
+            } else {
+                for (int e = tid; e < nev_all; e += TMA_NT)
+                    if (d.rec_owner[e] == (int)blockIdx.x && d.rec_k[e] == k) {
+                        stage[d.rec_off[2 * e]] += d.rec_add[e];
+                        stage[d.rec_off[2 * e + 1]] += d.rec_add[e];
+                    }
+            }
+            fence_proxy_async_smem();
             __syncthreads();
         }
         if (s_abort) break;
