@@ -423,6 +423,21 @@ def test_sinusoidal_initial_front():
     assert spec[3:].max() < 0.05 * spec[1:3].max()
 
 
+def test_initial_density_jitter_is_uniform():
+    """App. A: the initial density is uniform on [0.9, 1.1] rho_init below the
+    front, zero above; u = 0 so f = w_i rho."""
+    from scipy import stats as sst
+    p = wl.paper_params(width=64, height=64, front_row=40.0, front_amp=0.0, seed=21)
+    s = OracleSim(p)
+    f = s.pops()
+    rho = f.sum(0)
+    tissue = rho[:40].ravel()
+    assert np.all(rho[40:] == 0.0)
+    assert tissue.min() >= 0.09 and tissue.max() <= 0.11
+    assert sst.kstest((tissue - 0.09) / 0.02, "uniform").pvalue > 1e-3
+    assert np.allclose(f[:, :40, :], WQ[:, None, None] * rho[None, :40, :], rtol=1e-15, atol=0)
+
+
 def test_rear_wall_advances_and_freezes_rows():
     """App. A: the rear wall is kept at least max(gap, 10 w) behind hbar; the
     rows behind it are quiescent (unchanged), and active + quiescent mass is
