@@ -204,6 +204,30 @@ const char *lbm_last_cuda_error(void);
 /* Library version string, e.g. "0.1.0 sm_103a". */
 const char *lbm_version(void);
 
+/* ---- allocation-free variant (the paper has no counterpart) ----
+ * Front heights h(x) = 1 + highest set row of column x (0 if none) of a
+ * caller's occupancy bitmask, plus the mean height and the interface width,
+ * the same reduction lbm_step runs after every update, but without allocating
+ * anything. For callers that cannot allocate device memory: a thread that is
+ * capturing a CUDA graph, an application whose device memory is all held by
+ * another allocator, or a loop that must never stall on the allocator.
+ *  mask_dev    device, read: H rows of (W + 31) / 32 uint32 words; bit (x & 31)
+ *              of word (x >> 5) of row y is node (x, y).
+ *  heights_dev device, written: W int32.
+ *  stats_dev   device, written: two doubles, hbar = sum h / W and
+ *              w = sqrt(W sum h^2 - (sum h)^2) / W.
+ *  stream      cudaStream_t the work is enqueued on (NULL = legacy default).
+ * Its scratch is a fixed device array inside this library, sized for widths up
+ * to LBM_NOALLOC_MAX_WIDTH; larger widths (or heights above 32768) return
+ * LBM_ERR_INVALID_ARG. Every GPU that loads the library keeps that array until
+ * the process exits. The first call on each device looks up the array's device
+ * address with that device current, so make it before capturing any stream on
+ * that device. All calls share the array: calls whose kernels overlap on a GPU
+ * race and must be serialised (one stream, or events). Enqueues only. */
+#define LBM_NOALLOC_MAX_WIDTH 32768
+int lbm_front_heights_noalloc(const uint32_t *mask_dev, int32_t width, int32_t height, int32_t *heights_dev,
+                              double *stats_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

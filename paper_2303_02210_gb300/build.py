@@ -1,12 +1,13 @@
 """Builds the CUDA library ``liblbm_gb300.so`` in-tree for sm_103a (GB300).
 
-Three translation units compile in parallel and link into one shared library
+Four translation units compile in parallel and link into one shared library
 with the C ABI of ``include/lbm.h``:
 
 * ``lbm_fp32.cu``: FP32 kernels (fast path, FMA contraction allowed);
 * ``lbm_fp64.cu``: FP64 kernels with ``-fmad=false`` (debug path, rounds like
   the FP64 CPU oracle);
-* ``lbm_api.cu``: the C ABI, host code built with ``-ffp-contract=off``.
+* ``lbm_api.cu``: the C ABI, host code built with ``-ffp-contract=off``;
+* ``lbm_noalloc.cu``: the allocation-free front-height entry point.
 
 Run ``python -m paper_2303_02210_gb300.build`` or call ``build()``.
 """
@@ -25,6 +26,7 @@ UNITS = {
     "lbm_fp32": [],
     "lbm_fp64": ["-fmad=false"],
     "lbm_api": [],
+    "lbm_noalloc": [],
 }
 
 

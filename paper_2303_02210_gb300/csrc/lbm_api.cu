@@ -172,6 +172,8 @@ bool encode_population_map(CUtensorMap *m, void *base, int W, int H, int Wp, lon
 
 } // namespace
 
+int lbm::lbm_record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
 struct lbm_sim {
     lbm_params_t p;
     int device;

@@ -185,6 +185,9 @@ cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CU
                                   int variant, cudaStream_t s);
 // CTAs the TMA-staged update kernel runs on this many SMs.
 int launch_update_tma_ctas(int nsm, int variant);
+
+// Records a CUDA error for lbm_last_cuda_error and maps it to an LBM_ERR_* code.
+int lbm_record_cuda_error(cudaError_t e);
 constexpr int kTmaBoxX = 128, kTmaBoxY = 8;
 constexpr int kTmaMaxCtas = 1024; // the reciprocal above is exact for tile < 2^22
 

@@ -97,6 +97,7 @@ _SIGNATURES = {
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_last_cuda_error": (ctypes.c_char_p, []),
     "lbm_version": (ctypes.c_char_p, []),
+    "lbm_front_heights_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
 }
 
 _lib = None
@@ -166,6 +167,19 @@ def lbm_footprint(params: dict, precision: str = "fp32") -> int:
     out = ctypes.c_uint64()
     _check(load_library().lbm_footprint(ctypes.byref(p), ctypes.byref(out)), "lbm_footprint")
     return int(out.value)
+
+
+def lbm_front_heights_noalloc(mask_dev, width: int, height: int, heights_dev, stats_dev, stream=None):
+    """Allocation-free front heights and width of a device occupancy bitmask
+    (``include/lbm.h``). ``mask_dev`` (uint32, H x ceil(W/32)), ``heights_dev``
+    (int32, W) and ``stats_dev`` (float64, 2) are torch CUDA tensors owned by
+    the caller; nothing is allocated. Enqueued on ``stream`` (default: the
+    current torch stream)."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    _check(load_library().lbm_front_heights_noalloc(
+        ctypes.c_void_p(mask_dev.data_ptr()), int(width), int(height), ctypes.c_void_p(heights_dev.data_ptr()),
+        ctypes.c_void_p(stats_dev.data_ptr()), ctypes.c_void_p(s.cuda_stream)), "lbm_front_heights_noalloc")
 
 
 class Simulation:
