@@ -457,20 +457,23 @@ static void one_step(orc_sim *s)
                     fo[i] = fs[i] - omega * (fs[i] - fss);
                 }
                 /* step 6: mass-conserving noise (Eq. 4). Nine uniforms u_i on (0,1)
-                 * with 23 random bits each (two Philox blocks: the top 23 bits of
-                 * the eight words, and the low 9+9+5 bits of the first three);
-                 * eta~_i = sigma (2 u_i - 1), so eta_i = eta~_i - mean(eta~) =
-                 * 2 sigma (u_i - mean(u)). */
+                 * with 14 random bits each, from one Philox block: its four words
+                 * read as the 128-bit integer w0 + 2^32 w1 + 2^64 w2 + 2^96 w3,
+                 * whose bits 14 i .. 14 i + 13 are m_i (bits 126, 127 unused);
+                 * u_i = (m_i + 1/2) 2^-14. eta~_i = sigma (2 u_i - 1), so
+                 * eta_i = eta~_i - mean(eta~) = 2 sigma (u_i - mean(u)). */
                 if (s->p.sigma != 0.0) {
-                    uint32_t a[4], b[4];
-                    draw(s, (uint32_t)n, t, STREAM_NOISE + 0u, a);
-                    draw(s, (uint32_t)n, t, STREAM_NOISE + 1u, b);
-                    uint32_t wd[8] = {a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3]};
+                    uint32_t w[4];
+                    draw(s, (uint32_t)n, t, STREAM_NOISE, w);
                     uint32_t m[NQ];
-                    for (int i = 0; i < 8; ++i) m[i] = wd[i] >> 9;
-                    m[8] = ((wd[0] & 511u) << 14) | ((wd[1] & 511u) << 5) | ((wd[2] & 511u) >> 4);
+                    for (int i = 0; i < NQ; ++i) {
+                        const int bit = 14 * i, j = bit / 32, o = bit % 32;
+                        uint64_t two = (uint64_t)w[j];
+                        if (j + 1 < 4) two |= (uint64_t)w[j + 1] << 32;
+                        m[i] = (uint32_t)(two >> o) & 0x3FFFu;
+                    }
                     double u[NQ];
-                    for (int i = 0; i < NQ; ++i) u[i] = ((double)m[i] + 0.5) * 1.1920928955078125e-07;
+                    for (int i = 0; i < NQ; ++i) u[i] = ((double)m[i] + 0.5) * 6.103515625e-05;
                     double S = u[0];
                     for (int i = 1; i < NQ; ++i) S = S + u[i];
                     const double ubar = S / 9.0;

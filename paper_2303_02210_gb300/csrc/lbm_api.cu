@@ -56,8 +56,10 @@ Layout make_layout(const lbm_params_t &p)
 {
     Layout L{};
     L.elem = p.precision == LBM_FP64 ? 8 : 4;
-    L.Wp = (p.width + 31) / 32 * 32;
-    L.MW = L.Wp / 32;
+    // stored row: kXO columns left of x = 0 (x = -1 the ghost of W - 1), the
+    // W columns, the ghost of column 0 at x = W, padding to 128 bytes of FP32
+    L.Wp = (p.width + 2 * kXO + 31) / 32 * 32;
+    L.MW = (p.width + 31) / 32;
     L.P = (long long)L.Wp * p.height;
     // planner capacity: divisions per step at up to four times the initial
     // density over the whole lattice, at least 1024
@@ -155,13 +157,15 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// Population copy as a 3-D FP32 tensor {W, H, 9} with row pitch Wp and plane
-// pitch P elements; `bx` x `by` x 9 boxes. Out-of-range loads read zeros.
-bool encode_population_map(CUtensorMap *m, void *base, int W, int H, int Wp, long long P, int bx, int by)
+// Population copy as a 3-D FP32 tensor {Wp, H, 9} of whole stored rows
+// (coordinate x_stored = x + kXO, so the ghost columns are inside) with row
+// pitch Wp and plane pitch P elements; `bx` x `by` x 9 boxes. Out-of-range
+// loads read zeros.
+bool encode_population_map(CUtensorMap *m, void *base, int Wp, int H, long long P, int bx, int by)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, 9};
+    const cuuint64_t dims[3] = {(cuuint64_t)Wp, (cuuint64_t)H, 9};
     const cuuint64_t strides[2] = {(cuuint64_t)Wp * 4u, (cuuint64_t)P * 4u};
     const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 9};
     const cuuint32_t estr[3] = {1, 1, 1};
@@ -284,8 +288,8 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     const Layout &L = s->L;
     SimDev &d = s->d;
     std::memset(&d, 0, sizeof(d));
-    d.f[0] = base + L.off_f0;
-    d.f[1] = base + L.off_f1;
+    d.f[0] = base + L.off_f0 + (size_t)kXO * L.elem;
+    d.f[1] = base + L.off_f1 + (size_t)kXO * L.elem;
     d.mask = (uint32_t *)(base + L.off_mask);
     d.heights = (int32_t *)(base + L.off_heights);
     d.rows0 = (int32_t *)(base + L.off_rows0);
@@ -354,15 +358,19 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     s->tma_variant = p->update_kernel == 3 ? 1 : 0;
     const bool tma_inject = p->update_kernel != 4; // 4: the selector injects into global memory
     if (p->precision == LBM_FP32 && !p->y_periodic && p->update_kernel != 1) {
+        const int ty = launch_update_tma_rows(s->tma_variant);
+        d.upd_tyl2 = 0;
+        while ((1 << d.upd_tyl2) < ty) ++d.upd_tyl2;
         bool ok = true;
         for (int b = 0; b < 2 && ok; ++b)
-            ok = encode_population_map(&s->maps[b], d.f[b], d.W, d.H, d.Wp, d.P, kTmaBoxX + 8, kTmaBoxY + 2);
+            ok = encode_population_map(&s->maps[b], (char *)d.f[b] - (size_t)kXO * 4u, d.Wp, d.H, d.P, kTmaBoxX + 8,
+                                       ty + 2);
         s->use_tma = ok;
         d.inject_in_update = ok && tma_inject ? 1 : 0;
         d.upd_ctas = launch_update_tma_ctas(nsm, s->tma_variant);
         d.upd_magic = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d.upd_ctas - 1) / (uint64_t)d.upd_ctas);
-        if (d.upd_ctas > kTmaMaxCtas || (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) *
-                                                ((p->height + kTmaBoxY - 1) / kTmaBoxY) >= (1LL << 22)) {
+        if (d.upd_ctas > kTmaMaxCtas ||
+            (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) * ((p->height + ty - 1) / ty) >= (1LL << 22)) {
             s->use_tma = false;
             d.inject_in_update = 0;
         }
@@ -575,6 +583,7 @@ int lbm_set_populations(lbm_sim *s, const double *f_host)
             CK(cudaMemcpy2DAsync(dst, (size_t)s->L.Wp * el, tmp.data() + (size_t)i * W * H * el, (size_t)W * el,
                                  (size_t)W * el, H, cudaMemcpyHostToDevice, s->stream));
         }
+    CK(s->kt->ghosts(s->d, s->stream));
     // the stored mass accumulators restart from this state
     DevScalars *sc = s->d.sc;
     const unsigned long long zero = 0ull;

@@ -122,8 +122,10 @@ struct DevScalars {
 
 // Everything a kernel needs to know about one simulation.
 struct SimDev {
-    void *f[2];          // population copies, [q][y][x] with row pitch Wp
-    uint32_t *mask;      // occupancy bits, [y][Wp/32]
+    void *f[2];          // population copies, [q][y][x] with row pitch Wp: f[b] points at
+                         // (0, 0, 0); a stored row spans x = -kXO .. Wp - kXO - 1, where
+                         // x = -1 and x = W are ghost copies of columns W - 1 and 0
+    uint32_t *mask;      // occupancy bits, [y][MW], MW = ceil(W / 32)
     int32_t *heights;    // h(x), W entries
     DevScalars *sc;
     // proliferation planner
@@ -151,6 +153,7 @@ struct SimDev {
     int inject_in_update; // the selector only lists the divisions; the update kernel adds them
     int upd_ctas;         // CTAs of the TMA-staged update kernel (tiles dealt round-robin)
     uint32_t upd_magic;   // ceil(2^32 / upd_ctas): tile / upd_ctas = umulhi(tile, magic)
+    int upd_tyl2;         // log2 of the rows per tile of the TMA-staged update
     int *rec_owner;       // per division (selector order): owning CTA of its tile,
     int *rec_k;           // the tile's index among that CTA's tiles,
     int *rec_off;         // the two pre-stream slots' offsets in the staged box,
@@ -166,6 +169,7 @@ struct SimDev {
 struct KernelTable {
     int elem_bytes;
     cudaError_t (*fill)(const SimDev &, cudaStream_t);
+    cudaError_t (*ghosts)(const SimDev &, cudaStream_t);
     cudaError_t (*scan)(const SimDev &, int cur, cudaStream_t);
     cudaError_t (*observe)(const SimDev &, int cur, int init, cudaStream_t);
     cudaError_t (*cand)(const SimDev &, int cur, uint32_t t, cudaStream_t);
@@ -180,7 +184,7 @@ extern const KernelTable kTableF32;
 extern const KernelTable kTableF64;
 
 // TMA-staged FP32 update (lbm_update_tma.cuh). maps[b] loads from copy b
-// (box (128 + 8) x (8 + 2) x 9).
+// (box (kTmaBoxX + 8) x (rows per tile + 2) x 9, in stored-row coordinates).
 cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
                                   int variant, cudaStream_t s);
 // CTAs the TMA-staged update kernel runs on this many SMs.
@@ -188,7 +192,12 @@ int launch_update_tma_ctas(int nsm, int variant);
 
 // Records a CUDA error for lbm_last_cuda_error and maps it to an LBM_ERR_* code.
 int lbm_record_cuda_error(cudaError_t e);
-constexpr int kTmaBoxX = 128, kTmaBoxY = 8;
+// Rows per tile of a TMA-staged update variant.
+int launch_update_tma_rows(int variant);
+// Stored columns left of x = 0 (16 bytes of FP32, so that tile boxes start
+// aligned): x = -1 is the ghost of column W - 1.
+constexpr int kXO = 4;
+constexpr int kTmaBoxX = 128;
 constexpr int kTmaMaxCtas = 1024; // the reciprocal above is exact for tile < 2^22
 
 } // namespace lbm

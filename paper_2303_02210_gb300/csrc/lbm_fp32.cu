@@ -5,7 +5,6 @@
 namespace lbm {
 const KernelTable kTableF32 = make_table<float>();
 
-static_assert(kTmaBoxX == TMA_TX && kTmaBoxY == TMA_TY, "tensor-map boxes match the kernel tile");
 
 cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
                                   int variant, cudaStream_t s)
@@ -13,5 +12,7 @@ cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CU
     return launch_update_tma(d, cur, t, maps, nsm, variant, s);
 }
 
-int launch_update_tma_ctas(int nsm, int variant) { return (variant == 1 ? 3 : 2) * nsm; }
+int launch_update_tma_ctas(int nsm, int variant) { return tma_ctas_per_sm(variant) * nsm; }
+
+int launch_update_tma_rows(int variant) { return tma_rows(variant); }
 } // namespace lbm

@@ -106,24 +106,48 @@ __global__ void k_fill(SimDev d)
         d.sc->maxmass_accum = -1;
         d.sc->low_acc = 0x7fffffff;
     }
+    // every stored element of a row: x = -kXO .. Wp - kXO - 1; the ghost
+    // columns x = -1 and x = W take the values of x = W - 1 and x = 0
     const long long total = (long long)d.H * d.Wp;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(idx / d.Wp), x = (int)(idx % d.Wp);
+        const int y = (int)(idx / d.Wp), xs = (int)(idx % d.Wp) - kXO;
+        const int x = xs == -1 ? d.W - 1 : (xs == d.W ? 0 : xs);
         double rho = 0.0;
-        if (x < d.W && y < d.rows0[x]) {
+        if (x >= 0 && x < d.W && y < d.rows0[x]) {
             rho = d.rho_init;
             if (d.rho_jitter != 0.0) {
                 const u32x4 r = philox4x32_10(u32x4{(uint32_t)(y * d.W + x), 2u, STREAM_INIT, d.sim}, d.pk);
                 rho = d.rho_init * (1.0 + d.rho_jitter * (2.0 * u01(r.x) - 1.0));
             }
         }
+        const long long o = (long long)y * d.Wp + xs;
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
             const R v = (R)(wq<double>(i) * rho);
-            f0[i * d.P + idx] = v;
-            f1[i * d.P + idx] = v;
+            f0[i * d.P + o] = v;
+            f1[i * d.P + o] = v;
         }
+    }
+}
+
+// Ghost columns x = -1 and x = W of every row of both copies from columns
+// W - 1 and 0 (after the caller has written the populations).
+template <typename R>
+__global__ void k_ghosts(SimDev d)
+{
+    const long long total = 2LL * NQ * d.H;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < 2 * total;
+         k += (long long)gridDim.x * blockDim.x) {
+        R *f = (R *)d.f[k >= total ? 1 : 0];
+        const long long r = k >= total ? k - total : k;
+        const int side = (int)(r & 1);
+        const long long row = r >> 1; // plane * H + y
+        R *base = f + (row / d.H) * d.P + (row % d.H) * d.Wp;
+        if (side == 0)
+            base[-1] = base[d.W - 1];
+        else
+            base[d.W] = base[0];
     }
 }
 
@@ -269,19 +293,34 @@ __device__ __forceinline__ void collide(const R *g, R rho, R *fo, const Consts<R
     }
 }
 
-// Eq. 4: eta_i = 2 sigma (u_i - mean u), u_i uniform with 23 random bits from
-// the Philox blocks (n, t, 16, sim) and (n, t, 17, sim).
-template <typename R>
-__device__ __forceinline__ void noise_eta(R *eta, uint32_t n, uint32_t t, const SimDev &d, const Consts<R> &c)
+// The nine 14-bit fields of a Philox block read as one 128-bit integer
+// w.x + 2^32 w.y + 2^64 w.z + 2^96 w.w: field i is bits 14 i .. 14 i + 13.
+__device__ __forceinline__ void noise_fields(const u32x4 &w, uint32_t m[NQ])
 {
-    const u32x4 a = philox4x32_10(u32x4{n, t, STREAM_NOISE + 0u, d.sim}, d.pk);
-    const u32x4 b = philox4x32_10(u32x4{n, t, STREAM_NOISE + 1u, d.sim}, d.pk);
-    const uint32_t m[NQ] = {a.x >> 9, a.y >> 9, a.z >> 9, a.w >> 9, b.x >> 9, b.y >> 9, b.z >> 9, b.w >> 9,
-                            ((a.x & 511u) << 14) | ((a.y & 511u) << 5) | ((a.z & 511u) >> 4)};
+    m[0] = w.x;
+    m[1] = w.x >> 14;
+    m[2] = __funnelshift_r(w.x, w.y, 28);
+    m[3] = w.y >> 10;
+    m[4] = __funnelshift_r(w.y, w.z, 24);
+    m[5] = w.z >> 6;
+    m[6] = __funnelshift_r(w.z, w.w, 20);
+    m[7] = w.w >> 2;
+    m[8] = w.w >> 16;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) m[i] &= 0x3FFFu;
+}
+
+// Eq. 4: eta_i = 2 sigma (u_i - mean u), u_i = (m_i + 1/2) 2^-14 with m_i the
+// 14-bit fields of the node's Philox block (n, t, 16, sim), given as `w`.
+template <typename R>
+__device__ __forceinline__ void noise_eta_words(R *eta, const u32x4 &w, const Consts<R> &c)
+{
+    uint32_t m[NQ];
+    noise_fields(w, m);
     if constexpr (sizeof(R) == 8) {
         double u[NQ];
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) u[i] = ((double)m[i] + 0.5) * 1.1920928955078125e-07;
+        for (int i = 0; i < NQ; ++i) u[i] = ((double)m[i] + 0.5) * 6.103515625e-05;
         double S = u[0];
 #pragma unroll
         for (int i = 1; i < NQ; ++i) S = S + u[i];
@@ -289,16 +328,28 @@ __device__ __forceinline__ void noise_eta(R *eta, uint32_t n, uint32_t t, const 
 #pragma unroll
         for (int i = 0; i < NQ; ++i) eta[i] = c.two_sigma * (u[i] - ubar);
     } else {
-        // 1 + m 2^-23 exactly; the constant offset cancels in u_i - mean u
+        // 1 + m 2^-14 exactly; the constant offset cancels in u_i - mean u
         float v[NQ];
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) v[i] = __uint_as_float(0x3F800000u | m[i]);
+        for (int i = 0; i < NQ; ++i) v[i] = __uint_as_float(0x3F800000u | (m[i] << 9));
         const float S = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
         const float nb = -c.two_sigma * (S * (1.0f / 9.0f));
         eta[0] = 0.0f; // f_0 follows from mass conservation
 #pragma unroll
         for (int i = 1; i < NQ; ++i) eta[i] = fmaf(c.two_sigma, v[i], nb);
     }
+}
+
+// The noise block of node n at step t.
+__device__ __forceinline__ u32x4 noise_block(uint32_t n, uint32_t t, const SimDev &d)
+{
+    return philox4x32_10(u32x4{n, t, STREAM_NOISE, d.sim}, d.pk);
+}
+
+template <typename R>
+__device__ __forceinline__ void noise_eta(R *eta, uint32_t n, uint32_t t, const SimDev &d, const Consts<R> &c)
+{
+    noise_eta_words<R>(eta, noise_block(n, t, d), c);
 }
 
 template <typename R>
@@ -313,6 +364,23 @@ __device__ __forceinline__ void relax_core(const R *g, R rho, R *fo, uint32_t n,
     R eta[NQ];
     if constexpr (NOISE) {
         noise_eta<R>(eta, n, t, d, c);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) eta[i] = R(0);
+    }
+    if constexpr (sizeof(R) == 8)
+        collide<R>(g, rho, fo, c, NOISE ? eta : nullptr);
+    else
+        collide<R>(g, rho, fo, c, eta);
+}
+
+// relax_core with the node's noise block already drawn (`w`, unused without noise).
+template <typename R, bool NOISE>
+__device__ __forceinline__ void relax_words(const R *g, R rho, R *fo, const u32x4 &w, const Consts<R> &c)
+{
+    R eta[NQ];
+    if constexpr (NOISE) {
+        noise_eta_words<R>(eta, w, c);
     } else {
 #pragma unroll
         for (int i = 0; i < NQ; ++i) eta[i] = R(0);
@@ -421,7 +489,7 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d, int cur, uint32_t t)
     if (y_copy < y_r) {
         const long long n = (long long)(y_r - y_copy) * Wp;
         for (long long k = (long long)blockIdx.x * TPB + threadIdx.x; k < n; k += (long long)gridDim.x * TPB) {
-            const long long o = (long long)y_copy * Wp + k;
+            const long long o = (long long)y_copy * Wp + k - kXO; // whole stored rows, ghosts included
 #pragma unroll
             for (int i = 0; i < NQ; ++i) fout[i * P + o] = fin[i * P + o];
         }
@@ -505,7 +573,7 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d, int cur, uint32_t t)
                 }
                 const unsigned bits = __ballot_sync(0xffffffffu, occ);
                 const int wx0 = x - lane;
-                if (lane == 0 && wx0 < Wp) d.mask[(long long)y * d.MW + (wx0 >> 5)] = bits;
+                if (lane == 0 && wx0 < W) d.mask[(long long)y * d.MW + (wx0 >> 5)] = bits;
                 if (colok) {
                     R *o = fout + (long long)y * Wp + x;
 #pragma unroll
@@ -686,22 +754,23 @@ __device__ __forceinline__ long long block_exscan(long long v, long long *total,
 }
 
 // For the TMA-staged update: where division e goes. Its node's tile (of
-// kTmaBoxX x kTmaBoxY nodes of the active window; tiles are dealt
+// kTmaBoxX x 2^upd_tyl2 nodes of the active window; tiles are dealt
 // round-robin over upd_ctas CTAs), that tile's index among the owner's tiles,
 // and the offsets of the two pre-stream slots in the tile's staged box
-// ((kTmaBoxX + 8) x (kTmaBoxY + 2) x 9 with the tile at column 4, row 1):
-// the source (x - ex_q, y - ey_q) unwrapped in x, or across a wall the
-// node's own population opp(q).
+// ((kTmaBoxX + 8) x (2^upd_tyl2 + 2) x 9 with the tile at column 4, row 1):
+// the source (x - ex_q, y - ey_q) unwrapped in x (the box holds the ghost
+// columns -1 and W), or across a wall the node's own population opp(q).
 template <typename R>
 __device__ __forceinline__ void division_record(const SimDev &d, int e, uint32_t key, int cnt, int y_r)
 {
-    constexpr int LX = kTmaBoxX + 8, PL = (kTmaBoxY + 2) * LX;
+    constexpr int LX = kTmaBoxX + 8;
+    const int TY = 1 << d.upd_tyl2, PL = (TY + 2) * LX;
     const int x = key_x(key), y = key_y(key), p = key_pair(key);
     const int ncx = (d.W + kTmaBoxX - 1) / kTmaBoxX;
-    const int ty = (y - y_r) / kTmaBoxY, tx = x / kTmaBoxX;
+    const int ty = (y - y_r) >> d.upd_tyl2, tx = x / kTmaBoxX;
     const uint32_t tile = (uint32_t)(ty * ncx + tx);
     const uint32_t q = __umulhi(tile, d.upd_magic);
-    const int x0 = tx * kTmaBoxX, y0 = y_r + ty * kTmaBoxY;
+    const int x0 = tx * kTmaBoxX, y0 = y_r + ty * TY;
     d.rec_owner[e] = (int)(tile - q * (uint32_t)d.upd_ctas);
     d.rec_k[e] = (int)q;
 #pragma unroll
@@ -865,8 +934,16 @@ __global__ void __launch_bounds__(SEL_TPB) k_select(SimDev d, int cur, uint32_t 
 #pragma unroll
             for (int j = 0; j < SEL_BATCH; ++j) {
                 if (e0 + j * SEL_TPB < nlist) {
-                    f[sl[2 * j]] = val[2 * j] + add[j];
-                    f[sl[2 * j + 1]] = val[2 * j + 1] + add[j];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const long long o = sl[2 * j + h];
+                        const R v = val[2 * j + h] + add[j];
+                        f[o] = v;
+                        // the ghost copy of an edge column (read by the TMA-staged update)
+                        const int xc = (int)((o % d.P) % d.Wp);
+                        if (xc == 0) f[o + d.W] = v;
+                        if (xc == d.W - 1) f[o - d.W] = v;
+                    }
                 }
             }
         }
@@ -1127,6 +1204,11 @@ struct Launch {
         k_fill<R><<<4 * 152, 256, 0, s>>>(d);
         return cudaGetLastError();
     }
+    static cudaError_t ghosts(const SimDev &d, cudaStream_t s)
+    {
+        k_ghosts<R><<<152, 256, 0, s>>>(d);
+        return cudaGetLastError();
+    }
     static cudaError_t scan(const SimDev &d, int cur, cudaStream_t s)
     {
         k_scan<R><<<4 * 152, 256, 0, s>>>(d, cur);
@@ -1181,7 +1263,7 @@ struct Launch {
 template <typename R>
 constexpr KernelTable make_table()
 {
-    return KernelTable{(int)sizeof(R),        &Launch<R>::fill,   &Launch<R>::scan,
+    return KernelTable{(int)sizeof(R),        &Launch<R>::fill,   &Launch<R>::ghosts, &Launch<R>::scan,
                        &Launch<R>::observe,   &Launch<R>::cand,   &Launch<R>::select,
                        &Launch<R>::update,    &Launch<R>::fields, &Launch<R>::update_blocks_per_sm,
                        Launch<R>::UPD_TPB};

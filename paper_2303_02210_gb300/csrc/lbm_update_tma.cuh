@@ -1,22 +1,26 @@
 // TMA-staged fused update (FP32 storage, walls in y), the fast path of
-// App. A steps 1, 2, 4-7: same arithmetic as k_update<float>, different data
-// movement.
+// App. A steps 1-7 (step 3's divisions are added to the staged tile): the same
+// per-node arithmetic as k_update<float>, different data movement.
 //
-// Each CTA (persistent) walks tiles of TX columns x TY rows of the
-// active window. A tile's pre-stream populations arrive in shared memory as one
-// 3-D bulk tensor copy of box (TX + 8) x (TY + 2) x 9: the tile plus 4 aligned
-// columns on each side and one row above and below, for all nine planes.
-// Copies complete on an mbarrier; a CTA issues the copy of its next tile as
-// soon as its threads hold the current one in registers, so the copy overlaps
-// the compute. Coordinates outside the lattice (x < 0, y < 0, y >= H) arrive as
-// zeros; for the two tiles at the ends of a row band the periodic wrap in x is
-// patched into the staged tile (the column just outside the lattice on each
-// side). Each pulled value is then one shared-memory load at a compile-time
-// offset from the node's own position. One warp takes one row of a tile, one
-// lane four adjacent columns: aligned planes come in as one 16-byte shared
-// load, planes shifted in x as one 16-byte and one 4-byte load; results go
-// straight from registers to global memory as 16-byte stores (512 contiguous
-// bytes per warp and plane). Two CTAs share an SM.
+// Each CTA (persistent, CTAS per SM) walks tiles of 128 columns x TY rows of
+// the active window, dealt round-robin over the grid. A tile's pre-stream
+// populations arrive in shared memory as one 3-D bulk tensor copy of box
+// 136 x (TY + 2) x 9: the tile plus 4 stored columns on each side and one row
+// above and below, for all nine planes. The stored rows carry ghost copies of
+// the periodic neighbours (x = -1 holds column W - 1, x = W holds column 0), so
+// the box needs no patching and never starts outside the stored row.
+//
+// Pipeline: STAGES boxes per CTA. Consumers wait on the stage's `full`
+// mbarrier (transaction bytes, suspending rather than spinning), take their
+// values into registers and arrive on its `empty` mbarrier; thread 0 refills
+// the stage once every warp has arrived. Warps never wait for each other
+// otherwise (a CTA-wide barrier only on the tiles that receive divisions).
+//
+// Thread layout: two warps per tile row, each lane two adjacent columns
+// (2 lane, 2 lane + 1 of its warp's 64): unshifted planes are one 8-byte
+// shared load for both nodes, planes shifted in x two 4-byte loads; results
+// are 8-byte stores (256 contiguous bytes per warp and plane). Both nodes'
+// Philox blocks are drawn together before either node is relaxed.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -24,73 +28,97 @@
 
 namespace lbm {
 
-constexpr int TMA_TX = 128;                                      // 32 lanes x 4 columns
-constexpr int TMA_TY = 8;                                        // one warp per row
-constexpr int TMA_NT = 32 * TMA_TY;
-constexpr int TMA_LX = TMA_TX + 8;
-constexpr int TMA_LY = TMA_TY + 2;
-constexpr int TMA_IN_FLOATS = 9 * TMA_LY * TMA_LX;             // one box
-constexpr int TMA_IN_STRIDE = (TMA_IN_FLOATS + 31) / 32 * 32;   // stage pitch, 128-byte multiple
-constexpr uint32_t TMA_IN_BYTES = (uint32_t)TMA_IN_FLOATS * 4u; // bytes one box copy delivers
-// Slot additions (two per division) a CTA keeps in shared memory for its
-// staged tiles (more are read from global memory per tile); tiles flagged
-// per CTA.
-constexpr int TMA_EV_CAP = 1024;
+constexpr int TMA_TX = kTmaBoxX;   // 128 columns: two warps of 64
+constexpr int TMA_LX = TMA_TX + 8; // staged columns x0 - 4 .. x0 + 131
+// Divisions of a CTA kept in shared memory (more are read from global memory
+// per tile); tiles flagged per CTA.
+constexpr int TMA_EV_CAP = 512;
 constexpr int TMA_KFLAG_WORDS = 32;
-template <int STAGES>
-constexpr size_t tma_smem_bytes()
-{
-    return (size_t)STAGES * TMA_IN_STRIDE * 4 + 8 * STAGES + (size_t)TMA_EV_CAP * 12 + TMA_KFLAG_WORDS * 4 + 128;
-}
 // a stalled copy is given up after about two seconds at 2 GHz
 constexpr long long TMA_WAIT_BUDGET = 4000000000ll;
-static_assert(((TMA_IN_STRIDE * 4) % 128) == 0 && ((TMA_LX * 4) % 16) == 0, "smem alignment");
-static_assert(2 * (tma_smem_bytes<2>() + 1024) <= 227 * 1024, "two CTAs per SM by shared memory");
+static_assert(kXO % 4 == 0, "tile boxes start on 16-byte boundaries");
 
-constexpr int PLANE = TMA_LY * TMA_LX; // floats per staged plane
+template <int TY>
+struct TmaGeom {
+    static constexpr int NT = 64 * TY;                          // threads: two warps per row
+    static constexpr int WARPS = NT / 32;
+    static constexpr int LY = TY + 2;
+    static constexpr int PLANE = LY * TMA_LX;                   // floats per staged plane
+    static constexpr int IN_FLOATS = 9 * PLANE;                 // one box
+    static constexpr int STRIDE = (IN_FLOATS + 31) / 32 * 32;   // stage pitch, 128-byte multiple
+    static constexpr uint32_t BYTES = (uint32_t)IN_FLOATS * 4u; // bytes one box copy delivers
+};
 
-// Four consecutive staged values starting at p (16-byte aligned).
-__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-
-// The values a thread's four nodes pull for direction i: the staged row of
-// the source, shifted by -ex_i. `b` points at the thread's first node in plane
-// 0 (16-byte aligned).
-template <int I>
-__device__ __forceinline__ void pull4(const float *b, float v[4])
+template <int TY, int STAGES>
+constexpr size_t tma_smem_bytes()
 {
-    const float *p = b + I * PLANE - ey(I) * TMA_LX;
-    const float4 a = lds4(p);
-    if constexpr (ex(I) == 0) {
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    } else if constexpr (ex(I) == 1) { // from x - 1
-        v[0] = p[-1]; v[1] = a.x; v[2] = a.y; v[3] = a.z;
-    } else {                           // from x + 1
-        v[0] = a.y; v[1] = a.z; v[2] = a.w; v[3] = p[4];
+    return 128 + (size_t)STAGES * TmaGeom<TY>::STRIDE * 4 + 16 * STAGES + (size_t)TMA_EV_CAP * 16 +
+           TMA_KFLAG_WORDS * 4;
+}
+static_assert(3 * (tma_smem_bytes<4, 2>() + 1024) <= 228 * 1024, "three CTAs per SM by shared memory");
+static_assert(2 * (tma_smem_bytes<4, 3>() + 1024) <= 228 * 1024, "two CTAs per SM by shared memory");
+
+__device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+
+// The populations two adjacent nodes pull: `b` points at the first node's
+// staged plane-0 value (8-byte aligned). Across the rear (REAR) or top (TOP)
+// wall a node takes its own opposite population (half-way bounce-back).
+template <int PLANE, bool REAR, bool TOP>
+__device__ __forceinline__ void pull2(const float *b, float ga[NQ], float gb[NQ])
+{
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        const bool own = (ey(i) == 1 && REAR) || (ey(i) == -1 && TOP);
+        if (own) {
+            const float2 v = lds2(b + opp(i) * PLANE);
+            ga[i] = v.x;
+            gb[i] = v.y;
+        } else if (ex(i) == 0) {
+            const float2 v = lds2(b + i * PLANE - ey(i) * TMA_LX);
+            ga[i] = v.x;
+            gb[i] = v.y;
+        } else {
+            const float *p = b + i * PLANE - ey(i) * TMA_LX - ex(i);
+            ga[i] = p[0];
+            gb[i] = p[1];
+        }
     }
 }
 
-// The node's own populations of direction i (half-way bounce-back source).
-template <int I>
-__device__ __forceinline__ void own4(const float *b, float v[4])
+// One node: relaxation (or reversal below rho_c), the negative fix; returns
+// the mass the fix added.
+template <bool NOISE>
+__device__ __forceinline__ float update_node(const float g[NQ], float rho, bool occ, float fo[NQ], const u32x4 &w,
+                                             const Consts<float> &cf, int negfix)
 {
-    const float4 a = lds4(b + I * PLANE);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    if (occ) {
+        relax_words<float, NOISE>(g, rho, fo, w, cf);
+        return fix_negative<float>(fo, negfix);
+    }
+    // rho < rho_c: reverse the directions (two-step bounce-back)
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) fo[i] = g[opp(i)];
+    return 0.0f;
 }
 
-// STAGES staged tiles per CTA, CTAS CTAs per SM (registers are capped so
-// that they fit); NOISE: sigma != 0.
-template <int STAGES, int CTAS, bool NOISE>
-__global__ void __launch_bounds__(TMA_NT, CTAS)
+// CTAS CTAs per SM (registers are capped so that they fit); NOISE: sigma != 0.
+template <int TY, int STAGES, int CTAS, bool NOISE>
+__global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
     k_update_tma(SimDev d, int cur, uint32_t t, const __grid_constant__ CUtensorMap tm_in)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *s_in = (float *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    uint64_t *full = (uint64_t *)(s_in + STAGES * TMA_IN_STRIDE);
+    using G = TmaGeom<TY>;
+    constexpr int NT = G::NT, PLANE = G::PLANE;
+    extern __shared__ __align__(128) float smem_f[];
+    // stages on a 128-byte boundary (offset from the array itself, so that
+    // every access stays a shared-memory access)
+    float *s_in = smem_f + ((128u - (smem_u32(smem_f) & 127u)) & 127u) / 4u;
+    uint64_t *full = reinterpret_cast<uint64_t *>(s_in + STAGES * G::STRIDE);
+    uint64_t *empty = full + STAGES;
     // divisions of this CTA's tiles: local tile index, two staged offsets, amount
-    int *ev_k = (int *)(full + STAGES);
-    int *ev_off = ev_k + TMA_EV_CAP / 2;
-    float *ev_add = (float *)(ev_off + TMA_EV_CAP);
-    unsigned *kflag = (unsigned *)(ev_add + TMA_EV_CAP); // tiles with divisions
+    int *ev_k = reinterpret_cast<int *>(empty + STAGES);
+    int *ev_off = ev_k + TMA_EV_CAP;
+    float *ev_add = reinterpret_cast<float *>(ev_off + 2 * TMA_EV_CAP);
+    unsigned *kflag = reinterpret_cast<unsigned *>(ev_add + TMA_EV_CAP); // tiles with divisions
     __shared__ int s_abort, s_nev;
 
     const float *__restrict__ fin = (const float *)d.f[cur];
@@ -98,13 +126,15 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
     const int y_r = d.sc->y_r, y_copy = d.sc->y_copy, y_hi = d.sc->y_hi;
     const int W = d.W, H = d.H, Wp = d.Wp;
     const long long P = d.P;
-    const int tid = threadIdx.x, lane = tid & 31, r = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int half = warp & 1, row = warp >> 1; // column half and row of the tile
 
-    // rows the rear wall has just frozen: bring this copy up to date
+    // rows the rear wall has just frozen: bring this copy up to date (whole
+    // stored rows, ghosts included)
     if (y_copy < y_r) {
         const long long n = (long long)(y_r - y_copy) * Wp;
-        for (long long k = (long long)blockIdx.x * TMA_NT + tid; k < n; k += (long long)gridDim.x * TMA_NT) {
-            const long long o = (long long)y_copy * Wp + k;
+        for (long long k = (long long)blockIdx.x * NT + tid; k < n; k += (long long)gridDim.x * NT) {
+            const long long o = (long long)y_copy * Wp + k - kXO;
 #pragma unroll
             for (int i = 0; i < NQ; ++i) fout[i * P + o] = fin[i * P + o];
         }
@@ -112,27 +142,32 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
 
     const int ncx = (W + TMA_TX - 1) / TMA_TX;
     const int nrows = y_hi - y_r;
-    const int nty = nrows > 0 ? (nrows + TMA_TY - 1) / TMA_TY : 0;
+    const int nty = nrows > 0 ? (nrows + TY - 1) / TY : 0;
     const int ntiles = ncx * nty;
-    const int G = (int)gridDim.x;
-    const int count = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
-    // tile k of this CTA is blockIdx.x + k G; its (tx, ty) advance by (G % ncx, G / ncx)
-    const int dtx = G % ncx, dty = G / ncx;
+    const int Gd = (int)gridDim.x;
+    const int count = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / Gd + 1 : 0;
+    // tile k of this CTA is blockIdx.x + k Gd; its (tx, ty) advance by (Gd % ncx, Gd / ncx)
+    const int dtx = Gd % ncx, dty = Gd / ncx;
 
     if (tid == 0) {
         s_abort = 0;
         s_nev = 0;
         prefetch_tensormap(&tm_in);
-        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], G::WARPS);
+        }
         fence_mbar_init();
     }
     if (tid < TMA_KFLAG_WORDS) kflag[tid] = 0u;
     __syncthreads();
-    int itx = (int)blockIdx.x % ncx, ity = (int)blockIdx.x / ncx; // next tile to load (thread 0)
-    auto issue = [&](int k) {
-        const int s = k % STAGES;
-        mbar_arrive_expect_tx(&full[s], TMA_IN_BYTES);
-        tma_load_3d(s_in + s * TMA_IN_STRIDE, &tm_in, itx * TMA_TX - 4, y_r + ity * TMA_TY - 1, 0, &full[s]);
+    // producer state (thread 0): next tile to load and copies issued
+    int itx = (int)blockIdx.x % ncx, ity = (int)blockIdx.x / ncx, issued = 0;
+    auto issue = [&]() {
+        const int s = issued % STAGES;
+        mbar_arrive_expect_tx(&full[s], G::BYTES);
+        tma_load_3d(s_in + s * G::STRIDE, &tm_in, itx * TMA_TX - 4 + kXO, y_r + ity * TY - 1, 0, &full[s]);
+        ++issued;
         itx += dtx;
         ity += dty;
         if (itx >= ncx) {
@@ -142,27 +177,27 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
     };
     // the first tiles' copies run while the divisions are sorted out below
     if (tid == 0)
-        for (int k = 0; k < STAGES && k < count; ++k) issue(k);
+        while (issued < STAGES && issued < count) issue();
 
     // App. A step 3 for this CTA: the selector listed, per division, the CTA
     // that owns its node's tile, the tile's local index, the offsets of the
     // two pre-stream slots in the staged box and the amount; keep ours.
     const int nev_all = d.inject_in_update ? d.sc->n_events : 0;
-    constexpr int EV_BATCH = 16; // owner words a thread loads before it looks at any
-    for (int eb = 0; eb < nev_all; eb += TMA_NT * EV_BATCH) {
+    constexpr int EV_BATCH = 8; // owner words a thread loads before it looks at any
+    for (int eb = 0; eb < nev_all; eb += NT * EV_BATCH) {
         int own[EV_BATCH];
 #pragma unroll
         for (int j = 0; j < EV_BATCH; ++j) {
-            const int e = eb + j * TMA_NT + tid;
+            const int e = eb + j * NT + tid;
             own[j] = e < nev_all ? d.rec_owner[e] : -1;
         }
 #pragma unroll
         for (int j = 0; j < EV_BATCH; ++j) {
-            const int e = eb + j * TMA_NT + tid;
+            const int e = eb + j * NT + tid;
             if (own[j] == (int)blockIdx.x) {
                 const int at = atomicAdd(&s_nev, 1);
                 const int k = d.rec_k[e];
-                if (at < TMA_EV_CAP / 2) {
+                if (at < TMA_EV_CAP) {
                     ev_k[at] = k;
                     ev_off[2 * at] = d.rec_off[2 * e];
                     ev_off[2 * at + 1] = d.rec_off[2 * e + 1];
@@ -173,180 +208,172 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
         }
     }
     __syncthreads();
-    const int nev = s_nev;                            // divisions of this CTA
-    const bool ev_overflow = nev > TMA_EV_CAP / 2;    // then scan the global list per tile
+    const int nev = s_nev;                     // divisions of this CTA
+    const bool ev_overflow = nev > TMA_EV_CAP; // then scan the global list per tile
 
     const Consts<float> cf = make_consts<float>(d);
     const float rho_c = d.f_rho_c;
-    // periodic wrap patch: thread (plane pq, staged row pyb) for tid < 9 LY
-    const int pq = tid / TMA_LY, pyb = tid - pq * TMA_LY;
-    const bool patcher = tid < 9 * TMA_LY;
+    const int negfix = d.negfix;
+    const int cl = 64 * half + 2 * lane; // this thread's first column in the tile
     long long mass = 0;
     int maxrow = -1;
     float clip = 0.0f;
-    int done = 0;
+    bool dead = false; // a wait of this thread gave up: no more waits, same barriers
     int tx = (int)blockIdx.x % ncx, ty = (int)blockIdx.x / ncx;
 
     for (int k = 0; k < count; ++k) {
         const int s = k % STAGES;
         const uint32_t parity = (uint32_t)((k / STAGES) & 1);
-        const int x0 = tx * TMA_TX, y0 = y_r + ty * TMA_TY;
-        float *stage = s_in + s * TMA_IN_STRIDE;
-        // periodic wrap: the staged column x = -1 holds x = W - 1 and the
-        // column x = W holds x = 0
-        const bool left = tx == 0, right = tx == ncx - 1;
-        const int pyg = y0 - 1 + pyb;
-        const bool pok = patcher && (left || right) && pyg >= 0 && pyg < H;
-        float pl = 0.0f, pr = 0.0f;
-        if (pok) {
-            const float *rowp = fin + pq * P + (long long)pyg * Wp;
-            if (left) pl = rowp[W - 1];
-            if (right) pr = rowp[0];
-        }
-        if (!mbar_wait_bounded(&full[s], parity, TMA_WAIT_BUDGET)) atomicOr(&s_abort, 1);
-        if (left || right) { // uniform across the CTA
-            if (pok) {
-                float *sp = stage + pq * PLANE + pyb * TMA_LX;
-                if (left) sp[3] = pl;
-                if (right) sp[(W - x0) + 4] = pr;
-                fence_proxy_async_smem(); // before the next bulk copy overwrites them
-            }
-            __syncthreads();
+        const int x0 = tx * TMA_TX, y0 = y_r + ty * TY;
+        float *stage = s_in + s * G::STRIDE;
+        if (!dead && !mbar_wait_bounded(&full[s], parity, TMA_WAIT_BUDGET)) {
+            dead = true;
+            atomicOr(&s_abort, 1);
         }
         // divisions of this tile, added to the staged pre-stream slots
-        const bool has_ev = nev > 0 && (ev_overflow || k >= 32 * TMA_KFLAG_WORDS || ((kflag[k >> 5] >> (k & 31)) & 1u));
+        const bool has_ev =
+            nev > 0 && (ev_overflow || k >= 32 * TMA_KFLAG_WORDS || ((kflag[k >> 5] >> (k & 31)) & 1u));
         if (has_ev) { // uniform across the CTA
             if (!ev_overflow) {
-                for (int i = tid; i < nev; i += TMA_NT)
+                for (int i = tid; i < nev; i += NT)
                     if (ev_k[i] == k) {
                         stage[ev_off[2 * i]] += ev_add[i];
                         stage[ev_off[2 * i + 1]] += ev_add[i];
                     }
             } else {
-                for (int e = tid; e < nev_all; e += TMA_NT)
+                for (int e = tid; e < nev_all; e += NT)
                     if (d.rec_owner[e] == (int)blockIdx.x && d.rec_k[e] == k) {
                         stage[d.rec_off[2 * e]] += d.rec_add[e];
                         stage[d.rec_off[2 * e + 1]] += d.rec_add[e];
                     }
             }
-            fence_proxy_async_smem();
+            fence_proxy_async_smem(); // before a later bulk copy overwrites them
             __syncthreads();
         }
-        if (s_abort) break;
-        const int y = y0 + r;
-        const bool active = y < y_hi; // rows past the active window hold no mass (warp-uniform)
-        const int xb = x0 + 4 * lane;  // first of this thread's four columns
-        float g[NQ][4];
+        // the pulled populations of this thread's two nodes (rows past the
+        // active window hold no mass and are skipped; warp-uniform)
+        const int y = y0 + row;
+        const bool active = y < y_hi;
+        float ga[NQ], gb[NQ];
         if (active) {
-            const float *b = stage + (r + 1) * TMA_LX + 4 * lane + 4;
-            pull4<0>(b, g[0]);
-            pull4<1>(b, g[1]);
-            pull4<3>(b, g[3]);
-            if (y - 1 < y_r) { // rear wall: half-way bounce-back
-                own4<4>(b, g[2]);
-                own4<7>(b, g[5]);
-                own4<8>(b, g[6]);
-            } else {
-                pull4<2>(b, g[2]);
-                pull4<5>(b, g[5]);
-                pull4<6>(b, g[6]);
-            }
-            if (y + 1 >= H) { // top wall
-                own4<2>(b, g[4]);
-                own4<5>(b, g[7]);
-                own4<6>(b, g[8]);
-            } else {
-                pull4<4>(b, g[4]);
-                pull4<7>(b, g[7]);
-                pull4<8>(b, g[8]);
-            }
+            const float *b = stage + (row + 1) * TMA_LX + cl + 4;
+            const bool rear = y - 1 < y_r, top = y + 1 >= H; // half-way bounce-back walls
+            if (!rear && !top)
+                pull2<PLANE, false, false>(b, ga, gb);
+            else if (!top)
+                pull2<PLANE, true, false>(b, ga, gb);
+            else if (!rear)
+                pull2<PLANE, false, true>(b, ga, gb);
+            else
+                pull2<PLANE, true, true>(b, ga, gb);
         }
-        __syncthreads(); // the tile is in registers: the stage is free
-        if (tid == 0 && k + STAGES < count) issue(k + STAGES);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (tid == 0 && issued < count) {
+            // refill this stage once every warp has its values
+            if (!dead && !mbar_wait_bounded(&empty[s], parity, TMA_WAIT_BUDGET)) {
+                dead = true;
+                atomicOr(&s_abort, 1);
+            }
+            if (!dead) issue();
+        }
         if (active) {
-            float fo[NQ][4];
-            float rho[4], added[4];
-            bool occ[4];
-            unsigned nib = 0;
+            const int x = x0 + cl;
+            const bool oka = x < W, okb = x + 1 < W;
+            float rhoa = ga[0], rhob = gb[0];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float r0 = g[0][j];
-#pragma unroll
-                for (int i = 1; i < NQ; ++i) r0 = r0 + g[i][j];
-                rho[j] = r0;
-                occ[j] = xb + j < W && r0 >= rho_c;
-                added[j] = 0.0f;
-                nib |= (unsigned)occ[j] << j;
+            for (int i = 1; i < NQ; ++i) {
+                rhoa = rhoa + ga[i];
+                rhob = rhob + gb[i];
             }
-            if (__all_sync(0xffffffffu, nib == 15u)) {
-                // the bulk: every node of the warp's row is occupied
+            const bool occa = oka && rhoa >= rho_c, occb = okb && rhob >= rho_c;
+            if (__all_sync(0xffffffffu, occa && occb)) {
+                // the bulk: all 64 nodes of the warp's segment are occupied
+                const uint32_t n = (uint32_t)(y * W + x);
+                float fa[NQ], fb[NQ];
+                relax_words<float, NOISE>(ga, rhoa, fa, NOISE ? noise_block(n, t, d) : u32x4{0u, 0u, 0u, 0u}, cf);
+                relax_words<float, NOISE>(gb, rhob, fb, NOISE ? noise_block(n + 1u, t, d) : u32x4{0u, 0u, 0u, 0u},
+                                          cf);
+                float mn = fminf(fa[0], fb[0]);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float gj[NQ], fj[NQ];
-#pragma unroll
-                    for (int i = 0; i < NQ; ++i) gj[i] = g[i][j];
-                    relax_core<float, NOISE>(gj, rho[j], fj, (uint32_t)(y * W + xb + j), t, d, cf);
-#pragma unroll
-                    for (int i = 0; i < NQ; ++i) fo[i][j] = fj[i];
-                }
-                float mn = fo[0][0];
-#pragma unroll
-                for (int i = 0; i < NQ; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) mn = fminf(mn, fo[i][j]);
+                for (int i = 1; i < NQ; ++i) mn = fminf(mn, fminf(fa[i], fb[i]));
+                float adda = 0.0f, addb = 0.0f;
                 if (__any_sync(0xffffffffu, mn < 0.0f)) {
+                    adda = fix_negative<float>(fa, negfix);
+                    addb = fix_negative<float>(fb, negfix);
+                    clip += adda + addb;
+                }
+                if ((lane & 15) == 0) d.mask[(long long)y * d.MW + (x0 >> 5) + 2 * half + (lane >> 4)] = 0xffffffffu;
+                float *o = fout + (long long)y * Wp + x;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float fj[NQ];
+                for (int i = 0; i < NQ; ++i) *reinterpret_cast<float2 *>(o + i * P) = make_float2(fa[i], fb[i]);
+                const int xw = x0 + 64 * half; // first column of the warp
+                if (xw == 0 || xw + 63 == W - 1) { // a warp at the lattice edge: ghost copies
+                    if (x == 0) {
 #pragma unroll
-                        for (int i = 0; i < NQ; ++i) fj[i] = fo[i][j];
-                        added[j] = fix_negative<float>(fj, d.negfix);
+                        for (int i = 0; i < NQ; ++i) o[i * P + W] = fa[i];
+                    }
+                    if (x + 1 == W - 1) {
 #pragma unroll
-                        for (int i = 0; i < NQ; ++i) fo[i][j] = fj[i];
+                        for (int i = 0; i < NQ; ++i) o[i * P + 1 - W] = fb[i];
                     }
                 }
+                const float roa = rhoa + adda, rob = rhob + addb;
+                mass += fix24<float>(roa) + fix24<float>(rob);
+                if (roa != 0.0f || rob != 0.0f) maxrow = y;
             } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float gj[NQ], fj[NQ];
-#pragma unroll
-                    for (int i = 0; i < NQ; ++i) gj[i] = g[i][j];
-                    if (occ[j]) {
-                        relax_core<float, NOISE>(gj, rho[j], fj, (uint32_t)(y * W + xb + j), t, d, cf);
-                        added[j] = fix_negative<float>(fj, d.negfix);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < NQ; ++i) fj[i] = gj[opp(i)];
-                    }
-#pragma unroll
-                    for (int i = 0; i < NQ; ++i) fo[i][j] = fj[i];
+                u32x4 wa{0u, 0u, 0u, 0u}, wb{0u, 0u, 0u, 0u};
+                if (NOISE && (occa || occb)) {
+                    const uint32_t n = (uint32_t)(y * W + x);
+                    wa = noise_block(n, t, d);
+                    wb = noise_block(n + 1u, t, d);
                 }
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (xb + j < W) {
-                    clip += added[j];
-                    float fj[NQ];
-#pragma unroll
-                    for (int i = 0; i < NQ; ++i) fj[i] = fo[i][j];
-                    const float ro = node_mass<float>(fj, rho[j], added[j]);
+                float fa[NQ], fb[NQ];
+                const float adda = update_node<NOISE>(ga, rhoa, occa, fa, wa, cf, negfix);
+                const float addb = update_node<NOISE>(gb, rhob, occb, fb, wb, cf, negfix);
+                // occupancy bits: lanes 0-15 hold one 32-column word, lanes 16-31 the next
+                unsigned v = ((unsigned)occa | ((unsigned)occb << 1)) << (2 * (lane & 15));
+                v |= __shfl_xor_sync(0xffffffffu, v, 1);
+                v |= __shfl_xor_sync(0xffffffffu, v, 2);
+                v |= __shfl_xor_sync(0xffffffffu, v, 4);
+                v |= __shfl_xor_sync(0xffffffffu, v, 8);
+                const int word = (x0 >> 5) + 2 * half + (lane >> 4);
+                if ((lane & 15) == 0 && word < d.MW) d.mask[(long long)y * d.MW + word] = v;
+                float *o = fout + (long long)y * Wp + x;
+                if (okb) {
+    #pragma unroll
+                    for (int i = 0; i < NQ; ++i) *reinterpret_cast<float2 *>(o + i * P) = make_float2(fa[i], fb[i]);
+                } else if (oka) { // odd W: the last column alone (x = W is the ghost)
+    #pragma unroll
+                    for (int i = 0; i < NQ; ++i) o[i * P] = fa[i];
+                }
+                // ghost copies of the edge columns for the next step's boxes
+                if (x == 0) {
+    #pragma unroll
+                    for (int i = 0; i < NQ; ++i) o[i * P + W] = fa[i];
+                }
+                if (x == W - 1) {
+    #pragma unroll
+                    for (int i = 0; i < NQ; ++i) o[i * P - W] = fa[i];
+                }
+                if (x + 1 == W - 1) {
+    #pragma unroll
+                    for (int i = 0; i < NQ; ++i) o[i * P + 1 - W] = fb[i];
+                }
+                // populations are non-negative after every step, so a node holds
+                // mass iff their sum (rho + what the fix added) is non-zero
+                if (oka) {
+                    clip += adda;
+                    const float ro = rhoa + adda;
                     mass += fix24<float>(ro);
                     if (ro != 0.0f) maxrow = y;
                 }
-            }
-            // occupancy bits: lanes 8m..8m+7 hold the 32 columns of word m
-            unsigned v = nib << (4 * (lane & 7));
-            v |= __shfl_xor_sync(0xffffffffu, v, 1);
-            v |= __shfl_xor_sync(0xffffffffu, v, 2);
-            v |= __shfl_xor_sync(0xffffffffu, v, 4);
-            const int wx = (x0 >> 5) + (lane >> 3);
-            if ((lane & 7) == 0 && wx < d.MW) d.mask[(long long)y * d.MW + wx] = v;
-            // four columns at a time; columns in [W, Wp) are padding nobody reads
-            if (xb < Wp) {
-                float *o = fout + (long long)y * Wp + xb;
-#pragma unroll
-                for (int i = 0; i < NQ; ++i)
-                    *reinterpret_cast<float4 *>(o + i * P) = make_float4(fo[i][0], fo[i][1], fo[i][2], fo[i][3]);
+                if (okb) {
+                    clip += addb;
+                    const float ro = rhob + addb;
+                    mass += fix24<float>(ro);
+                    if (ro != 0.0f) maxrow = y;
+                }
             }
         }
         tx += dtx;
@@ -355,12 +382,11 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
             tx -= ncx;
             ++ty;
         }
-        ++done;
     }
     if (tid == 0 && s_abort) {
         atomicOr(&d.sc->status, ST_TIMEOUT);
-        // let every copy this CTA issued land before the CTA exits
-        for (int k = done; k < count && k < done + STAGES; ++k)
+        // let the copies still in flight land before the CTA exits
+        for (int k = issued - STAGES > 0 ? issued - STAGES : 0; k < issued; ++k)
             mbar_wait_bounded(&full[k % STAGES], (uint32_t)((k / STAGES) & 1), TMA_WAIT_BUDGET);
     }
     mass = warp_sum_ll(mass);
@@ -373,7 +399,7 @@ __global__ void __launch_bounds__(TMA_NT, CTAS)
     }
 }
 
-template <int STAGES, int CTAS, bool NOISE>
+template <int TY, int STAGES, int CTAS, bool NOISE>
 cudaError_t launch_update_tma_variant(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
                                       cudaStream_t s)
 {
@@ -382,26 +408,30 @@ cudaError_t launch_update_tma_variant(const SimDev &d, int cur, uint32_t t, cons
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64 || !attr[dev]) {
-        e = cudaFuncSetAttribute(k_update_tma<STAGES, CTAS, NOISE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tma_smem_bytes<STAGES>());
+        e = cudaFuncSetAttribute(k_update_tma<TY, STAGES, CTAS, NOISE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tma_smem_bytes<TY, STAGES>());
         if (e != cudaSuccess) return e;
         if (dev < 64) attr[dev] = true;
     }
     // maps[b] loads from population copy b
-    k_update_tma<STAGES, CTAS, NOISE><<<CTAS * nsm, TMA_NT, tma_smem_bytes<STAGES>(), s>>>(d, cur, t, maps[cur]);
+    k_update_tma<TY, STAGES, CTAS, NOISE>
+        <<<CTAS * nsm, TmaGeom<TY>::NT, tma_smem_bytes<TY, STAGES>(), s>>>(d, cur, t, maps[cur]);
     return cudaGetLastError();
 }
 
-// variant 0: two staged tiles, two CTAs per SM; variant 1: one staged tile,
-// three CTAs per SM
+// variant 0: two staged tiles per CTA, three CTAs per SM; variant 1: three
+// staged tiles per CTA, two CTAs per SM. Both use tiles of 4 rows.
+constexpr int tma_rows(int /*variant*/) { return 4; }
+constexpr int tma_ctas_per_sm(int variant) { return variant == 1 ? 2 : 3; }
+
 inline cudaError_t launch_update_tma(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
                                      int variant, cudaStream_t s)
 {
     if (variant == 1)
-        return d.noise_on ? launch_update_tma_variant<1, 3, true>(d, cur, t, maps, nsm, s)
-                          : launch_update_tma_variant<1, 3, false>(d, cur, t, maps, nsm, s);
-    return d.noise_on ? launch_update_tma_variant<2, 2, true>(d, cur, t, maps, nsm, s)
-                      : launch_update_tma_variant<2, 2, false>(d, cur, t, maps, nsm, s);
+        return d.noise_on ? launch_update_tma_variant<4, 3, 2, true>(d, cur, t, maps, nsm, s)
+                          : launch_update_tma_variant<4, 3, 2, false>(d, cur, t, maps, nsm, s);
+    return d.noise_on ? launch_update_tma_variant<4, 2, 3, true>(d, cur, t, maps, nsm, s)
+                      : launch_update_tma_variant<4, 2, 3, false>(d, cur, t, maps, nsm, s);
 }
 
 } // namespace lbm

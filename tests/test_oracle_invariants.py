@@ -166,6 +166,28 @@ def test_noise_statistics_match_eq4():
     assert np.abs(eta.mean(axis=1)).max() < 3 * np.sqrt(8 / 27) * sigma / 64
 
 
+def test_noise_uniforms_have_fourteen_bit_resolution():
+    """Eq. 4 with the 14-bit reading of the uniforms: eta_i - eta_j =
+    2 sigma (u_i - u_j) = 2 sigma (m_i - m_j) 2^-14 with m integer in
+    [0, 2^14). On a rest state every difference, scaled by 2^14 / (2 sigma),
+    is an integer of magnitude below 2^14, and the extremes come close to it.
+    A field of the wrong width, a dropped 1/2 or a wrong scale breaks one of
+    these."""
+    sigma = 2.0 ** -6  # exact in binary, so the scaled differences are exact
+    p = periodic(width=64, height=64, sigma=sigma)
+    s = OracleSim(p)
+    f0 = s.pops()
+    s.step(1)
+    eta = (s.pops() - f0).reshape(9, -1)
+    d = (eta[1:] - eta[0]) * (2.0 ** 14) / (2.0 * sigma)
+    assert np.abs(d - np.rint(d)).max() < 1e-6
+    assert np.abs(d).max() < 2 ** 14
+    assert np.abs(d).max() > 2 ** 14 * 0.99
+    # the lowest bit of each field is random too: half the differences are odd
+    odd = np.mod(np.rint(d), 2).astype(bool).mean()
+    assert 0.47 < odd < 0.53
+
+
 def test_literal_negative_fix_adds_twice_the_deficit():
     """App. A step 7 read literally: f_opp(i) += |f_i| and f_i = 0 adds 2|f_i|
     of mass (and keeps momentum). With growth off, the mass gained equals the
