@@ -46,10 +46,10 @@ uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
 
 struct Layout {
     int Wp, MW, hcap, ns_max;
-    long long P, kc_max;
+    long long P;
     int elem;
-    uint64_t off_f0, off_f1, off_mask, off_heights, off_rows0, off_sc, off_cflags, off_ckeys, off_gkl, off_gwpref,
-        off_hkeys, off_hcnt, off_hlist, off_evk, off_evc, off_rown, off_rk, off_roff, off_radd, total;
+    uint64_t off_f0, off_f1, off_mask, off_heights, off_rows0, off_sc, off_hkeys, off_hcnt, off_hlist, off_evk,
+        off_evc, off_rown, off_rk, off_roff, off_radd, off_bcnt, off_bucket, off_pl64, off_pl32, total;
 };
 
 Layout make_layout(const lbm_params_t &p)
@@ -73,7 +73,6 @@ Layout make_layout(const lbm_params_t &p)
     L.ns_max = (int)cap;
     L.hcap = 1;
     while (L.hcap < 2 * L.ns_max) L.hcap <<= 1;
-    L.kc_max = ((4LL * L.ns_max + 1024) + 31) & ~31LL;
     uint64_t o = 0;
     const uint64_t fbytes = (uint64_t)9 * (uint64_t)L.P * (uint64_t)L.elem;
     L.off_f0 = o; o = align256(o + fbytes);
@@ -82,19 +81,21 @@ Layout make_layout(const lbm_params_t &p)
     L.off_heights = o; o = align256(o + (uint64_t)p.width * 4u);
     L.off_rows0 = o; o = align256(o + (uint64_t)p.width * 4u);
     L.off_sc = o; o = align256(o + sizeof(DevScalars));
-    L.off_cflags = o; o = align256(o + (uint64_t)(L.kc_max / 32) * 4u);
-    L.off_ckeys = o; o = align256(o + (uint64_t)L.kc_max * 4u);
-    L.off_gkl = o; o = align256(o + (uint64_t)L.ns_max * 4u);
-    L.off_gwpref = o; o = align256(o + (uint64_t)(L.kc_max / 32) * 4u);
     L.off_hkeys = o; o = align256(o + (uint64_t)L.hcap * 4u);
     L.off_hcnt = o; o = align256(o + (uint64_t)L.hcap * 4u);
     L.off_hlist = o; o = align256(o + (uint64_t)L.ns_max * 4u);
-    L.off_evk = o; o = align256(o + (uint64_t)L.ns_max * 4u);
-    L.off_evc = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    // event lists of two consecutive steps (the planner selects one step ahead)
+    L.off_evk = o; o = align256(o + (uint64_t)L.ns_max * 8u);
+    L.off_evc = o; o = align256(o + (uint64_t)L.ns_max * 8u);
     L.off_rown = o; o = align256(o + (uint64_t)L.ns_max * 4u);
     L.off_rk = o; o = align256(o + (uint64_t)L.ns_max * 4u);
     L.off_roff = o; o = align256(o + (uint64_t)L.ns_max * 8u);
     L.off_radd = o; o = align256(o + (uint64_t)L.ns_max * 4u);
+    L.off_bcnt = o; o = align256(o + (uint64_t)kTmaMaxCtas * 4u);
+    L.off_bucket = o; o = align256(o + (uint64_t)kTmaMaxCtas * kBucketCap * 4u);
+    // planner partials: S1, S2, frozen mass (int64); top, low, two count buffers (int32)
+    L.off_pl64 = o; o = align256(o + (uint64_t)kPlanMaxBlocks * 3u * 8u);
+    L.off_pl32 = o; o = align256(o + (uint64_t)kPlanMaxBlocks * 4u * 4u);
     L.total = o;
     return L;
 }
@@ -294,10 +295,6 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     d.heights = (int32_t *)(base + L.off_heights);
     d.rows0 = (int32_t *)(base + L.off_rows0);
     d.sc = (DevScalars *)(base + L.off_sc);
-    d.cflags = (uint32_t *)(base + L.off_cflags);
-    d.ckeys = (uint32_t *)(base + L.off_ckeys);
-    d.gkl = (uint32_t *)(base + L.off_gkl);
-    d.gwpref = (int32_t *)(base + L.off_gwpref);
     d.hkeys = (uint32_t *)(base + L.off_hkeys);
     d.hcnt = (uint32_t *)(base + L.off_hcnt);
     d.hlist = (int32_t *)(base + L.off_hlist);
@@ -307,6 +304,14 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     d.rec_k = (int *)(base + L.off_rk);
     d.rec_off = (int *)(base + L.off_roff);
     d.rec_add = (float *)(base + L.off_radd);
+    d.bucket_cnt = (int *)(base + L.off_bcnt);
+    d.bucket = (int *)(base + L.off_bucket);
+    d.pl_s1 = (long long *)(base + L.off_pl64);
+    d.pl_s2 = d.pl_s1 + kPlanMaxBlocks;
+    d.pl_mass = d.pl_s2 + kPlanMaxBlocks;
+    d.pl_top = (int *)(base + L.off_pl32);
+    d.pl_low = d.pl_top + kPlanMaxBlocks;
+    d.pl_cnt = d.pl_low + kPlanMaxBlocks; // two buffers
     d.W = p->width;
     d.H = p->height;
     d.Wp = L.Wp;
@@ -314,7 +319,6 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     d.P = L.P;
     d.hcap = L.hcap;
     d.ns_max = L.ns_max;
-    d.kc_max = L.kc_max;
     d.omega = 1.0 / p->tau;
     d.cmu = 1.0 - p->mu;
     d.rho_c = p->rho_c;
@@ -352,7 +356,17 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     const int ncx = (p->width + s->kt->update_tile_x - 1) / s->kt->update_tile_x;
     const int g0 = nsm * (bps > 0 ? bps : 1);
     d.update_grid = g0 >= ncx ? (g0 / ncx) * ncx : ncx;
-    d.cand_grid = 2 * nsm;
+    // the planner's blocks must all be resident at once (cooperative launch)
+    const int pbs = s->kt->plan_blocks_per_sm();
+    // one block per SM at most, fewer when few divisions per step are possible
+    // (every grid barrier costs an arrival per block)
+    const int pg = (int)std::min<long long>(nsm, std::max<long long>(16, (L.ns_max + 2 * 512 - 1) / (2 * 512)));
+    d.plan_grid = pbs > 0 ? std::min(pg, kPlanMaxBlocks) : 0;
+    if (d.plan_grid < 1) {
+        if (s->own_arena) cudaFree(s->arena);
+        delete s;
+        return LBM_ERR_CUDA;
+    }
     s->use_tma = false;
     s->tma_grid = nsm;
     s->tma_variant = p->update_kernel == 3 ? 1 : 0;
@@ -394,7 +408,8 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
         if (e != cudaSuccess) { rc = cuda_fail(e); break; }
         if ((e = s->kt->fill(d, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
         if ((e = s->kt->scan(d, 0, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
-        if ((e = s->kt->observe(d, 0, 1, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
+        // observables of the initial state and the divisions of step 0
+        if ((e = s->kt->plan(d, 0, 0u, 1, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
         e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) { rc = cuda_fail(e); break; }
     } while (0);
@@ -410,16 +425,15 @@ int lbm_step(lbm_sim *s, int64_t nsteps)
 {
     if (!s || nsteps < 0) return LBM_ERR_INVALID_ARG;
     USE_DEVICE(s);
-    const bool grow = s->p.growth_mode != LBM_GROW_NONE;
     for (int64_t k = 0; k < nsteps; ++k) {
         const uint32_t t = (uint32_t)s->step;
-        if (grow) {
-            CK(s->kt->cand(s->d, s->cur, t, s->stream));
-            CK(s->kt->select(s->d, s->cur, t, s->stream));
-            s->launches += 2;
-        }
         const bool timed = s->timing && s->ev_used + 2 <= (int64_t)s->ev.size();
         if (timed) CK(cudaEventRecord(s->ev[s->ev_used], s->stream));
+        // App. A steps 1-7 with the divisions the planner selected for step t
+        if (!s->d.inject_in_update && s->p.growth_mode != LBM_GROW_NONE) {
+            CK(s->kt->inject(s->d, s->cur, t, s->stream));
+            s->launches += 1;
+        }
         if (s->use_tma)
             CK(launch_update_tma_f32(s->d, s->cur, t, s->maps, s->tma_grid, s->tma_variant, s->stream));
         else
@@ -428,7 +442,8 @@ int lbm_step(lbm_sim *s, int64_t nsteps)
             CK(cudaEventRecord(s->ev[s->ev_used + 1], s->stream));
             s->ev_used += 2;
         }
-        CK(s->kt->observe(s->d, s->cur ^ 1, 0, s->stream));
+        // observables of the new state; divisions of step t + 1
+        CK(s->kt->plan(s->d, s->cur ^ 1, t + 1u, 0, s->stream));
         s->launches += 2;
         s->cur ^= 1;
         ++s->step;
@@ -443,6 +458,15 @@ int lbm_sync(lbm_sim *s)
     CK(cudaStreamSynchronize(s->stream));
     CK(cudaGetLastError());
     return LBM_OK;
+}
+
+// Eq. 6 from the exact integer sums S1 = sum h, S2 = sum h^2 of the front
+// heights: hbar = S1 / W, w = sqrt(W S2 - S1^2) / W (IEEE double, the same
+// operations in the same order as the kernels' FP64 wall rule).
+static void eq6(long long S1, long long S2, int W, double *hbar, double *w)
+{
+    *hbar = (double)S1 / (double)W;
+    *w = std::sqrt((double)((long long)W * S2 - S1 * S1)) / (double)W;
 }
 
 static int read_scalars(lbm_sim *s, DevScalars *hs)
@@ -476,8 +500,7 @@ int lbm_stats(lbm_sim *s, lbm_stats_t *out)
     out->mass = (double)hs.mass_fix * kFixInv;
     out->quiescent_mass = (double)hs.quiescent_fix * kFixInv;
     out->carry = hs.carry;
-    out->hbar = hs.hbar;
-    out->w = hs.w;
+    eq6(hs.S1, hs.S2, s->p.width, &out->hbar, &out->w);
     out->clip_mass = hs.clip_mass;
     out->y_r = hs.y_r;
     out->H_top = hs.H_top;
@@ -500,15 +523,16 @@ int lbm_front_heights(lbm_sim *s, int32_t *h_host, double *hbar, double *w)
 {
     if (!s) return LBM_ERR_INVALID_ARG;
     USE_DEVICE(s);
-    // only the returned values cross the bus: W int32 and two doubles
-    double hw[2];
+    // only W int32 and the two exact Eq. 6 sums (int64) cross the bus
+    long long sums[2];
     if (h_host)
         CK(cudaMemcpyAsync(h_host, s->d.heights, sizeof(int32_t) * s->p.width, cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(&hw[0], &s->d.sc->hbar, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(&hw[1], &s->d.sc->w, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(sums, &s->d.sc->S1, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
-    if (hbar) *hbar = hw[0];
-    if (w) *w = hw[1];
+    double hb, wv;
+    eq6(sums[0], sums[1], s->p.width, &hb, &wv);
+    if (hbar) *hbar = hb;
+    if (w) *w = wv;
     return LBM_OK;
 }
 
@@ -592,7 +616,8 @@ int lbm_set_populations(lbm_sim *s, const double *f_host)
     CK(cudaMemcpyAsync(&sc->maxmass_accum, &minus1, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(&sc->status, &zeroi, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     CK(s->kt->scan(s->d, s->cur, s->stream));
-    CK(s->kt->observe(s->d, s->cur, 1, s->stream));
+    // observe this state again and redo the selection of the next step
+    CK(s->kt->plan(s->d, s->cur, (uint32_t)s->step, 1, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return LBM_OK;
 }
@@ -617,27 +642,29 @@ int lbm_last_events(lbm_sim *s, int64_t *node, int32_t *pair, int32_t *count, in
     DevScalars hs;
     int rc = read_scalars(s, &hs);
     if (rc != LBM_OK) return rc;
-    const int ne = s->p.growth_mode == LBM_GROW_NONE ? 0 : hs.n_events;
-    *n = ne;
-    if (ne == 0 || cap == 0) return LBM_OK;
-    if (!node || !pair || !count) return LBM_ERR_INVALID_ARG;
+    const int ne = s->p.growth_mode == LBM_GROW_NONE || s->step == 0 ? 0 : hs.n_events;
+    *n = 0;
+    if (ne == 0) return LBM_OK;
+    if (cap > 0 && (!node || !pair || !count)) return LBM_ERR_INVALID_ARG;
     std::vector<uint32_t> vk(ne);
     std::vector<int32_t> vc(ne);
-    CK(cudaMemcpyAsync(vk.data(), s->d.ev_key, ne * sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(vc.data(), s->d.ev_count, ne * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    // the list of the latest step (lists alternate by step parity), one entry
+    // per draw rank; repeats of an earlier rank's (node, pair) carry count 0
+    const size_t off = (size_t)((s->step - 1) & 1) * (size_t)s->L.ns_max;
+    CK(cudaMemcpyAsync(vk.data(), s->d.ev_key + off, ne * sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(vc.data(), s->d.ev_count + off, ne * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     std::vector<long long> vn(ne);
     std::vector<int32_t> vp(ne);
+    std::vector<int> ord;
     for (int i = 0; i < ne; ++i) {
         vn[i] = (long long)key_y(vk[i]) * s->p.width + key_x(vk[i]);
         vp[i] = key_pair(vk[i]);
+        if (vc[i] > 0) ord.push_back(i);
     }
-    std::vector<int> ord(ne);
-    for (int i = 0; i < ne; ++i) ord[i] = i;
-    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
-        return vn[a] * 4 + vp[a] < vn[b] * 4 + vp[b];
-    });
-    const int64_t m = std::min<int64_t>(cap, ne);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return vn[a] * 4 + vp[a] < vn[b] * 4 + vp[b]; });
+    *n = (int64_t)ord.size();
+    const int64_t m = std::min<int64_t>(cap, (int64_t)ord.size());
     for (int64_t i = 0; i < m; ++i) {
         node[i] = vn[ord[i]];
         pair[i] = vp[ord[i]];

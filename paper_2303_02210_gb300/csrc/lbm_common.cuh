@@ -102,7 +102,7 @@ struct DevScalars {
     int y_r, y_copy, y_hi, H_top, hmin;
     int maxmass_accum; // highest row holding mass, accumulated by the update kernel
     int status;
-    int n_events;      // distinct (node, pair) events of the latest step
+    int n_events;      // event-list entries (draw ranks) of the latest step
     // accumulators of the multi-block observer (reset by its last block)
     long long S1_acc, S2_acc;
     int top_acc, low_acc;
@@ -118,6 +118,23 @@ struct DevScalars {
     double acc_ratio;     // candidates per division seen last time
     int plan_ylo;         // first candidate row
     int plan_nwin_zero;   // n_s > 0 but no candidate row
+    // the fused planner (k_plan) selects the divisions of the next step at the
+    // end of the current one; their statistics are committed by the following
+    // k_plan, after the update that applies them has run
+    long long pend_req;   // n_s of the selected step
+    long long pend_acc;   // divisions selected (<= n_s)
+    long long pend_cand;  // candidates drawn up to the n_s-th accept (or the cap)
+    double pend_carry;    // carried fraction after that step's n_s
+    int pend_nev;         // list entries of the selection (its draw ranks)
+    int pend_starved;     // the selection came up short
+    int rec_n;            // division records of the next update
+    int pad1;
+    long long sel_kstop;  // candidate index + 1 of the n_s-th accept
+    unsigned long long bar_ctr; // grid-barrier arrivals of k_plan (grows by the grid size per barrier)
+    // k_plan scratch: n_s from the mass before any freezing, computed by one
+    // block while the others scan the front
+    long long spec_req;
+    double spec_carry, spec_kcf;
 };
 
 // Everything a kernel needs to know about one simulation.
@@ -129,20 +146,16 @@ struct SimDev {
     int32_t *heights;    // h(x), W entries
     DevScalars *sc;
     // proliferation planner
-    uint32_t *cflags;    // accept bit per candidate of the parallel pass
-    uint32_t *ckeys;     // node*4 + pair per candidate of the parallel pass
-    uint32_t *gkl;       // accepted keys in draw order (large n_s)
-    int32_t *gwpref;     // accepted count before each word of cflags (large n_s)
-    uint32_t *hkeys;     // open-addressing table for large n_s, key = node*4 + pair
+    uint32_t *hkeys;     // open-addressing table of the selected (node, pair), EMPTY when unused
     uint32_t *hcnt;
-    int32_t *hlist;      // slots in insertion order
-    uint32_t *ev_key;    // divisions of the latest step: packed (node, pair) keys
-    int32_t *ev_count;   // and how often each was drawn
+    int32_t *hlist;      // per selected division (draw rank): its table slot if it was the
+                         // first draw of its (node, pair), else -1
+    uint32_t *ev_key;    // divisions of step t at [(t & 1) ns_max, ...) by draw rank: packed (node, pair)
+    int32_t *ev_count;   // and how often it was drawn (0 for repeats of an earlier rank)
     int32_t *rows0;      // initial occupied rows per column
     int W, H, Wp, MW;
     long long P;         // plane stride in elements (Wp * H)
     int hcap, ns_max;
-    long long kc_max;    // capacity of cflags in candidates
     // model constants (all derived on the host once, in double)
     double omega, cmu, rho_c, rho_cell, half_cell, growth_rate, rho0, sigma;
     double rho_init, rho_jitter, wall_min_gap, wall_w_factor;
@@ -158,11 +171,16 @@ struct SimDev {
     int *rec_k;           // the tile's index among that CTA's tiles,
     int *rec_off;         // the two pre-stream slots' offsets in the staged box,
     float *rec_add;       // and count * rho_cell / 2
+    int *bucket_cnt;      // divisions per CTA of the TMA-staged update (kTmaMaxCtas)
+    int *bucket;          // their record indices, kBucketCap per CTA
+    // per-block partials of the fused planner (kPlanMaxBlocks each)
+    long long *pl_s1, *pl_s2, *pl_mass;
+    int *pl_top, *pl_low, *pl_cnt;
+    int plan_grid;        // blocks of the fused planner (all co-resident)
     // the same constants rounded to float once on the host, so that no kernel
     // evaluates double arithmetic per node (the FP64 pipe is narrow)
     float f_rho_c, f_omega, f_cmu, f_om1, f_ow0, f_ow1, f_ow5, f_two_sigma;
     int update_grid;     // persistent grid of the update kernel
-    int cand_grid;       // grid of the candidate pass
 };
 
 // Launchers of one precision (implemented once per storage type).
@@ -171,11 +189,13 @@ struct KernelTable {
     cudaError_t (*fill)(const SimDev &, cudaStream_t);
     cudaError_t (*ghosts)(const SimDev &, cudaStream_t);
     cudaError_t (*scan)(const SimDev &, int cur, cudaStream_t);
-    cudaError_t (*observe)(const SimDev &, int cur, int init, cudaStream_t);
-    cudaError_t (*cand)(const SimDev &, int cur, uint32_t t, cudaStream_t);
-    cudaError_t (*select)(const SimDev &, int cur, uint32_t t, cudaStream_t);
+    // fused planner: observe copy `cur`, select the divisions of step tn
+    cudaError_t (*plan)(const SimDev &, int cur, uint32_t tn, int init, cudaStream_t);
+    // the selected divisions of step t into copy `cur` (update kernels without staging)
+    cudaError_t (*inject)(const SimDev &, int cur, uint32_t t, cudaStream_t);
     cudaError_t (*update)(const SimDev &, int cur, uint32_t t, cudaStream_t);
     cudaError_t (*fields)(const SimDev &, int cur, double *rho, double *ux, double *uy, cudaStream_t);
+    int (*plan_blocks_per_sm)();
     int (*update_blocks_per_sm)();
     int update_tile_x; // columns per block of the update kernel
 };
@@ -199,5 +219,7 @@ int launch_update_tma_rows(int variant);
 constexpr int kXO = 4;
 constexpr int kTmaBoxX = 128;
 constexpr int kTmaMaxCtas = 1024; // the reciprocal above is exact for tile < 2^22
+constexpr int kBucketCap = 64;     // division records listed per update CTA (more: full scan)
+constexpr int kPlanMaxBlocks = 1024;
 
 } // namespace lbm

@@ -1,5 +1,5 @@
 // FP32 storage and arithmetic: the fast path.
-#include "lbm_kernels.cuh"
+#include "lbm_launch.cuh"
 #include "lbm_update_tma.cuh"
 
 namespace lbm {

@@ -2,22 +2,19 @@
 // storage type R (float: fast path; double: debug path, compiled without FMA
 // contraction so that it rounds exactly like the FP64 CPU oracle).
 //
-// One time step (App. A of Killeen et al., arXiv 2303.02210) is four launches:
-//   k_cand,   proliferation (Sec. II, Eq. 5): counter-based candidate draws,
-//   k_select  acceptance on the streamed density rho*, first-n_s selection in
-//             draw order, merge of repeated sites and injection of
-//             count * rho_cell/2 into the two pre-stream slots that stream into
-//             each chosen (node, pair).
+// One time step (App. A of Killeen et al., arXiv 2303.02210) is two launches:
 //   k_update  the fused pass over the active window: pull streaming with
 //             half-way bounce-back walls, moments (Eq. 1), friction u*, f^SS
 //             (Eq. 3), BGK relaxation or reversal below rho_c (Eq. 2 and the
 //             two-step bounce-back of Sec. II), Philox noise (Eq. 4), the
 //             negative-population fix (App. A step 7), the store, the occupancy
 //             bitmask (one warp ballot per 32 nodes) and the exact fixed-point
-//             mass / top-mass-row reductions. Persistent grid.
-//   k_observe front heights from the bitmask (warp ballots), Eq. 6 sums,
-//             the rear-wall rule (App. A, last paragraph), the active mass,
-//             the next window and the next step's proliferation plan.
+//             mass / top-mass-row reductions (k_update_tma, lbm_update_tma.cuh,
+//             is the TMA-staged FP32 form);
+//   k_plan    (lbm_plan.cuh) the observables of the new state and the
+//             proliferation of the next step: front heights, Eq. 6, the rear
+//             wall, n_s, candidate draws, acceptance, selection and merge,
+//             injection (or records for k_update_tma).
 #pragma once
 
 #include "lbm_common.cuh"
@@ -474,7 +471,7 @@ __device__ __forceinline__ R fix_negative(R *fo, int mode)
 
 // ===========================================================================
 // Fused update of the active window (App. A steps 1, 2, 4-7; the injection of
-// step 3 was already added to the pre-stream slots by k_select).
+// step 3 was already added to the pre-stream slots by k_plan).
 template <typename R, int TPB, int NR>
 __global__ void __launch_bounds__(TPB) k_update(SimDev d, int cur, uint32_t t)
 {
@@ -598,18 +595,11 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d, int cur, uint32_t t)
 }
 
 // ===========================================================================
-// Proliferation (App. A step 3; Sec. II and Eq. 5), planned by the observer
-// at the end of the previous step, then two launches:
-//   k_cand   all SMs evaluate the first plan_kc candidates of the counter
-//            stream (Philox (k, t, 1, sim)): node, pair, rho* gathered from
-//            the 9 pre-stream slots, acceptance by the growth mode; one accept
-//            bit per candidate (warp ballot).
-//   k_select one block: block scan of the accept bits, the first n_s accepted
-//            candidates in draw order (more are drawn here if the parallel
-//            pass came up short), repeated (node, pair) merged in a hash table
-//            (shared memory up to SEL_SMEM_EVENTS divisions), and the
-//            injection of count * rho_cell/2 into the two pre-stream slots of
-//            each (node, pair).
+// Proliferation helpers (App. A step 3; Sec. II and Eq. 5), used by the fused
+// planner: counter-based candidate draws (Philox (k, t, 1, sim)), the
+// streamed density rho* gathered from the nine pre-stream slots, the
+// open-addressing table that merges repeated (node, pair) draws, and the
+// per-division records of the TMA-staged update.
 
 template <typename R>
 __device__ __forceinline__ R rho_star(const SimDev &d, const R *f, int y_r, int x, int y)
@@ -635,58 +625,18 @@ __device__ __forceinline__ Candidate draw_candidate(const SimDev &d, long long k
                                                     unsigned long long nwin)
 {
     const u32x4 r = philox4x32_10(u32x4{(uint32_t)k, t, STREAM_PROLIF, d.sim}, d.pk);
-    const unsigned long long idx = ((unsigned long long)r.x * nwin) >> 32;
-    const long long node = (long long)ylo * d.W + (long long)idx;
+    // node = ylo W + floor(r.x nwin / 2^32); nwin <= W H < 2^30, so the offset
+    // in the window splits into row and column in 32-bit arithmetic
+    const uint32_t idx = (uint32_t)(((unsigned long long)r.x * nwin) >> 32);
     Candidate c;
-    c.y = (int)(node / d.W);
-    c.x = (int)(node % d.W);
+    c.y = ylo + (int)(idx / (uint32_t)d.W);
+    c.x = (int)(idx % (uint32_t)d.W);
     c.pair = (int)(r.y >> 30);
     c.u = r.z;
     return c;
 }
 
-template <typename R>
-__device__ __forceinline__ bool accept(const SimDev &d, const R *f, int y_r, const Candidate &c)
-{
-    const R rs = rho_star<R>(d, f, y_r, c.x, c.y);
-    switch (d.growth_mode) {
-    case GROW_BULK:
-    case GROW_BAND: return rs >= rho_c_of<R>(d);
-    case GROW_EDGE: return rs >= rho_c_of<R>(d) && (d.heights[c.x] - c.y) <= d.edge_depth;
-    case GROW_DENSITY: return (double)rs > d.rho_c && u01(c.u) < 1.0 - (double)rs / d.rho0; // Eq. 5
-    default: return false;
-    }
-}
-
-constexpr int CAND_TPB = 256;
-
-template <typename R>
-__global__ void __launch_bounds__(CAND_TPB) k_cand(SimDev d, int cur, uint32_t t)
-{
-    const DevScalars *sc = d.sc;
-    const long long ns = sc->plan_ns, kc = sc->plan_kc;
-    if (ns <= 0) return;
-    const R *f = (const R *)d.f[cur];
-    const int y_r = sc->y_r, ylo = sc->plan_ylo;
-    const unsigned long long nwin = sc->plan_nwin;
-    const long long stride = (long long)gridDim.x * CAND_TPB;
-    for (long long k = (long long)blockIdx.x * CAND_TPB + threadIdx.x; k < kc; k += stride) {
-        const Candidate c = draw_candidate(d, k, t, ylo, nwin);
-        const bool ok = accept<R>(d, f, y_r, c);
-        const unsigned b = __ballot_sync(0xffffffffu, ok);
-        if ((threadIdx.x & 31) == 0) d.cflags[k >> 5] = b;
-        d.ckeys[k] = pack_key(c.x, c.y, c.pair);
-    }
-}
-
-constexpr int SEL_TPB = 1024;
-constexpr int SEL_SMEM_SLOTS = 16384;  // hash slots in shared memory
-constexpr int SEL_SMEM_EVENTS = 8192;  // divisions per step handled in shared memory
-constexpr int SEL_SMEM_WORDS = 4096;   // accept-bit words handled in shared memory
-constexpr size_t SEL_SMEM_BYTES =
-    (size_t)SEL_SMEM_SLOTS * 8 + (size_t)SEL_SMEM_EVENTS * 8 + (size_t)SEL_SMEM_WORDS * 4;
 constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;
-constexpr int SEL_BATCH = 4; // independent memory accesses a selector thread keeps in flight
 
 struct EventTable {
     uint32_t *keys;
@@ -708,49 +658,6 @@ __device__ __forceinline__ int table_insert(const EventTable &tb, uint32_t key)
         slot = (slot + 1u) & tb.mask;
     }
     return -1;
-}
-
-// Appends the new slots of a warp to the table's list with one atomic per
-// warp. Every lane of the warp calls it (newslot < 0: nothing to append).
-__device__ __forceinline__ void table_append(const EventTable &tb, int newslot, int *nlist)
-{
-    const unsigned m = __ballot_sync(0xffffffffu, newslot >= 0);
-    if (!m) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(nlist, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (newslot >= 0) tb.list[base + __popc(m & ((1u << lane) - 1u))] = newslot;
-}
-
-// exclusive block scan of one int per thread; returns the prefix, *total the sum
-__device__ __forceinline__ long long block_exscan(long long v, long long *total, long long *s_w)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const long long a = lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0;
-        long long b = a;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long u = __shfl_up_sync(0xffffffffu, b, o);
-            if (lane >= o) b += u;
-        }
-        s_w[lane] = b - a;
-        if (lane == 31) s_w[32] = b;
-    }
-    __syncthreads();
-    const long long r = s_w[warp] + incl - v;
-    *total = s_w[32];
-    __syncthreads();
-    return r;
 }
 
 // For the TMA-staged update: where division e goes. Its node's tile (of
@@ -783,391 +690,6 @@ __device__ __forceinline__ void division_record(const SimDev &d, int e, uint32_t
     d.rec_add[e] = (float)((double)cnt * d.half_cell);
 }
 
-template <typename R>
-__global__ void __launch_bounds__(SEL_TPB) k_select(SimDev d, int cur, uint32_t t)
-{
-    extern __shared__ unsigned char smem[];
-    __shared__ long long s_w[33];
-    __shared__ long long s_kstop, s_acc;
-    __shared__ int s_nlist;
-    R *f = (R *)d.f[cur];
-    DevScalars *sc = d.sc;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long ns = sc->plan_ns, kc = sc->plan_kc;
-    const long long cap = 64 * ns + 1024;
-    const long long nw = kc >> 5;
-    const int y_r = sc->y_r, ylo = sc->plan_ylo;
-    const unsigned long long nwin = sc->plan_nwin;
-    const bool small = ns <= SEL_SMEM_EVENTS && nw <= SEL_SMEM_WORDS;
-    EventTable tb;
-    uint32_t *kl;  // accepted keys in draw order
-    int32_t *wpref; // accepted candidates before each accept-bit word
-    if (small) {
-        tb.keys = (uint32_t *)smem;
-        tb.cnt = tb.keys + SEL_SMEM_SLOTS;
-        tb.list = (int32_t *)(tb.cnt + SEL_SMEM_SLOTS);
-        kl = (uint32_t *)(tb.list + SEL_SMEM_EVENTS);
-        wpref = (int32_t *)(kl + SEL_SMEM_EVENTS);
-        tb.mask = SEL_SMEM_SLOTS - 1;
-        for (int i = tid; i < SEL_SMEM_SLOTS; i += SEL_TPB) {
-            tb.keys[i] = EMPTY_KEY;
-            tb.cnt[i] = 0u;
-        }
-    } else {
-        tb.keys = d.hkeys;
-        tb.cnt = d.hcnt;
-        tb.list = d.hlist;
-        tb.mask = (unsigned)d.hcap - 1u;
-        kl = d.gkl;
-        wpref = d.gwpref;
-    }
-    if (tid == 0) {
-        s_kstop = 0;
-        s_acc = 0;
-        s_nlist = 0;
-    }
-    __syncthreads();
-    if (ns > 0) {
-        // (1) accepted count before each word of the parallel pass
-        const long long wpt = (nw + SEL_TPB - 1) / SEL_TPB;
-        const long long w0 = (long long)tid * wpt, w1 = w0 + wpt < nw ? w0 + wpt : nw;
-        long long cnt = 0;
-        for (long long w = w0; w < w1; ++w) cnt += __popc(d.cflags[w]);
-        long long total;
-        long long run = block_exscan(cnt, &total, s_w);
-        for (long long w = w0; w < w1; ++w) {
-            wpref[w] = (int32_t)run;
-            run += __popc(d.cflags[w]);
-        }
-        __syncthreads();
-        // (2) the first n_s accepted keys in draw order: one warp per word,
-        // one lane per candidate; each warp loads SEL_BATCH words and their
-        // keys before using any of them
-        const uint32_t *__restrict__ cfl = d.cflags;
-        const uint32_t *__restrict__ ckk = d.ckeys;
-        for (long long w0b = warp; w0b < nw; w0b += (long long)(SEL_TPB / 32) * SEL_BATCH) {
-            uint32_t word[SEL_BATCH], key[SEL_BATCH];
-#pragma unroll
-            for (int j = 0; j < SEL_BATCH; ++j) {
-                const long long w = w0b + (long long)j * (SEL_TPB / 32);
-                word[j] = w < nw ? cfl[w] : 0u;
-                key[j] = ((word[j] >> lane) & 1u) ? ckk[(w << 5) + lane] : 0u;
-            }
-#pragma unroll
-            for (int j = 0; j < SEL_BATCH; ++j) {
-                const long long w = w0b + (long long)j * (SEL_TPB / 32);
-                if ((word[j] >> lane) & 1u) {
-                    const long long r = wpref[w] + __popc(word[j] & ((1u << lane) - 1u));
-                    if (r < ns) {
-                        kl[r] = key[j];
-                        if (r == ns - 1) s_kstop = (w << 5) + lane + 1;
-                    }
-                }
-            }
-        }
-        if (tid == 0) s_acc = total;
-        __syncthreads();
-        // (3) merge repeated (node, pair) draws
-        const long long nins = total < ns ? total : ns;
-        for (long long r0 = 0; r0 < nins; r0 += SEL_TPB) {
-            const long long r = r0 + tid;
-            table_append(tb, r < nins ? table_insert(tb, kl[r]) : -1, &s_nlist);
-        }
-        __syncthreads();
-        // (4) more draws if the parallel pass accepted fewer than n_s
-        for (long long base = kc; s_acc < ns && base < cap; base += SEL_TPB) {
-            const long long k = base + tid;
-            bool ok = false;
-            Candidate c;
-            if (k < cap) {
-                c = draw_candidate(d, k, t, ylo, nwin);
-                ok = accept<R>(d, f, y_r, c);
-            }
-            long long tot;
-            const long long r = s_acc + block_exscan(ok ? 1 : 0, &tot, s_w);
-            int ins = -1;
-            if (ok && r < ns) {
-                ins = table_insert(tb, pack_key(c.x, c.y, c.pair));
-                if (r == ns - 1) s_kstop = k + 1;
-            }
-            table_append(tb, ins, &s_nlist);
-            __syncthreads();
-            if (tid == 0) s_acc += tot;
-            __syncthreads();
-        }
-    }
-    __syncthreads();
-    // (3) inject count * rho_cell/2 into the two pre-stream slots of each
-    // (node, pair), or leave that to the update kernel (the TMA-staged one adds
-    // them to its staged tiles). Distinct (node, pair) never share a slot (each
-    // slot streams into exactly one direction of one node), so a thread gathers
-    // all the slots of its batch before it stores any.
-    const int nlist = s_nlist;
-    for (int e0 = tid; e0 < nlist; e0 += SEL_TPB * SEL_BATCH) {
-        long long sl[2 * SEL_BATCH];
-        R val[2 * SEL_BATCH], add[SEL_BATCH];
-#pragma unroll
-        for (int j = 0; j < SEL_BATCH; ++j) {
-            const int e = e0 + j * SEL_TPB;
-            if (e < nlist) {
-                const int slot = tb.list[e];
-                const uint32_t key = tb.keys[slot];
-                const int cnt = (int)tb.cnt[slot];
-                if (!d.inject_in_update) {
-                    const int x = key_x(key), y = key_y(key), p = key_pair(key);
-                    add[j] = (R)((double)cnt * d.half_cell);
-                    sl[2 * j] = pull_slot(d, y_r, x, y, pair_a(p));
-                    sl[2 * j + 1] = pull_slot(d, y_r, x, y, pair_b(p));
-                    val[2 * j] = f[sl[2 * j]];
-                    val[2 * j + 1] = f[sl[2 * j + 1]];
-                }
-                d.ev_key[e] = key;
-                d.ev_count[e] = cnt;
-                if (d.inject_in_update) division_record<R>(d, e, key, cnt, y_r);
-                if (!small) {
-                    tb.keys[slot] = EMPTY_KEY;
-                    tb.cnt[slot] = 0u;
-                }
-            }
-        }
-        if (!d.inject_in_update) {
-#pragma unroll
-            for (int j = 0; j < SEL_BATCH; ++j) {
-                if (e0 + j * SEL_TPB < nlist) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const long long o = sl[2 * j + h];
-                        const R v = val[2 * j + h] + add[j];
-                        f[o] = v;
-                        // the ghost copy of an edge column (read by the TMA-staged update)
-                        const int xc = (int)((o % d.P) % d.Wp);
-                        if (xc == 0) f[o + d.W] = v;
-                        if (xc == d.W - 1) f[o - d.W] = v;
-                    }
-                }
-            }
-        }
-    }
-    if (tid == 0) {
-        // commit the plan made at the end of the previous step
-        sc->ns_last = sc->plan_req;
-        sc->ns_total += sc->plan_req;
-        sc->carry = sc->plan_carry;
-        const long long acc = s_acc < ns ? s_acc : ns;
-        sc->div_total += acc;
-        sc->events_last = acc;
-        sc->n_events = nlist;
-        if (sc->plan_nwin_zero) {
-            sc->starved_steps += 1;
-            sc->status |= ST_STARVED;
-            sc->cand_last = 0;
-        } else if (ns > 0 && s_acc < ns) {
-            sc->starved_steps += 1;
-            sc->status |= ST_STARVED;
-            sc->cand_last = cap;
-        } else {
-            sc->cand_last = ns > 0 ? s_kstop : 0;
-        }
-        if (ns > 0 && s_acc >= ns) sc->acc_ratio = (double)s_kstop / (double)ns;
-    }
-}
-
-// ===========================================================================
-// Observables after an update (or of the initial state when init != 0).
-// Many blocks, one warp per 32-column word of the occupancy mask: front heights
-// h(x) = 1 + highest occupied row (32 rows per pass, one ballot per column),
-// partial Eq. 6 sums by atomics. The last block to finish then does the serial
-// part: Eq. 6 width, the rear-wall rule (App. A, last paragraph), the mass of
-// rows it freezes, the active mass, the next window, and the proliferation
-// plan of the next step (n_s from M and the carried fraction, Sec. II).
-constexpr int OBS_TPB = 256;
-constexpr int OBS_WARPS = OBS_TPB / 32;
-
-template <typename R>
-__global__ void __launch_bounds__(OBS_TPB) k_observe(SimDev d, int cur, int init)
-{
-    DevScalars *sc = d.sc;
-    const R *f = (const R *)d.f[cur];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    __shared__ long long s_a[OBS_WARPS], s_b[OBS_WARPS];
-    __shared__ int s_top[OBS_WARPS], s_low[OBS_WARPS];
-    __shared__ int s_last, s_new_yr;
-    const int y_r = sc->y_r;
-    const int maxmass = sc->maxmass_accum;
-    int ytop = maxmass > y_r - 1 ? maxmass : y_r - 1;
-    if (ytop > d.H - 1) ytop = d.H - 1;
-
-    long long S1 = 0, S2 = 0;
-    int top = 0, low = 0x7fffffff;
-    for (int m = blockIdx.x * OBS_WARPS + warp; m < d.MW; m += gridDim.x * OBS_WARPS) {
-        const int x = m * 32 + lane;
-        unsigned pending = __ballot_sync(0xffffffffu, x < d.W);
-        int h = 0;
-        for (int yb = ytop; yb >= 0 && pending; yb -= 32) {
-            const int y = yb - lane;
-            const unsigned word = y >= 0 ? d.mask[(long long)y * d.MW + m] : 0u;
-            unsigned any = word;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(0xffffffffu, any, o);
-            unsigned todo = pending & any;
-            while (todo) {
-                const int c = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const unsigned b = __ballot_sync(0xffffffffu, (word >> c) & 1u);
-                if (lane == c) h = yb - (__ffs(b) - 1) + 1;
-                pending &= ~(1u << c);
-            }
-        }
-        if (x < d.W) {
-            d.heights[x] = h;
-            S1 += h;
-            S2 += (long long)h * h;
-            top = max(top, h);
-            low = min(low, h);
-        }
-    }
-    S1 = warp_sum_ll(S1);
-    S2 = warp_sum_ll(S2);
-    top = warp_max_i(top);
-    low = warp_min_i(low);
-    if (lane == 0) {
-        s_a[warp] = S1;
-        s_b[warp] = S2;
-        s_top[warp] = top;
-        s_low[warp] = low;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        long long a = 0, b = 0;
-        int tp = 0, lw = 0x7fffffff;
-        for (int i = 0; i < OBS_WARPS; ++i) {
-            a += s_a[i];
-            b += s_b[i];
-            tp = max(tp, s_top[i]);
-            lw = min(lw, s_low[i]);
-        }
-        atomicAdd((unsigned long long *)&sc->S1_acc, (unsigned long long)a);
-        atomicAdd((unsigned long long *)&sc->S2_acc, (unsigned long long)b);
-        atomicMax(&sc->top_acc, tp);
-        atomicMin(&sc->low_acc, lw);
-        __threadfence();
-        const unsigned ticket = atomicAdd(&sc->obs_done, 1u);
-        s_last = ticket == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    volatile DevScalars *vs = sc;
-    if (tid == 0) {
-        const long long a = vs->S1_acc, b = vs->S2_acc;
-        sc->S1 = a;
-        sc->S2 = b;
-        sc->H_top = vs->top_acc;
-        sc->hmin = vs->low_acc;
-        // Eq. 6: w = sqrt(W S2 - S1^2) / W
-        sc->hbar = (double)a / (double)d.W;
-        sc->w = sqrt((double)((long long)d.W * b - a * a)) / (double)d.W;
-        // the rear wall is kept behind the front at all times, the initial
-        // state included
-        int nyr = y_r;
-        if (d.wall_mode == 1 && !d.y_periodic) {
-            double gap = d.wall_min_gap;
-            const double wg = d.wall_w_factor * sc->w;
-            if (wg > gap) gap = wg;
-            double c = floor(sc->hbar - gap);
-            if (c > (double)(d.H - 1)) c = (double)(d.H - 1);
-            const int cand = (int)c;
-            if (cand > nyr) nyr = cand;
-        }
-        s_new_yr = nyr;
-    }
-    __syncthreads();
-    const int nyr = s_new_yr;
-    // mass of the rows the wall freezes now
-    long long fm = 0;
-    if (nyr > y_r) {
-        const long long n = (long long)(nyr - y_r) * d.W;
-        for (long long k = tid; k < n; k += OBS_TPB) {
-            const int y = y_r + (int)(k / d.W), x = (int)(k % d.W);
-            const long long o = (long long)y * d.Wp + x;
-            R r = f[o];
-#pragma unroll
-            for (int i = 1; i < NQ; ++i) r = r + f[i * d.P + o];
-            fm += fix24<R>(r);
-        }
-    }
-    fm = warp_sum_ll(fm);
-    if (lane == 0) s_a[warp] = fm;
-    __syncthreads();
-    if (tid == 0) {
-        long long frozen = 0;
-        for (int i = 0; i < OBS_WARPS; ++i) frozen += s_a[i];
-        const long long acc = (long long)sc->mass_accum;
-        sc->mass_fix = acc - frozen;
-        sc->quiescent_fix += frozen;
-        int yhi;
-        if (d.y_periodic) {
-            yhi = d.H;
-        } else {
-            yhi = maxmass + 2 < d.H ? maxmass + 2 : d.H;
-            if (!init && sc->y_hi > yhi) yhi = sc->y_hi; // the window never shrinks
-        }
-        if (!init) {
-            sc->node_updates += (long long)d.W * (long long)(sc->y_hi > y_r ? sc->y_hi - y_r : 0);
-            sc->step += 1;
-        }
-        sc->y_copy = y_r;
-        sc->y_r = nyr;
-        sc->y_hi = yhi;
-        if (maxmass >= d.H - 1) sc->status |= ST_FRONT_AT_TOP;
-        sc->mass_accum = 0ull;
-        sc->maxmass_accum = -1;
-        sc->S1_acc = 0;
-        sc->S2_acc = 0;
-        sc->top_acc = 0;
-        sc->low_acc = 0x7fffffff;
-        sc->obs_done = 0u;
-        // proliferation plan of the next step (Sec. II): n_s sites from the
-        // active mass and the carried fraction, drawn from the active portion
-        // restricted by the growth mode
-        if (d.growth_mode != GROW_NONE) {
-            const double mass = (double)sc->mass_fix * kFixInv;
-            const double xns = d.growth_rate * mass / d.rho_cell + sc->carry;
-            const double fl = floor(xns);
-            long long ns = (long long)fl;
-            sc->plan_req = ns;
-            sc->plan_carry = xns - fl;
-            int ylo = nyr, yhi_c = sc->H_top;
-            if (d.growth_mode == GROW_EDGE) {
-                const int e = sc->hmin - d.edge_depth;
-                if (e > ylo) ylo = e;
-            } else if (d.growth_mode == GROW_BAND) {
-                if (nyr + d.band_rows < yhi_c) yhi_c = nyr + d.band_rows;
-            }
-            const unsigned long long nwin =
-                yhi_c > ylo ? (unsigned long long)(yhi_c - ylo) * (unsigned long long)d.W : 0ull;
-            if (ns > d.ns_max) {
-                sc->status |= ST_CAPACITY;
-                ns = 0;
-            }
-            sc->plan_nwin_zero = (ns > 0 && nwin == 0) ? 1 : 0;
-            if (nwin == 0) ns = 0;
-            sc->plan_ns = ns;
-            sc->plan_ylo = ylo;
-            sc->plan_nwin = nwin;
-            // candidates for the parallel pass: n_s times the ratio seen last
-            // step, with a margin; the selector draws more if it falls short
-            double ratio = sc->acc_ratio > 1.0 ? sc->acc_ratio : 1.0;
-            long long kc = (long long)ceil((double)ns * ratio * 1.15) + 64;
-            const long long cap = 64 * ns + 1024;
-            if (kc > cap) kc = cap;
-            kc = (kc + 31) & ~31ll;
-            if (kc > d.kc_max) kc = d.kc_max;
-            sc->plan_kc = ns > 0 ? kc : 0;
-        }
-    }
-}
-
 // rho and u of copy `cur` into device arrays of W*H doubles (Eq. 1).
 template <typename R>
 __global__ void k_fields(SimDev d, int cur, double *rho, double *ux, double *uy)
@@ -1190,83 +712,6 @@ __global__ void k_fields(SimDev d, int cur, double *rho, double *ux, double *uy)
         ux[k] = r != 0.0 ? jx / r : 0.0;
         uy[k] = r != 0.0 ? jy / r : 0.0;
     }
-}
-
-// ---------------------------------------------------------------------------
-// Launchers of one storage type.
-template <typename R>
-struct Launch {
-    static constexpr int UPD_TPB = 128;
-    static constexpr int UPD_NR = sizeof(R) == 4 ? 2 : 1;
-
-    static cudaError_t fill(const SimDev &d, cudaStream_t s)
-    {
-        k_fill<R><<<4 * 152, 256, 0, s>>>(d);
-        return cudaGetLastError();
-    }
-    static cudaError_t ghosts(const SimDev &d, cudaStream_t s)
-    {
-        k_ghosts<R><<<152, 256, 0, s>>>(d);
-        return cudaGetLastError();
-    }
-    static cudaError_t scan(const SimDev &d, int cur, cudaStream_t s)
-    {
-        k_scan<R><<<4 * 152, 256, 0, s>>>(d, cur);
-        return cudaGetLastError();
-    }
-    static cudaError_t observe(const SimDev &d, int cur, int init, cudaStream_t s)
-    {
-        int g = (d.MW + OBS_WARPS - 1) / OBS_WARPS;
-        if (g > 4 * 152) g = 4 * 152;
-        k_observe<R><<<g, OBS_TPB, 0, s>>>(d, cur, init);
-        return cudaGetLastError();
-    }
-    static cudaError_t cand(const SimDev &d, int cur, uint32_t t, cudaStream_t s)
-    {
-        k_cand<R><<<d.cand_grid, CAND_TPB, 0, s>>>(d, cur, t);
-        return cudaGetLastError();
-    }
-    static cudaError_t select(const SimDev &d, int cur, uint32_t t, cudaStream_t s)
-    {
-        // the shared-memory opt-in is per device
-        static bool attr[64] = {};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        if (dev >= 64 || !attr[dev]) {
-            e = cudaFuncSetAttribute(k_select<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEL_SMEM_BYTES);
-            if (e != cudaSuccess) return e;
-            if (dev < 64) attr[dev] = true;
-        }
-        k_select<R><<<1, SEL_TPB, SEL_SMEM_BYTES, s>>>(d, cur, t);
-        return cudaGetLastError();
-    }
-    static cudaError_t update(const SimDev &d, int cur, uint32_t t, cudaStream_t s)
-    {
-        k_update<R, UPD_TPB, UPD_NR><<<d.update_grid, UPD_TPB, 0, s>>>(d, cur, t);
-        return cudaGetLastError();
-    }
-    static cudaError_t fields(const SimDev &d, int cur, double *rho, double *ux, double *uy, cudaStream_t s)
-    {
-        k_fields<R><<<4 * 152, 256, 0, s>>>(d, cur, rho, ux, uy);
-        return cudaGetLastError();
-    }
-    static int update_blocks_per_sm()
-    {
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<R, UPD_TPB, UPD_NR>, UPD_TPB, 0) != cudaSuccess)
-            return 0;
-        return n;
-    }
-};
-
-template <typename R>
-constexpr KernelTable make_table()
-{
-    return KernelTable{(int)sizeof(R),        &Launch<R>::fill,   &Launch<R>::ghosts, &Launch<R>::scan,
-                       &Launch<R>::observe,   &Launch<R>::cand,   &Launch<R>::select,
-                       &Launch<R>::update,    &Launch<R>::fields, &Launch<R>::update_blocks_per_sm,
-                       Launch<R>::UPD_TPB};
 }
 
 } // namespace lbm

@@ -1,0 +1,591 @@
+// Fused planner: everything between two update launches in one cooperative
+// kernel (all blocks co-resident, separated by grid barriers whose waits are
+// bounded):
+//
+//   A  front heights h(x) = 1 + highest occupied row of the bitmask (one warp
+//      per 32-column word, one ballot per column), per-block Eq. 6 sums; one
+//      block meanwhile works out n_s = floor(g M / rho_cell + carry) (Sec. II)
+//      from the mass the update accumulated;
+//   B  (every block, redundantly) the rear-wall rule (App. A, last paragraph)
+//      with Eq. 6, the mass of the rows it freezes (n_s again if any), and
+//      the candidate window of the growth mode;
+//   C  the first candidates of the counter stream Philox (k, t, 1, sim), each
+//      block a contiguous range: node, pair, rho* gathered from the nine
+//      pre-stream slots, acceptance by the growth mode (Eq. 5 for density-
+//      dependent growth), the block's accepted count;
+//   D  draw ranks of the accepted candidates (block prefix over the other
+//      blocks' counts); the first n_s are counted in an open-addressing table
+//      keyed by (node, pair) and listed by rank (more candidates are drawn in
+//      rounds if the first pass came up short);
+//   E  per rank: the count of its (node, pair) if it was the first draw of
+//      it (0 for repeats), and for the TMA-staged update one record in the
+//      bucket of the CTA that owns its tile (that kernel adds count *
+//      rho_cell/2 to the staged pre-stream slots; for the other update kernels
+//      k_inject adds it to the stored populations right before the update);
+//      the table is emptied again.
+//
+// Block 0 then writes the observables, commits the statistics of the step
+// that just ran (its divisions were selected by the previous k_plan) and
+// keeps the new selection's statistics pending.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+constexpr int PLAN_NT = 512;
+constexpr int PLAN_WARPS = PLAN_NT / 32;
+constexpr int PLAN_R = 8; // candidates per thread in the first pass
+// a stalled barrier is given up after about two seconds at 2 GHz
+constexpr long long PLAN_WAIT_BUDGET = 4000000000ll;
+
+// Grid barrier on a monotone arrival counter: a block's thread 0 adds one and
+// waits until the counter reaches the next multiple of the grid size (the
+// counter persists across launches, which all use the same grid). The wait
+// is bounded: on timeout ST_TIMEOUT is raised and later barriers no longer wait.
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void plan_grid_sync(DevScalars *sc, int *s_dead)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long g = gridDim.x;
+        const unsigned long long old = atomicAdd(&sc->bar_ctr, 1ull);
+        const unsigned long long target = (old / g + 1ull) * g;
+        if (!*s_dead) {
+            const long long t0 = clock64();
+            while (ld_acquire_u64(&sc->bar_ctr) < target) {
+                if (clock64() - t0 > PLAN_WAIT_BUDGET) {
+                    *s_dead = 1;
+                    atomicOr(&sc->status, ST_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Block-wide sums / extrema of one value per thread (result on every thread).
+__device__ __forceinline__ long long plan_block_sum(long long v, long long *s_ll)
+{
+    v = warp_sum_ll(v);
+    if ((threadIdx.x & 31) == 0) s_ll[threadIdx.x >> 5] = v;
+    __syncthreads();
+    long long r = 0;
+    for (int i = 0; i < PLAN_WARPS; ++i) r += s_ll[i];
+    __syncthreads();
+    return r;
+}
+
+// Exclusive block scan of one count per thread; *total gets the block sum.
+__device__ __forceinline__ int plan_block_exscan(int v, int *total, int *s_i)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_i[warp] = incl;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int i = 0; i < PLAN_WARPS; ++i) {
+        const int c = s_i[i];
+        before += i < warp ? c : 0;
+        all += c;
+    }
+    __syncthreads();
+    *total = all;
+    return before + incl - v;
+}
+
+// The division of draw rank `rank`: counted in the table keyed by (node,
+// pair); the rank's list entry is the table slot if this draw was the first of
+// its (node, pair), else -1.
+__device__ __forceinline__ void plan_select(const SimDev &d, uint32_t key, int rank, size_t buf)
+{
+    EventTable tb;
+    tb.keys = d.hkeys;
+    tb.cnt = d.hcnt;
+    tb.list = d.hlist;
+    tb.mask = (unsigned)d.hcap - 1u;
+    const int slot = table_insert(tb, key);
+    d.hlist[rank] = slot;
+    d.ev_key[buf + rank] = key;
+}
+
+// Acceptance of a candidate (as `accept`, with the heights of this launch
+// read from L2: other blocks wrote them before the last grid barrier).
+template <typename R>
+__device__ __forceinline__ bool plan_accept(const SimDev &d, const R *f, int y_r, const Candidate &c)
+{
+    const R rs = rho_star<R>(d, f, y_r, c.x, c.y);
+    switch (d.growth_mode) {
+    case GROW_BULK:
+    case GROW_BAND: return rs >= rho_c_of<R>(d);
+    case GROW_EDGE: return rs >= rho_c_of<R>(d) && (__ldcg(&d.heights[c.x]) - c.y) <= d.edge_depth;
+    case GROW_DENSITY: return (double)rs > d.rho_c && u01(c.u) < 1.0 - (double)rs / d.rho0; // Eq. 5
+    default: return false;
+    }
+}
+
+// n_s = floor(g M / rho_cell + carry) (Sec. II) from the fixed-point active
+// mass, the carried fraction after it, and the first-pass candidate count
+// before clipping, ceil(n_s ratio 1.15) + 64 (FP64, as the oracle).
+__device__ __forceinline__ void plan_ns(const SimDev &d, long long mass_fix, double carry_in, double ratio_in,
+                                        long long *ns_req, double *carry_out, double *kcf)
+{
+    const double mass = (double)mass_fix * kFixInv;
+    const double xns = d.growth_rate * mass / d.rho_cell + carry_in;
+    const double fl = floor(xns);
+    *ns_req = (long long)fl;
+    *carry_out = xns - fl;
+    const double ratio = ratio_in > 1.0 ? ratio_in : 1.0;
+    *kcf = ceil((double)*ns_req * ratio * 1.15) + 64.0;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int cur, uint32_t tn, int init)
+{
+    DevScalars *sc = d.sc;
+    R *f = (R *)d.f[cur];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = (int)gridDim.x, blk = (int)blockIdx.x;
+    __shared__ long long s_ll[PLAN_WARPS];
+    __shared__ int s_i[PLAN_WARPS], s_i2[PLAN_WARPS];
+    __shared__ int s_dead;
+    __shared__ unsigned long long s_kstop;
+    __shared__ long long s_req;
+    __shared__ double s_carry, s_kcf;
+
+    // ---- the state left by the update that just ran (read before any block writes)
+    const int y_r = sc->y_r, y_hi_old = sc->y_hi;
+    const int maxmass = sc->maxmass_accum;
+    const long long mass_acc = (long long)sc->mass_accum;
+    const double carry_in = init ? sc->carry : sc->pend_carry;
+    const double ratio_in = sc->acc_ratio;
+    const bool grow = d.growth_mode != GROW_NONE;
+    if (tid == 0) {
+        s_dead = 0;
+        s_kstop = 0ull;
+    }
+    if (d.inject_in_update)
+        for (int i = blk * PLAN_NT + tid; i < d.upd_ctas; i += G * PLAN_NT) d.bucket_cnt[i] = 0;
+    // n_s if no row is frozen now (almost always): the last block, which has
+    // the least front to scan, works it out in FP64 while the others scan
+    if (grow && blk == G - 1 && tid == 0) {
+        long long req;
+        double cy, kcf;
+        plan_ns(d, mass_acc, carry_in, ratio_in, &req, &cy, &kcf);
+        sc->spec_req = req;
+        sc->spec_carry = cy;
+        sc->spec_kcf = kcf;
+    }
+
+    // ---- A: front heights, per-block Eq. 6 sums
+    int ytop = maxmass > y_r - 1 ? maxmass : y_r - 1;
+    if (ytop > d.H - 1) ytop = d.H - 1;
+    long long S1 = 0, S2 = 0;
+    int top = 0, low = 0x7fffffff;
+    for (int m = blk * PLAN_WARPS + warp; m < d.MW; m += G * PLAN_WARPS) {
+        const int x = m * 32 + lane;
+        unsigned pending = __ballot_sync(0xffffffffu, x < d.W);
+        int h = 0;
+        for (int yb = ytop; yb >= 0 && pending; yb -= 32) {
+            const int y = yb - lane;
+            const unsigned word = y >= 0 ? d.mask[(long long)y * d.MW + m] : 0u;
+            unsigned any = word;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(0xffffffffu, any, o);
+            unsigned todo = pending & any;
+            while (todo) {
+                const int c = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const unsigned bb = __ballot_sync(0xffffffffu, (word >> c) & 1u);
+                if (lane == c) h = yb - (__ffs(bb) - 1) + 1;
+                pending &= ~(1u << c);
+            }
+        }
+        if (x < d.W) {
+            d.heights[x] = h;
+            S1 += h;
+            S2 += (long long)h * h;
+            top = max(top, h);
+            low = min(low, h);
+        }
+    }
+    {
+        const long long a = plan_block_sum(S1, s_ll);
+        const long long b2 = plan_block_sum(S2, s_ll);
+        top = warp_max_i(top);
+        low = warp_min_i(low);
+        if (lane == 0) {
+            s_i[warp] = top;
+            s_i2[warp] = low;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int tp = 0, lw = 0x7fffffff;
+            for (int i = 0; i < PLAN_WARPS; ++i) {
+                tp = max(tp, s_i[i]);
+                lw = min(lw, s_i2[i]);
+            }
+            d.pl_s1[blk] = a;
+            d.pl_s2[blk] = b2;
+            d.pl_top[blk] = tp;
+            d.pl_low[blk] = lw;
+        }
+    }
+    plan_grid_sync(sc, &s_dead);
+
+    // ---- B: Eq. 6 sums, the rear wall, the active mass and the next plan
+    // (every block computes the same values from the same partials)
+    const bool advancing = d.wall_mode == 1 && !d.y_periodic;
+    const bool need_s = blk == 0 || advancing;
+    long long S1a = 0, S2a = 0;
+    int topa = 0, lowa = 0x7fffffff;
+    for (int i = tid; i < G; i += PLAN_NT) {
+        if (need_s) {
+            S1a += __ldcg(&d.pl_s1[i]);
+            S2a += __ldcg(&d.pl_s2[i]);
+        }
+        topa = max(topa, __ldcg(&d.pl_top[i]));
+        lowa = min(lowa, __ldcg(&d.pl_low[i]));
+    }
+    if (tid == 0 && grow) {
+        s_req = __ldcg(&sc->spec_req);
+        s_carry = __ldcg(&sc->spec_carry);
+        s_kcf = __ldcg(&sc->spec_kcf);
+    }
+    if (need_s) { // uniform
+        S1a = plan_block_sum(S1a, s_ll);
+        S2a = plan_block_sum(S2a, s_ll);
+    }
+    topa = warp_max_i(topa);
+    lowa = warp_min_i(lowa);
+    if (lane == 0) {
+        s_i[warp] = topa;
+        s_i2[warp] = lowa;
+    }
+    __syncthreads();
+    topa = 0;
+    lowa = 0x7fffffff;
+    for (int i = 0; i < PLAN_WARPS; ++i) {
+        topa = max(topa, s_i[i]);
+        lowa = min(lowa, s_i2[i]);
+    }
+    // the rear wall is kept behind the front at all times, the initial state
+    // included: y_r <- max(y_r, floor(hbar - max(gap, 10 w))), Eq. 6 for w.
+    // A float estimate first; the FP64 rule (as the oracle) only decides when
+    // the wall can move
+    int nyr = y_r;
+    if (advancing) {
+        const long long var = (long long)d.W * S2a - S1a * S1a;
+        const float hf = (float)S1a / (float)d.W;
+        const float wf = sqrtf((float)var) / (float)d.W;
+        const float cf = hf - fmaxf((float)d.wall_min_gap, (float)d.wall_w_factor * wf);
+        if (cf > (float)y_r + 0.9f) {
+            const double hbar = (double)S1a / (double)d.W;
+            const double wdt = sqrt((double)var) / (double)d.W;
+            double gap = d.wall_min_gap;
+            const double wg = d.wall_w_factor * wdt;
+            if (wg > gap) gap = wg;
+            double c = floor(hbar - gap);
+            if (c > (double)(d.H - 1)) c = (double)(d.H - 1);
+            const int cand = (int)c;
+            if (cand > nyr) nyr = cand;
+        }
+    }
+    // mass of the rows the wall freezes now
+    long long frozen = 0;
+    if (nyr > y_r) { // uniform across the grid
+        const long long n = (long long)(nyr - y_r) * d.W;
+        long long fm = 0;
+        for (long long k = (long long)blk * PLAN_NT + tid; k < n; k += (long long)G * PLAN_NT) {
+            const int y = y_r + (int)(k / d.W), x = (int)(k % d.W);
+            const long long o = (long long)y * d.Wp + x;
+            R r = f[o];
+#pragma unroll
+            for (int i = 1; i < NQ; ++i) r = r + f[i * d.P + o];
+            fm += fix24<R>(r);
+        }
+        fm = plan_block_sum(fm, s_ll);
+        if (tid == 0) d.pl_mass[blk] = fm;
+        plan_grid_sync(sc, &s_dead);
+        long long a = 0;
+        for (int i = tid; i < G; i += PLAN_NT) a += __ldcg(&d.pl_mass[i]);
+        frozen = plan_block_sum(a, s_ll);
+        if (tid == 0 && grow) {
+            long long req;
+            double cy, kcf;
+            plan_ns(d, mass_acc - frozen, carry_in, ratio_in, &req, &cy, &kcf);
+            s_req = req;
+            s_carry = cy;
+            s_kcf = kcf;
+        }
+    }
+    __syncthreads();
+    const long long mass_fix = mass_acc - frozen;
+    // proliferation plan (Sec. II): n_s sites, drawn from the active portion
+    // restricted by the growth mode
+    long long ns_req = 0, ns = 0, kc = 0;
+    double carry_out = carry_in;
+    int ylo = nyr, capacity = 0, nwin_zero = 0;
+    unsigned long long nwin = 0ull;
+    if (grow) {
+        ns_req = s_req;
+        carry_out = s_carry;
+        ns = ns_req;
+        int yhi_c = topa;
+        if (d.growth_mode == GROW_EDGE) {
+            const int e = lowa - d.edge_depth;
+            if (e > ylo) ylo = e;
+        } else if (d.growth_mode == GROW_BAND) {
+            if (nyr + d.band_rows < yhi_c) yhi_c = nyr + d.band_rows;
+        }
+        nwin = yhi_c > ylo ? (unsigned long long)(yhi_c - ylo) * (unsigned long long)d.W : 0ull;
+        if (ns > d.ns_max) {
+            capacity = 1;
+            ns = 0;
+        }
+        nwin_zero = (ns > 0 && nwin == 0) ? 1 : 0;
+        if (nwin == 0) ns = 0;
+        // candidates of the first pass: n_s times the ratio seen last step,
+        // with a margin; more are drawn below if it falls short
+        kc = (long long)s_kcf;
+        const long long cap = 64 * ns + 1024;
+        if (kc > cap) kc = cap;
+        const long long kmax = (long long)G * PLAN_NT * PLAN_R;
+        if (kc > kmax) kc = kmax;
+        if (ns <= 0) kc = 0;
+    }
+    const size_t buf = (size_t)(tn & 1u) * (size_t)d.ns_max; // event list of step tn
+
+    // ---- C/D: candidates in draw order, the first n_s accepted, merged
+    long long acc = 0; // accepted candidates so far (all blocks agree)
+    if (ns > 0) {      // uniform
+        const long long cap = 64 * ns + 1024;
+        // first pass: block blk draws candidates [blk C, blk C + C); in round
+        // i thread tid takes candidate blk C + i PLAN_NT + tid, so that the
+        // gathers of a round are all in flight together
+        const long long C = (kc + G - 1) / G;
+        const int rounds = (int)((C + PLAN_NT - 1) / PLAN_NT); // <= PLAN_R (kc <= kmax)
+        uint32_t keys[PLAN_R];
+        unsigned accb = 0;
+#pragma unroll
+        for (int i = 0; i < PLAN_R; ++i) {
+            const long long j = (long long)i * PLAN_NT + tid;
+            const long long k = (long long)blk * C + j;
+            keys[i] = 0u;
+            if (i < rounds && j < C && k < kc) {
+                const Candidate c = draw_candidate(d, k, tn, ylo, nwin);
+                if (plan_accept<R>(d, f, nyr, c)) {
+                    accb |= 1u << i;
+                    keys[i] = pack_key(c.x, c.y, c.pair);
+                }
+            }
+        }
+        // accepted before each of this thread's candidates within the block (draw order)
+        int pre[PLAN_R];
+        int tot_b = 0;
+#pragma unroll
+        for (int i = 0; i < PLAN_R; ++i) {
+            pre[i] = 0;
+            if (i < rounds) { // uniform
+                int t_i;
+                pre[i] = tot_b + plan_block_exscan((int)((accb >> i) & 1u), &t_i, s_i);
+                tot_b += t_i;
+            }
+        }
+        if (tid == 0) d.pl_cnt[blk] = tot_b;
+        plan_grid_sync(sc, &s_dead);
+        long long before = 0, total = 0;
+        for (int i = tid; i < G; i += PLAN_NT) {
+            const long long c = __ldcg(&d.pl_cnt[i]);
+            total += c;
+            before += i < blk ? c : 0;
+        }
+        before = plan_block_sum(before, s_ll);
+        total = plan_block_sum(total, s_ll);
+#pragma unroll
+        for (int i = 0; i < PLAN_R; ++i) {
+            if (i < rounds && ((accb >> i) & 1u)) {
+                const long long rank = before + pre[i];
+                if (rank == ns - 1) s_kstop = (unsigned long long)(blk * C + (long long)i * PLAN_NT + tid + 1);
+                if (rank < ns) plan_select(d, keys[i], (int)rank, buf);
+            }
+        }
+        acc = total;
+        // more draws, a grid-wide round at a time, while short of n_s
+        long long base = kc;
+        int round = 1;
+        while (acc < ns && base < cap) { // uniform
+            const long long k = base + (long long)blk * PLAN_NT + tid;
+            bool a = false;
+            uint32_t key = 0u;
+            if (k < cap) {
+                const Candidate c = draw_candidate(d, k, tn, ylo, nwin);
+                a = plan_accept<R>(d, f, nyr, c);
+                key = pack_key(c.x, c.y, c.pair);
+            }
+            int tot_r;
+            const int pr = plan_block_exscan(a ? 1 : 0, &tot_r, s_i);
+            int *cnt = d.pl_cnt + (round & 1) * kPlanMaxBlocks;
+            if (tid == 0) cnt[blk] = tot_r;
+            plan_grid_sync(sc, &s_dead);
+            long long bf = 0, tt = 0;
+            for (int i = tid; i < G; i += PLAN_NT) {
+                const long long c = __ldcg(&cnt[i]);
+                tt += c;
+                bf += i < blk ? c : 0;
+            }
+            bf = plan_block_sum(bf, s_ll);
+            tt = plan_block_sum(tt, s_ll);
+            const long long rank = acc + bf + pr;
+            if (a && rank == ns - 1) s_kstop = (unsigned long long)(k + 1);
+            if (a && rank < ns) plan_select(d, key, (int)rank, buf);
+            acc += tt;
+            base += (long long)G * PLAN_NT;
+            ++round;
+        }
+        __syncthreads();
+        if (tid == 0 && s_kstop) sc->sel_kstop = (long long)s_kstop;
+    }
+    plan_grid_sync(sc, &s_dead);
+
+    // ---- E: counts of the merged divisions, per-CTA records, table emptied
+    const int nsel = (int)(acc < ns ? acc : ns); // selected divisions (draw ranks)
+    for (int r = blk * PLAN_NT + tid; r < nsel; r += G * PLAN_NT) {
+        const int slot = __ldcg(&d.hlist[r]);
+        if (slot < 0) { // a repeat of an earlier rank's (node, pair)
+            d.ev_count[buf + r] = 0;
+            if (d.inject_in_update) d.rec_owner[r] = -1;
+            continue;
+        }
+        const uint32_t key = d.ev_key[buf + r];
+        const int cnt = (int)__ldcg(&d.hcnt[slot]);
+        d.ev_count[buf + r] = cnt;
+        if (d.inject_in_update) {
+            division_record<R>(d, r, key, cnt, nyr);
+            const int owner = d.rec_owner[r];
+            const int at = atomicAdd(&d.bucket_cnt[owner], 1);
+            if (at < kBucketCap) d.bucket[owner * kBucketCap + at] = r;
+        }
+        d.hkeys[slot] = EMPTY_KEY;
+        d.hcnt[slot] = 0u;
+    }
+
+    // ---- block 0: commit the step that ran, the observables, the new selection
+    if (blk == 0 && tid == 0) {
+        if (!init) {
+            sc->ns_last = sc->pend_req;
+            sc->ns_total += sc->pend_req;
+            sc->carry = sc->pend_carry;
+            sc->div_total += sc->pend_acc;
+            sc->events_last = sc->pend_acc;
+            sc->n_events = sc->pend_nev;
+            sc->cand_last = sc->pend_cand;
+            if (sc->pend_starved) {
+                sc->starved_steps += 1;
+                sc->status |= ST_STARVED;
+            }
+            sc->node_updates += (long long)d.W * (long long)(y_hi_old > y_r ? y_hi_old - y_r : 0);
+            sc->step += 1;
+        }
+        sc->S1 = S1a;
+        sc->S2 = S2a;
+        sc->H_top = topa;
+        sc->hmin = lowa;
+        sc->mass_fix = mass_fix;
+        sc->quiescent_fix += frozen;
+        int yhi;
+        if (d.y_periodic) {
+            yhi = d.H;
+        } else {
+            yhi = maxmass + 2 < d.H ? maxmass + 2 : d.H;
+            if (!init && y_hi_old > yhi) yhi = y_hi_old; // the window never shrinks
+        }
+        sc->y_copy = y_r;
+        sc->y_r = nyr;
+        sc->y_hi = yhi;
+        if (maxmass >= d.H - 1) sc->status |= ST_FRONT_AT_TOP;
+        if (capacity) sc->status |= ST_CAPACITY;
+        sc->mass_accum = 0ull;
+        sc->maxmass_accum = -1;
+        // the selection for step tn, applied by the next update
+        const long long cap = 64 * ns + 1024;
+        const long long kstop = sc->sel_kstop;
+        sc->pend_req = ns_req;
+        sc->pend_carry = carry_out;
+        sc->pend_acc = nsel;
+        sc->pend_nev = nsel;
+        sc->pend_starved = (nwin_zero || (ns > 0 && acc < ns)) ? 1 : 0;
+        sc->pend_cand = nwin_zero ? 0 : (ns > 0 && acc < ns ? cap : (ns > 0 ? kstop : 0));
+        if (ns > 0 && acc >= ns) sc->acc_ratio = (double)kstop / (double)ns;
+        sc->plan_req = ns_req;
+        sc->plan_ns = ns;
+        sc->plan_kc = kc;
+        sc->plan_ylo = ylo;
+        sc->plan_nwin = nwin;
+        sc->plan_carry = carry_out;
+        sc->rec_n = nsel;
+    }
+}
+
+// App. A step 3 for the update kernels that read the populations from global
+// memory: count * rho_cell/2 into the two pre-stream slots of each selected
+// (node, pair) of step t, right before the update of step t. Distinct
+// (node, pair) never share a slot (each slot streams into exactly one
+// direction of one node).
+template <typename R>
+__global__ void k_inject(SimDev d, int cur, uint32_t t)
+{
+    R *f = (R *)d.f[cur];
+    const int n = d.sc->rec_n, y_r = d.sc->y_r;
+    const size_t buf = (size_t)(t & 1u) * (size_t)d.ns_max;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int cnt = d.ev_count[buf + e];
+        if (cnt == 0) continue; // a repeat, counted at its first rank
+        const uint32_t key = d.ev_key[buf + e];
+        const int x = key_x(key), y = key_y(key), p = key_pair(key);
+        const R add = (R)((double)cnt * d.half_cell);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long o = pull_slot(d, y_r, x, y, h == 0 ? pair_a(p) : pair_b(p));
+            const R v = f[o] + add;
+            f[o] = v;
+            // the ghost copy of an edge column (read by the TMA-staged update)
+            const int xc = (int)((o % d.P) % d.Wp);
+            if (xc == 0) f[o + d.W] = v;
+            if (xc == d.W - 1) f[o - d.W] = v;
+        }
+    }
+}
+
+template <typename R>
+cudaError_t launch_plan(const SimDev &d, int cur, uint32_t tn, int init, cudaStream_t s)
+{
+    void *args[] = {(void *)&d, (void *)&cur, (void *)&tn, (void *)&init};
+    return cudaLaunchCooperativeKernel((const void *)k_plan<R>, dim3((unsigned)d.plan_grid), dim3(PLAN_NT), args, 0,
+                                       s);
+}
+
+template <typename R>
+int plan_blocks_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plan<R>, PLAN_NT, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+} // namespace lbm

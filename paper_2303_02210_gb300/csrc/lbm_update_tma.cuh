@@ -34,6 +34,7 @@ constexpr int TMA_LX = TMA_TX + 8; // staged columns x0 - 4 .. x0 + 131
 // per tile); tiles flagged per CTA.
 constexpr int TMA_EV_CAP = 512;
 constexpr int TMA_KFLAG_WORDS = 32;
+static_assert(kBucketCap <= TMA_EV_CAP, "a full bucket fits in shared memory");
 // a stalled copy is given up after about two seconds at 2 GHz
 constexpr long long TMA_WAIT_BUDGET = 4000000000ll;
 static_assert(kXO % 4 == 0, "tile boxes start on 16-byte boundaries");
@@ -179,31 +180,47 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
     if (tid == 0)
         while (issued < STAGES && issued < count) issue();
 
-    // App. A step 3 for this CTA: the selector listed, per division, the CTA
-    // that owns its node's tile, the tile's local index, the offsets of the
-    // two pre-stream slots in the staged box and the amount; keep ours.
-    const int nev_all = d.inject_in_update ? d.sc->n_events : 0;
-    constexpr int EV_BATCH = 8; // owner words a thread loads before it looks at any
-    for (int eb = 0; eb < nev_all; eb += NT * EV_BATCH) {
-        int own[EV_BATCH];
-#pragma unroll
-        for (int j = 0; j < EV_BATCH; ++j) {
-            const int e = eb + j * NT + tid;
-            own[j] = e < nev_all ? d.rec_owner[e] : -1;
+    // App. A step 3 for this CTA: the planner wrote one record per division
+    // (the tile's local index among its owner's tiles, the offsets of the two
+    // pre-stream slots in the staged box, the amount) and listed the records
+    // of each owner CTA in its bucket; read ours (all records if the bucket
+    // overflowed).
+    const int nev_all = d.inject_in_update ? d.sc->rec_n : 0;
+    const int mine = nev_all > 0 ? d.bucket_cnt[blockIdx.x] : 0;
+    if (mine <= kBucketCap) {
+        for (int j = tid; j < mine; j += NT) {
+            const int e = d.bucket[blockIdx.x * kBucketCap + j];
+            const int k = d.rec_k[e];
+            ev_k[j] = k;
+            ev_off[2 * j] = d.rec_off[2 * e];
+            ev_off[2 * j + 1] = d.rec_off[2 * e + 1];
+            ev_add[j] = d.rec_add[e];
+            if (k < 32 * TMA_KFLAG_WORDS) atomicOr(&kflag[k >> 5], 1u << (k & 31));
         }
+        if (tid == 0) s_nev = mine;
+    } else {
+        constexpr int EV_BATCH = 8; // owner words a thread loads before it looks at any
+        for (int eb = 0; eb < nev_all; eb += NT * EV_BATCH) {
+            int own[EV_BATCH];
 #pragma unroll
-        for (int j = 0; j < EV_BATCH; ++j) {
-            const int e = eb + j * NT + tid;
-            if (own[j] == (int)blockIdx.x) {
-                const int at = atomicAdd(&s_nev, 1);
-                const int k = d.rec_k[e];
-                if (at < TMA_EV_CAP) {
-                    ev_k[at] = k;
-                    ev_off[2 * at] = d.rec_off[2 * e];
-                    ev_off[2 * at + 1] = d.rec_off[2 * e + 1];
-                    ev_add[at] = d.rec_add[e];
+            for (int j = 0; j < EV_BATCH; ++j) {
+                const int e = eb + j * NT + tid;
+                own[j] = e < nev_all ? d.rec_owner[e] : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < EV_BATCH; ++j) {
+                const int e = eb + j * NT + tid;
+                if (own[j] == (int)blockIdx.x) {
+                    const int at = atomicAdd(&s_nev, 1);
+                    const int k = d.rec_k[e];
+                    if (at < TMA_EV_CAP) {
+                        ev_k[at] = k;
+                        ev_off[2 * at] = d.rec_off[2 * e];
+                        ev_off[2 * at + 1] = d.rec_off[2 * e + 1];
+                        ev_add[at] = d.rec_add[e];
+                    }
+                    if (k < 32 * TMA_KFLAG_WORDS) atomicOr(&kflag[k >> 5], 1u << (k & 31));
                 }
-                if (k < 32 * TMA_KFLAG_WORDS) atomicOr(&kflag[k >> 5], 1u << (k & 31));
             }
         }
     }
@@ -267,6 +284,9 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
             else
                 pull2<PLANE, true, true>(b, ga, gb);
         }
+        // the stage may be refilled (by the async proxy) once every warp has
+        // arrived: order this thread's shared-memory reads before that
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         if (tid == 0 && issued < count) {

@@ -220,3 +220,27 @@ def test_fp32_tma_kernel_bit_exact_with_plain_kernel(name, kernel):
         assert np.array_equal(a.pops(), b.pops())
         assert np.array_equal(a.mask(), b.mask())
         assert np.array_equal(a.heights(), b.heights())
+
+
+def test_fp32_tma_repeatable_on_reused_memory():
+    """The TMA-staged update refills a shared-memory stage as soon as every
+    warp holds its values; a refill that overtakes a pending shared-memory
+    read would corrupt one warp's nodes now and then, depending on timing and
+    on what the reused device memory held before. Eight fresh simulations of
+    the full-size workload, three back-to-back steps each, must all agree bit
+    for bit with the plain-load kernel."""
+    import torch
+    from paper_2303_02210_gb300.lbm import Simulation
+    p = wl.lattice_edge(seed=1)
+    a = Simulation(p, precision="fp32", update_kernel="plain")
+    a.step(3)
+    ref = a.pops()
+    del a
+    for trial in range(8):
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        b = Simulation(p, precision="fp32", update_kernel="tma")
+        b.step(3)
+        fb = b.pops()
+        del b
+        assert np.array_equal(fb, ref), f"trial {trial}: {int((fb != ref).sum())} populations differ"
