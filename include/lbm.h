@@ -184,6 +184,12 @@ int lbm_clear_status(lbm_sim *sim);
  * the nodes they updated. Enabling again resets the record. */
 int lbm_timing_enable(lbm_sim *sim, int64_t max_launches);
 int lbm_timing_read(lbm_sim *sim, int64_t *launches, double *total_ms, int64_t *nodes);
+/* Times only one update launch in every `stride` (>= 1, else
+ * LBM_ERR_INVALID_ARG) while timing is enabled: an event pair around a launch
+ * keeps it from overlapping the preceding planner kernel, so sparse sampling
+ * leaves the measured run close to an untimed one. `nodes` from
+ * lbm_timing_read still counts every step since lbm_timing_enable. Default 1. */
+int lbm_timing_stride(lbm_sim *sim, int64_t stride);
 
 /* Bytes of population traffic one node update moves in the fused update
  * kernel (9 loads + 9 stores of the storage type). */

@@ -200,6 +200,7 @@ struct lbm_sim {
     int64_t ev_used;
     bool timing;
     int64_t timing_nodes0;
+    int64_t timing_stride, timing_count;
 };
 
 extern "C" {
@@ -270,6 +271,8 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     s->launches = 0;
     s->ev_used = 0;
     s->timing = false;
+    s->timing_stride = 1;
+    s->timing_count = 0;
     if (arena) {
         if (arena_bytes < s->L.total || ((uintptr_t)arena & 255u) != 0) {
             delete s;
@@ -427,7 +430,8 @@ int lbm_step(lbm_sim *s, int64_t nsteps)
     USE_DEVICE(s);
     for (int64_t k = 0; k < nsteps; ++k) {
         const uint32_t t = (uint32_t)s->step;
-        const bool timed = s->timing && s->ev_used + 2 <= (int64_t)s->ev.size();
+        const bool timed = s->timing && (s->timing_count++ % s->timing_stride) == 0 &&
+                           s->ev_used + 2 <= (int64_t)s->ev.size();
         if (timed) CK(cudaEventRecord(s->ev[s->ev_used], s->stream));
         // App. A steps 1-7 with the divisions the planner selected for step t
         if (!s->d.inject_in_update && s->p.growth_mode != LBM_GROW_NONE) {
@@ -683,11 +687,19 @@ int lbm_timing_enable(lbm_sim *s, int64_t max_launches)
         s->ev.push_back(e);
     }
     s->ev_used = 0;
+    s->timing_count = 0;
     s->timing = max_launches > 0;
     DevScalars hs;
     int rc = read_scalars(s, &hs);
     if (rc != LBM_OK) return rc;
     s->timing_nodes0 = hs.node_updates;
+    return LBM_OK;
+}
+
+int lbm_timing_stride(lbm_sim *s, int64_t stride)
+{
+    if (!s || stride < 1) return LBM_ERR_INVALID_ARG;
+    s->timing_stride = stride;
     return LBM_OK;
 }
 

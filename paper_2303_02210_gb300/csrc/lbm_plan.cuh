@@ -30,6 +30,7 @@
 #pragma once
 
 #include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 
@@ -142,11 +143,13 @@ __device__ __forceinline__ bool plan_accept(const SimDev &d, const R *f, int y_r
 // n_s = floor(g M / rho_cell + carry) (Sec. II) from the fixed-point active
 // mass, the carried fraction after it, and the first-pass candidate count
 // before clipping, ceil(n_s ratio 1.15) + 64 (FP64, as the oracle).
-__device__ __forceinline__ void plan_ns(const SimDev &d, long long mass_fix, double carry_in, double ratio_in,
-                                        long long *ns_req, double *carry_out, double *kcf)
+// (Not inlined: it runs once per launch, and two inlined copies would only
+// add to the instruction fetches of a kernel that runs cold.)
+static __device__ __noinline__ void plan_ns(double growth_rate, double rho_cell, long long mass_fix, double carry_in,
+                                     double ratio_in, long long *ns_req, double *carry_out, double *kcf)
 {
     const double mass = (double)mass_fix * kFixInv;
-    const double xns = d.growth_rate * mass / d.rho_cell + carry_in;
+    const double xns = growth_rate * mass / rho_cell + carry_in;
     const double fl = floor(xns);
     *ns_req = (long long)fl;
     *carry_out = xns - fl;
@@ -167,7 +170,14 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int cur, uint32_t tn
     __shared__ unsigned long long s_kstop;
     __shared__ long long s_req;
     __shared__ double s_carry, s_kcf;
+    // first-pass candidates of this block: key, and rank among the block's
+    // accepted candidates (-1: rejected)
+    __shared__ uint32_t s_key[PLAN_NT * PLAN_R];
+    __shared__ int s_lr[PLAN_NT * PLAN_R];
 
+    // the next update (launched as a programmatic dependent) may start its
+    // prologue now; it waits for this grid's completion before reading
+    grid_dependents_launch();
     // ---- the state left by the update that just ran (read before any block writes)
     const int y_r = sc->y_r, y_hi_old = sc->y_hi;
     const int maxmass = sc->maxmass_accum;
@@ -186,7 +196,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int cur, uint32_t tn
     if (grow && blk == G - 1 && tid == 0) {
         long long req;
         double cy, kcf;
-        plan_ns(d, mass_acc, carry_in, ratio_in, &req, &cy, &kcf);
+        plan_ns(d.growth_rate, d.rho_cell, mass_acc, carry_in, ratio_in, &req, &cy, &kcf);
         sc->spec_req = req;
         sc->spec_carry = cy;
         sc->spec_kcf = kcf;
@@ -328,7 +338,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int cur, uint32_t tn
         if (tid == 0 && grow) {
             long long req;
             double cy, kcf;
-            plan_ns(d, mass_acc - frozen, carry_in, ratio_in, &req, &cy, &kcf);
+            plan_ns(d.growth_rate, d.rho_cell, mass_acc - frozen, carry_in, ratio_in, &req, &cy, &kcf);
             s_req = req;
             s_carry = cy;
             s_kcf = kcf;
@@ -380,32 +390,25 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int cur, uint32_t tn
         // gathers of a round are all in flight together
         const long long C = (kc + G - 1) / G;
         const int rounds = (int)((C + PLAN_NT - 1) / PLAN_NT); // <= PLAN_R (kc <= kmax)
-        uint32_t keys[PLAN_R];
-        unsigned accb = 0;
-#pragma unroll
-        for (int i = 0; i < PLAN_R; ++i) {
+        // (the round loops are not unrolled: this kernel runs with a cold
+        // instruction cache, and every copy of the candidate code costs fetches)
+        int tot_b = 0;
+#pragma unroll 1
+        for (int i = 0; i < rounds; ++i) {
             const long long j = (long long)i * PLAN_NT + tid;
             const long long k = (long long)blk * C + j;
-            keys[i] = 0u;
-            if (i < rounds && j < C && k < kc) {
+            bool a = false;
+            uint32_t key = 0u;
+            if (j < C && k < kc) {
                 const Candidate c = draw_candidate(d, k, tn, ylo, nwin);
-                if (plan_accept<R>(d, f, nyr, c)) {
-                    accb |= 1u << i;
-                    keys[i] = pack_key(c.x, c.y, c.pair);
-                }
+                a = plan_accept<R>(d, f, nyr, c);
+                key = pack_key(c.x, c.y, c.pair);
             }
-        }
-        // accepted before each of this thread's candidates within the block (draw order)
-        int pre[PLAN_R];
-        int tot_b = 0;
-#pragma unroll
-        for (int i = 0; i < PLAN_R; ++i) {
-            pre[i] = 0;
-            if (i < rounds) { // uniform
-                int t_i;
-                pre[i] = tot_b + plan_block_exscan((int)((accb >> i) & 1u), &t_i, s_i);
-                tot_b += t_i;
-            }
+            int t_i;
+            const int pre = plan_block_exscan(a ? 1 : 0, &t_i, s_i);
+            s_key[j] = key;
+            s_lr[j] = a ? tot_b + pre : -1;
+            tot_b += t_i;
         }
         if (tid == 0) d.pl_cnt[blk] = tot_b;
         plan_grid_sync(sc, &s_dead);
@@ -417,12 +420,14 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int cur, uint32_t tn
         }
         before = plan_block_sum(before, s_ll);
         total = plan_block_sum(total, s_ll);
-#pragma unroll
-        for (int i = 0; i < PLAN_R; ++i) {
-            if (i < rounds && ((accb >> i) & 1u)) {
-                const long long rank = before + pre[i];
-                if (rank == ns - 1) s_kstop = (unsigned long long)(blk * C + (long long)i * PLAN_NT + tid + 1);
-                if (rank < ns) plan_select(d, keys[i], (int)rank, buf);
+#pragma unroll 1
+        for (int i = 0; i < rounds; ++i) {
+            const int j = i * PLAN_NT + tid;
+            const int lr = s_lr[j];
+            if (lr >= 0) {
+                const long long rank = before + lr;
+                if (rank == ns - 1) s_kstop = (unsigned long long)(blk * C + j + 1);
+                if (rank < ns) plan_select(d, s_key[j], (int)rank, buf);
             }
         }
         acc = total;

@@ -124,11 +124,28 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
 
     const float *__restrict__ fin = (const float *)d.f[cur];
     float *__restrict__ fout = (float *)d.f[cur ^ 1];
-    const int y_r = d.sc->y_r, y_copy = d.sc->y_copy, y_hi = d.sc->y_hi;
     const int W = d.W, H = d.H, Wp = d.Wp;
     const long long P = d.P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int half = warp & 1, row = warp >> 1; // column half and row of the tile
+
+    // prologue, which may overlap the end of the planner (programmatic
+    // dependent launch): barriers, tensor map, tile flags
+    if (tid == 0) {
+        s_abort = 0;
+        s_nev = 0;
+        prefetch_tensormap(&tm_in);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], G::WARPS);
+        }
+        fence_mbar_init();
+    }
+    if (tid < TMA_KFLAG_WORDS) kflag[tid] = 0u;
+    __syncthreads();
+    // everything below reads what the planner wrote
+    grid_dependency_wait();
+    const int y_r = d.sc->y_r, y_copy = d.sc->y_copy, y_hi = d.sc->y_hi;
 
     // rows the rear wall has just frozen: bring this copy up to date (whole
     // stored rows, ghosts included)
@@ -149,19 +166,6 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
     const int count = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / Gd + 1 : 0;
     // tile k of this CTA is blockIdx.x + k Gd; its (tx, ty) advance by (Gd % ncx, Gd / ncx)
     const int dtx = Gd % ncx, dty = Gd / ncx;
-
-    if (tid == 0) {
-        s_abort = 0;
-        s_nev = 0;
-        prefetch_tensormap(&tm_in);
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], G::WARPS);
-        }
-        fence_mbar_init();
-    }
-    if (tid < TMA_KFLAG_WORDS) kflag[tid] = 0u;
-    __syncthreads();
     // producer state (thread 0): next tile to load and copies issued
     int itx = (int)blockIdx.x % ncx, ity = (int)blockIdx.x / ncx, issued = 0;
     auto issue = [&]() {
@@ -433,10 +437,20 @@ cudaError_t launch_update_tma_variant(const SimDev &d, int cur, uint32_t t, cons
         if (e != cudaSuccess) return e;
         if (dev < 64) attr[dev] = true;
     }
-    // maps[b] loads from population copy b
-    k_update_tma<TY, STAGES, CTAS, NOISE>
-        <<<CTAS * nsm, TmaGeom<TY>::NT, tma_smem_bytes<TY, STAGES>(), s>>>(d, cur, t, maps[cur]);
-    return cudaGetLastError();
+    // maps[b] loads from population copy b. Launched as a programmatic
+    // dependent of the planner: its CTAs may start (and run the prologue)
+    // before the planner has finished, and wait for it in grid_dependency_wait.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(CTAS * nsm));
+    cfg.blockDim = dim3(TmaGeom<TY>::NT);
+    cfg.dynamicSmemBytes = tma_smem_bytes<TY, STAGES>();
+    cfg.stream = s;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    la[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_update_tma<TY, STAGES, CTAS, NOISE>, d, cur, t, maps[cur]);
 }
 
 // variant 0: two staged tiles per CTA, three CTAs per SM; variant 1: three

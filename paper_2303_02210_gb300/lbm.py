@@ -91,6 +91,7 @@ _SIGNATURES = {
     "lbm_clear_status": (ctypes.c_int, [_P]),
     "lbm_timing_enable": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbm_timing_read": (ctypes.c_int, [_P, _P, _P, _P]),
+    "lbm_timing_stride": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbm_bytes_per_node": (ctypes.c_int, [_P, _P]),
     "lbm_sync": (ctypes.c_int, [_P]),
     "lbm_destroy": (None, [_P]),
@@ -308,6 +309,9 @@ class Simulation:
 
     def lbm_timing_enable(self, max_launches: int):
         _check(self._lib.lbm_timing_enable(self._h, int(max_launches)), "lbm_timing_enable")
+
+    def lbm_timing_stride(self, stride: int):
+        _check(self._lib.lbm_timing_stride(self._h, int(stride)), "lbm_timing_stride")
 
     def lbm_timing_read(self):
         n = ctypes.c_int64()
