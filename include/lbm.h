@@ -37,7 +37,8 @@ extern "C" {
 /* ---- device status bits (lbm_stats_t.status; sticky until lbm_clear_status) ---- */
 #define LBM_STATUS_FRONT_AT_TOP 1   /* mass reached row H-1 (the top wall) */
 #define LBM_STATUS_GROWTH_STARVED 2 /* a step accepted fewer than n_s divisions */
-#define LBM_STATUS_CAPACITY 4       /* n_s exceeded the planner capacity; growth skipped */
+#define LBM_STATUS_CAPACITY 4       /* n_s exceeded the planner capacity, or the exact mass sum
+                                       overflowed int64 (a runaway lattice); growth skipped */
 #define LBM_STATUS_TIMEOUT 8        /* a bulk copy did not complete in time; the step was abandoned */
 
 /* ---- enumerations used in lbm_params_t ---- */

@@ -364,7 +364,10 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int cur, uint32_t tn
             if (nyr + d.band_rows < yhi_c) yhi_c = nyr + d.band_rows;
         }
         nwin = yhi_c > ylo ? (unsigned long long)(yhi_c - ylo) * (unsigned long long)d.W : 0ull;
-        if (ns > d.ns_max) {
+        // more than the planner holds, or a negative request (the exact
+        // fixed-point mass overflowed: only a runaway lattice gets there):
+        // no divisions this step, and the status says so
+        if (ns > d.ns_max || ns < 0 || mass_fix < 0) {
             capacity = 1;
             ns = 0;
         }

@@ -244,3 +244,22 @@ def test_fp32_tma_repeatable_on_reused_memory():
         fb = b.pops()
         del b
         assert np.array_equal(fb, ref), f"trial {trial}: {int((fb != ref).sum())} populations differ"
+
+
+def test_runaway_mass_is_flagged_not_faulting():
+    """With the paper's parameters the literal negative-population fix keeps
+    adding mass once the front is pinned at the top wall, until the exact
+    int64 fixed-point mass overflows. The planner must then skip growth and
+    raise the capacity bit (a negative request once turned into a garbage
+    division count and out-of-range reads)."""
+    from paper_2303_02210_gb300.lbm import Simulation
+    p = wl.paper_params(width=64, height=128, front_row=16.0, seed=1, sim_id=1)
+    g = Simulation(p, precision="fp32")
+    g.step(6000)
+    st = g.stats()
+    assert st["status"] & 1 and st["status"] & 4  # front at the top, growth skipped
+    assert st["events_last"] >= 0
+    f = g.pops()  # the context is still usable
+    assert f.shape == (9, 128, 64)
+    h, _, _ = g.front_heights()
+    assert h.max() <= 128
