@@ -211,13 +211,36 @@ const char *lbm_last_cuda_error(void);
 /* Library version string, e.g. "0.1.0 sm_103a". */
 const char *lbm_version(void);
 
+/* ---- batched stepping of independent simulations ----
+ * The ensembles the roughness statistics of Sec. III need (many realisations
+ * of Eq. 6's w(t)) are many small, independent lattices; stepped one after
+ * another they leave most of the GPU idle. A batch advances its simulations
+ * together: one replay of a CUDA graph holding, for each simulation, a chain
+ * of steps (update + planner) as an independent branch, so the kernels of
+ * different simulations run side by side. Each simulation computes exactly
+ * what lbm_step would (the same kernels, the same counters).
+ *  sims    n distinct handles on one device, created by lbm_create and not
+ *          in kernel timing; the batch keeps the pointers, the caller keeps
+ *          ownership and must destroy the batch before any of them.
+ *  stream  cudaStream_t the graphs are launched on (NULL = legacy default).
+ * lbm_batch_step enqueues nsteps steps of every member, ordered after the work
+ * already on each member's own stream and before the work enqueued there
+ * afterwards; queries on a member (lbm_stats, lbm_front_heights, ...) then see
+ * the result. Between lbm_batch_step calls the members may also be stepped on
+ * their own. The graphs are captured in lbm_batch_create (LBM_ERR_CUDA if
+ * capture fails); lbm_batch_create allocates streams, events and graphs. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **out);
+int lbm_batch_step(lbm_batch *batch, int64_t nsteps);
+int lbm_batch_destroy(lbm_batch *batch);
+
 /* ---- allocation-free variant (the paper has no counterpart) ----
  * Front heights h(x) = 1 + highest set row of column x (0 if none) of a
  * caller's occupancy bitmask, plus the mean height and the interface width,
  * the same reduction lbm_step runs after every update, but without allocating
- * anything. For callers that cannot allocate device memory: a thread that is
- * capturing a CUDA graph, an application whose device memory is all held by
- * another allocator, or a loop that must never stall on the allocator.
+ * anything. For callers that cannot allocate device memory: an application
+ * whose device memory is all held by another allocator (a framework's caching
+ * pool), or a loop that must never stall on the allocator.
  *  mask_dev    device, read: H rows of (W + 31) / 32 uint32 words; bit (x & 31)
  *              of word (x >> 5) of row y is node (x, y).
  *  heights_dev device, written: W int32.

@@ -384,7 +384,9 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
                                        ty + 2);
         s->use_tma = ok;
         d.inject_in_update = ok && tma_inject ? 1 : 0;
-        d.upd_ctas = launch_update_tma_ctas(nsm, s->tma_variant);
+        // persistent CTAs, but no more than the lattice has tiles
+        const long long tiles = (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) * ((p->height + ty - 1) / ty);
+        d.upd_ctas = (int)std::min<long long>(launch_update_tma_ctas(nsm, s->tma_variant), tiles);
         d.upd_magic = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d.upd_ctas - 1) / (uint64_t)d.upd_ctas);
         if (d.upd_ctas > kTmaMaxCtas ||
             (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) * ((p->height + ty - 1) / ty) >= (1LL << 22)) {
@@ -412,7 +414,7 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
         if ((e = s->kt->fill(d, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
         if ((e = s->kt->scan(d, 0, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
         // observables of the initial state and the divisions of step 0
-        if ((e = s->kt->plan(d, 0, 0u, 1, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
+        if ((e = s->kt->plan(d, 1, s->stream)) != cudaSuccess) { rc = cuda_fail(e); break; }
         e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) { rc = cuda_fail(e); break; }
     } while (0);
@@ -424,33 +426,42 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     return LBM_OK;
 }
 
+// App. A steps 1-7 of the step the device scalars hold, with the divisions
+// the planner selected for it, on stream `st`.
+static cudaError_t launch_update(lbm_sim *s, cudaStream_t st, bool pdl = true)
+{
+    if (!s->d.inject_in_update && s->p.growth_mode != LBM_GROW_NONE) {
+        cudaError_t e = s->kt->inject(s->d, st);
+        if (e != cudaSuccess) return e;
+    }
+    return s->use_tma ? launch_update_tma_f32(s->d, s->maps, s->tma_variant, pdl, st) : s->kt->update(s->d, st);
+}
+
+// Host-side mirror of one completed step (the kernels keep theirs on the device).
+static void advance_host_step(lbm_sim *s)
+{
+    s->launches += (!s->d.inject_in_update && s->p.growth_mode != LBM_GROW_NONE) ? 3 : 2;
+    s->cur ^= 1;
+    ++s->step;
+}
+
 int lbm_step(lbm_sim *s, int64_t nsteps)
 {
     if (!s || nsteps < 0) return LBM_ERR_INVALID_ARG;
     USE_DEVICE(s);
     for (int64_t k = 0; k < nsteps; ++k) {
-        const uint32_t t = (uint32_t)s->step;
         const bool timed = s->timing && (s->timing_count++ % s->timing_stride) == 0 &&
                            s->ev_used + 2 <= (int64_t)s->ev.size();
         if (timed) CK(cudaEventRecord(s->ev[s->ev_used], s->stream));
-        // App. A steps 1-7 with the divisions the planner selected for step t
-        if (!s->d.inject_in_update && s->p.growth_mode != LBM_GROW_NONE) {
-            CK(s->kt->inject(s->d, s->cur, t, s->stream));
-            s->launches += 1;
-        }
-        if (s->use_tma)
-            CK(launch_update_tma_f32(s->d, s->cur, t, s->maps, s->tma_grid, s->tma_variant, s->stream));
-        else
-            CK(s->kt->update(s->d, s->cur, t, s->stream));
+        cudaError_t e = launch_update(s, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e);
         if (timed) {
             CK(cudaEventRecord(s->ev[s->ev_used + 1], s->stream));
             s->ev_used += 2;
         }
-        // observables of the new state; divisions of step t + 1
-        CK(s->kt->plan(s->d, s->cur ^ 1, t + 1u, 0, s->stream));
-        s->launches += 2;
-        s->cur ^= 1;
-        ++s->step;
+        // observables of the new state; divisions of the next step
+        CK(s->kt->plan(s->d, 0, s->stream));
+        advance_host_step(s);
     }
     return LBM_OK;
 }
@@ -621,7 +632,7 @@ int lbm_set_populations(lbm_sim *s, const double *f_host)
     CK(cudaMemcpyAsync(&sc->status, &zeroi, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     CK(s->kt->scan(s->d, s->cur, s->stream));
     // observe this state again and redo the selection of the next step
-    CK(s->kt->plan(s->d, s->cur, (uint32_t)s->step, 1, s->stream));
+    CK(s->kt->plan(s->d, 1, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return LBM_OK;
 }
@@ -746,5 +757,132 @@ const char *lbm_strerror(int code)
 const char *lbm_last_cuda_error(void) { return g_cuda_err; }
 
 const char *lbm_version(void) { return "0.1.0 sm_103a"; }
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched stepping: independent simulations advanced together by replaying a
+// CUDA graph that holds one chain of steps per simulation as parallel branches
+// (the kernels read the step index from each simulation's device scalars, so
+// the same graph serves every step).
+struct lbm_batch {
+    std::vector<lbm_sim *> sims;
+    int device;
+    cudaStream_t user;   // the caller's stream
+    cudaStream_t origin; // the batch's own stream, which the graphs are captured from and run on
+    std::vector<cudaStream_t> branch;
+    cudaEvent_t fork;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec[2]; // one step, kBatchChain steps
+};
+
+namespace {
+constexpr int kBatchChain = 4; // steps per branch in the longer graph
+
+// Captures `steps` steps of every simulation, one branch each, into an
+// executable graph.
+cudaError_t batch_capture(lbm_batch *b, int steps, cudaGraphExec_t *out)
+{
+    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t first = cudaEventRecord(b->fork, b->origin);
+    for (size_t i = 0; i < b->sims.size() && first == cudaSuccess; ++i) {
+        lbm_sim *s = b->sims[i];
+        first = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+        for (int k = 0; k < steps && first == cudaSuccess; ++k) {
+            first = launch_update(s, b->branch[i], false);
+            if (first == cudaSuccess) first = s->kt->plan(s->d, 0, b->branch[i]);
+        }
+        if (first == cudaSuccess) first = cudaEventRecord(b->join[i], b->branch[i]);
+        if (first == cudaSuccess) first = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->origin, &g);
+    if (first == cudaSuccess) first = e;
+    if (first == cudaSuccess) first = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return first;
+}
+} // namespace
+
+extern "C" {
+
+int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **out)
+{
+    if (!sims || n < 1 || !out) return LBM_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!sims[i] || sims[i]->device != sims[0]->device || sims[i]->timing) return LBM_ERR_INVALID_ARG;
+        for (int32_t j = 0; j < i; ++j)
+            if (sims[j] == sims[i]) return LBM_ERR_INVALID_ARG;
+    }
+    CK(cudaSetDevice(sims[0]->device));
+    lbm_batch *b = new lbm_batch();
+    b->sims.assign(sims, sims + n);
+    b->device = sims[0]->device;
+    b->user = (cudaStream_t)stream;
+    b->origin = nullptr;
+    b->exec[0] = b->exec[1] = nullptr;
+    b->fork = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+    // one-time kernel attributes are set outside the capture
+    for (int32_t i = 0; i < n && e == cudaSuccess; ++i)
+        if (sims[i]->use_tma) e = prepare_update_tma_f32(sims[i]->d, sims[i]->tma_variant);
+    for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->branch.push_back(st);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->join.push_back(ev);
+    }
+    if (e == cudaSuccess) e = batch_capture(b, 1, &b->exec[0]);
+    if (e == cudaSuccess) e = batch_capture(b, kBatchChain, &b->exec[1]);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return cuda_fail(e);
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *b, int64_t nsteps)
+{
+    if (!b || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(b->device));
+    // after whatever the caller's stream and each simulation's own stream hold ...
+    CK(cudaEventRecord(b->fork, b->user));
+    CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        CK(cudaEventRecord(b->join[i], b->sims[i]->stream));
+        CK(cudaStreamWaitEvent(b->origin, b->join[i], 0));
+    }
+    int64_t left = nsteps;
+    for (; left >= kBatchChain; left -= kBatchChain) CK(cudaGraphLaunch(b->exec[1], b->origin));
+    for (; left > 0; --left) CK(cudaGraphLaunch(b->exec[0], b->origin));
+    // ... and before whatever comes next on it
+    CK(cudaEventRecord(b->fork, b->origin));
+    CK(cudaStreamWaitEvent(b->user, b->fork, 0));
+    for (lbm_sim *s : b->sims) {
+        CK(cudaStreamWaitEvent(s->stream, b->fork, 0));
+        for (int64_t k = 0; k < nsteps; ++k) advance_host_step(s);
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return LBM_OK;
+    cudaSetDevice(b->device);
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    for (int i = 0; i < 2; ++i)
+        if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+    for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+    return LBM_OK;
+}
 
 } // extern "C"

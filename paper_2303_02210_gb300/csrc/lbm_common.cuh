@@ -189,11 +189,14 @@ struct KernelTable {
     cudaError_t (*fill)(const SimDev &, cudaStream_t);
     cudaError_t (*ghosts)(const SimDev &, cudaStream_t);
     cudaError_t (*scan)(const SimDev &, int cur, cudaStream_t);
-    // fused planner: observe copy `cur`, select the divisions of step tn
-    cudaError_t (*plan)(const SimDev &, int cur, uint32_t tn, int init, cudaStream_t);
-    // the selected divisions of step t into copy `cur` (update kernels without staging)
-    cudaError_t (*inject)(const SimDev &, int cur, uint32_t t, cudaStream_t);
-    cudaError_t (*update)(const SimDev &, int cur, uint32_t t, cudaStream_t);
+    // Per-step kernels read the step t from the device scalars (step t reads
+    // population copy t & 1), so a captured step can be replayed unchanged.
+    // fused planner: observe the state after the latest update (init: the
+    // current state) and select the divisions of the next step
+    cudaError_t (*plan)(const SimDev &, int init, cudaStream_t);
+    // the selected divisions of the coming step (update kernels without staging)
+    cudaError_t (*inject)(const SimDev &, cudaStream_t);
+    cudaError_t (*update)(const SimDev &, cudaStream_t);
     cudaError_t (*fields)(const SimDev &, int cur, double *rho, double *ux, double *uy, cudaStream_t);
     int (*plan_blocks_per_sm)();
     int (*update_blocks_per_sm)();
@@ -205,8 +208,10 @@ extern const KernelTable kTableF64;
 
 // TMA-staged FP32 update (lbm_update_tma.cuh). maps[b] loads from copy b
 // (box (kTmaBoxX + 8) x (rows per tile + 2) x 9, in stored-row coordinates).
-cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
-                                  int variant, cudaStream_t s);
+// Sets the kernel attributes a launch needs (done by the first launch too).
+cudaError_t prepare_update_tma_f32(const SimDev &d, int variant);
+// pdl: launch as a programmatic dependent of the preceding planner kernel.
+cudaError_t launch_update_tma_f32(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s);
 // CTAs the TMA-staged update kernel runs on this many SMs.
 int launch_update_tma_ctas(int nsm, int variant);
 

@@ -6,10 +6,11 @@ namespace lbm {
 const KernelTable kTableF32 = make_table<float>();
 
 
-cudaError_t launch_update_tma_f32(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
-                                  int variant, cudaStream_t s)
+cudaError_t prepare_update_tma_f32(const SimDev &d, int variant) { return prepare_update_tma(d, variant); }
+
+cudaError_t launch_update_tma_f32(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s)
 {
-    return launch_update_tma(d, cur, t, maps, nsm, variant, s);
+    return launch_update_tma(d, maps, variant, pdl, s);
 }
 
 int launch_update_tma_ctas(int nsm, int variant) { return tma_ctas_per_sm(variant) * nsm; }

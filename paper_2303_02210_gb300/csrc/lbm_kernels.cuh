@@ -473,8 +473,12 @@ __device__ __forceinline__ R fix_negative(R *fo, int mode)
 // Fused update of the active window (App. A steps 1, 2, 4-7; the injection of
 // step 3 was already added to the pre-stream slots by k_plan).
 template <typename R, int TPB, int NR>
-__global__ void __launch_bounds__(TPB) k_update(SimDev d, int cur, uint32_t t)
+__global__ void __launch_bounds__(TPB) k_update(SimDev d)
 {
+    // the step is read from the device (so a captured step replays as is):
+    // step t reads copy t & 1
+    const uint32_t t = (uint32_t)d.sc->step;
+    const int cur = (int)(t & 1u);
     const R *__restrict__ fin = (const R *)d.f[cur];
     R *__restrict__ fout = (R *)d.f[cur ^ 1];
     const int y_r = d.sc->y_r, y_copy = d.sc->y_copy, y_hi = d.sc->y_hi;

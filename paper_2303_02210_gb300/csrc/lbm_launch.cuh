@@ -27,18 +27,18 @@ struct Launch {
         k_scan<R><<<4 * 152, 256, 0, s>>>(d, cur);
         return cudaGetLastError();
     }
-    static cudaError_t plan(const SimDev &d, int cur, uint32_t tn, int init, cudaStream_t s)
+    static cudaError_t plan(const SimDev &d, int init, cudaStream_t s)
     {
-        return launch_plan<R>(d, cur, tn, init, s);
+        return launch_plan<R>(d, init, s);
     }
-    static cudaError_t inject(const SimDev &d, int cur, uint32_t t, cudaStream_t s)
+    static cudaError_t inject(const SimDev &d, cudaStream_t s)
     {
-        k_inject<R><<<152, 128, 0, s>>>(d, cur, t);
+        k_inject<R><<<152, 128, 0, s>>>(d);
         return cudaGetLastError();
     }
-    static cudaError_t update(const SimDev &d, int cur, uint32_t t, cudaStream_t s)
+    static cudaError_t update(const SimDev &d, cudaStream_t s)
     {
-        k_update<R, UPD_TPB, UPD_NR><<<d.update_grid, UPD_TPB, 0, s>>>(d, cur, t);
+        k_update<R, UPD_TPB, UPD_NR><<<d.update_grid, UPD_TPB, 0, s>>>(d);
         return cudaGetLastError();
     }
     static cudaError_t fields(const SimDev &d, int cur, double *rho, double *ux, double *uy, cudaStream_t s)

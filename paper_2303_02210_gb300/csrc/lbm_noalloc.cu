@@ -1,8 +1,8 @@
 // Allocation-free front heights: a variant of the observer's front-height
-// reduction for callers that cannot allocate device memory, for example code
-// that runs while a CUDA graph is being captured on its thread, a host whose
-// device memory is entirely reserved by another allocator, or a latency-bound
-// loop that must not wait on the allocator. Its cross-block scratch (one
+// reduction for callers that cannot allocate device memory, for example a
+// host whose device memory is entirely reserved by another allocator (a
+// framework's caching pool), or a latency-bound loop that must not wait on
+// the allocator. Its cross-block scratch (one
 // partial result per block and a completion counter) is a file-scope device
 // array that every GPU loading this library holds until the process exits.
 #include <cstdio>

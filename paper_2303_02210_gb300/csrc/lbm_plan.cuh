@@ -158,9 +158,13 @@ static __device__ __noinline__ void plan_ns(double growth_rate, double rho_cell,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int cur, uint32_t tn, int init)
+__global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
 {
     DevScalars *sc = d.sc;
+    // the state to observe is copy tn & 1, tn the step the selection is for:
+    // the current step count for the initial state, else the next one
+    const uint32_t tn = (uint32_t)sc->step + (init ? 0u : 1u);
+    const int cur = (int)(tn & 1u);
     R *f = (R *)d.f[cur];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = (int)gridDim.x, blk = (int)blockIdx.x;
@@ -556,8 +560,10 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int cur, uint32_t tn
 // (node, pair) never share a slot (each slot streams into exactly one
 // direction of one node).
 template <typename R>
-__global__ void k_inject(SimDev d, int cur, uint32_t t)
+__global__ void k_inject(SimDev d)
 {
+    const uint32_t t = (uint32_t)d.sc->step;
+    const int cur = (int)(t & 1u);
     R *f = (R *)d.f[cur];
     const int n = d.sc->rec_n, y_r = d.sc->y_r;
     const size_t buf = (size_t)(t & 1u) * (size_t)d.ns_max;
@@ -581,11 +587,20 @@ __global__ void k_inject(SimDev d, int cur, uint32_t t)
 }
 
 template <typename R>
-cudaError_t launch_plan(const SimDev &d, int cur, uint32_t tn, int init, cudaStream_t s)
+cudaError_t launch_plan(const SimDev &d, int init, cudaStream_t s)
 {
-    void *args[] = {(void *)&d, (void *)&cur, (void *)&tn, (void *)&init};
-    return cudaLaunchCooperativeKernel((const void *)k_plan<R>, dim3((unsigned)d.plan_grid), dim3(PLAN_NT), args, 0,
-                                       s);
+    // a cooperative launch: every block resident at once (the grid barriers
+    // rely on it), or the launch fails
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)d.plan_grid);
+    cfg.blockDim = dim3(PLAN_NT);
+    cfg.stream = s;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeCooperative;
+    la[0].val.cooperative = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_plan<R>, d, init);
 }
 
 template <typename R>

@@ -105,7 +105,7 @@ __device__ __forceinline__ float update_node(const float g[NQ], float rho, bool 
 // CTAS CTAs per SM (registers are capped so that they fit); NOISE: sigma != 0.
 template <int TY, int STAGES, int CTAS, bool NOISE>
 __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
-    k_update_tma(SimDev d, int cur, uint32_t t, const __grid_constant__ CUtensorMap tm_in)
+    k_update_tma(SimDev d, const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1)
 {
     using G = TmaGeom<TY>;
     constexpr int NT = G::NT, PLANE = G::PLANE;
@@ -122,8 +122,6 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
     unsigned *kflag = reinterpret_cast<unsigned *>(ev_add + TMA_EV_CAP); // tiles with divisions
     __shared__ int s_abort, s_nev;
 
-    const float *__restrict__ fin = (const float *)d.f[cur];
-    float *__restrict__ fout = (float *)d.f[cur ^ 1];
     const int W = d.W, H = d.H, Wp = d.Wp;
     const long long P = d.P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -134,7 +132,8 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
     if (tid == 0) {
         s_abort = 0;
         s_nev = 0;
-        prefetch_tensormap(&tm_in);
+        prefetch_tensormap(&tm0);
+        prefetch_tensormap(&tm1);
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], G::WARPS);
@@ -145,6 +144,13 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
     __syncthreads();
     // everything below reads what the planner wrote
     grid_dependency_wait();
+    // step t (read from the device, so a captured step replays as is) pulls
+    // from copy t & 1 (tensor map tm0 or tm1) and writes the other
+    const uint32_t t = (uint32_t)d.sc->step;
+    const int cur = (int)(t & 1u);
+    const CUtensorMap *tm = cur ? &tm1 : &tm0;
+    const float *__restrict__ fin = (const float *)d.f[cur];
+    float *__restrict__ fout = (float *)d.f[cur ^ 1];
     const int y_r = d.sc->y_r, y_copy = d.sc->y_copy, y_hi = d.sc->y_hi;
 
     // rows the rear wall has just frozen: bring this copy up to date (whole
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
     auto issue = [&]() {
         const int s = issued % STAGES;
         mbar_arrive_expect_tx(&full[s], G::BYTES);
-        tma_load_3d(s_in + s * G::STRIDE, &tm_in, itx * TMA_TX - 4 + kXO, y_r + ity * TY - 1, 0, &full[s]);
+        tma_load_3d(s_in + s * G::STRIDE, tm, itx * TMA_TX - 4 + kXO, y_r + ity * TY - 1, 0, &full[s]);
         ++issued;
         itx += dtx;
         ity += dty;
@@ -423,9 +429,9 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
     }
 }
 
+// The kernel's shared-memory opt-in (once per device).
 template <int TY, int STAGES, int CTAS, bool NOISE>
-cudaError_t launch_update_tma_variant(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
-                                      cudaStream_t s)
+cudaError_t prepare_update_tma_variant()
 {
     static bool attr[64] = {};
     int dev = 0;
@@ -437,11 +443,26 @@ cudaError_t launch_update_tma_variant(const SimDev &d, int cur, uint32_t t, cons
         if (e != cudaSuccess) return e;
         if (dev < 64) attr[dev] = true;
     }
+    return cudaSuccess;
+}
+
+inline cudaError_t prepare_update_tma(const SimDev &d, int variant)
+{
+    if (variant == 1)
+        return d.noise_on ? prepare_update_tma_variant<4, 3, 2, true>() : prepare_update_tma_variant<4, 3, 2, false>();
+    return d.noise_on ? prepare_update_tma_variant<4, 2, 3, true>() : prepare_update_tma_variant<4, 2, 3, false>();
+}
+
+template <int TY, int STAGES, int CTAS, bool NOISE>
+cudaError_t launch_update_tma_variant(const SimDev &d, const CUtensorMap *maps, bool pdl, cudaStream_t s)
+{
+    cudaError_t e = prepare_update_tma_variant<TY, STAGES, CTAS, NOISE>();
+    if (e != cudaSuccess) return e;
     // maps[b] loads from population copy b. Launched as a programmatic
     // dependent of the planner: its CTAs may start (and run the prologue)
     // before the planner has finished, and wait for it in grid_dependency_wait.
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(CTAS * nsm));
+    cfg.gridDim = dim3((unsigned)d.upd_ctas); // at most CTAS per SM
     cfg.blockDim = dim3(TmaGeom<TY>::NT);
     cfg.dynamicSmemBytes = tma_smem_bytes<TY, STAGES>();
     cfg.stream = s;
@@ -449,8 +470,8 @@ cudaError_t launch_update_tma_variant(const SimDev &d, int cur, uint32_t t, cons
     la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     la[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = la;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_update_tma<TY, STAGES, CTAS, NOISE>, d, cur, t, maps[cur]);
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_update_tma<TY, STAGES, CTAS, NOISE>, d, maps[0], maps[1]);
 }
 
 // variant 0: two staged tiles per CTA, three CTAs per SM; variant 1: three
@@ -458,14 +479,13 @@ cudaError_t launch_update_tma_variant(const SimDev &d, int cur, uint32_t t, cons
 constexpr int tma_rows(int /*variant*/) { return 4; }
 constexpr int tma_ctas_per_sm(int variant) { return variant == 1 ? 2 : 3; }
 
-inline cudaError_t launch_update_tma(const SimDev &d, int cur, uint32_t t, const CUtensorMap *maps, int nsm,
-                                     int variant, cudaStream_t s)
+inline cudaError_t launch_update_tma(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s)
 {
     if (variant == 1)
-        return d.noise_on ? launch_update_tma_variant<4, 3, 2, true>(d, cur, t, maps, nsm, s)
-                          : launch_update_tma_variant<4, 3, 2, false>(d, cur, t, maps, nsm, s);
-    return d.noise_on ? launch_update_tma_variant<4, 2, 3, true>(d, cur, t, maps, nsm, s)
-                      : launch_update_tma_variant<4, 2, 3, false>(d, cur, t, maps, nsm, s);
+        return d.noise_on ? launch_update_tma_variant<4, 3, 2, true>(d, maps, pdl, s)
+                          : launch_update_tma_variant<4, 3, 2, false>(d, maps, pdl, s);
+    return d.noise_on ? launch_update_tma_variant<4, 2, 3, true>(d, maps, pdl, s)
+                      : launch_update_tma_variant<4, 2, 3, false>(d, maps, pdl, s);
 }
 
 } // namespace lbm

@@ -99,6 +99,9 @@ _SIGNATURES = {
     "lbm_last_cuda_error": (ctypes.c_char_p, []),
     "lbm_version": (ctypes.c_char_p, []),
     "lbm_front_heights_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+    "lbm_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+    "lbm_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "lbm_batch_destroy": (ctypes.c_int, [_P]),
 }
 
 _lib = None
@@ -330,3 +333,41 @@ class Simulation:
         _check(self._lib.lbm_sync(self._h), "lbm_sync")
 
     sync = lbm_sync
+
+
+class Batch:
+    """Independent simulations stepped together (``lbm_batch_create`` ...
+    ``lbm_batch_destroy``): one CUDA-graph replay advances every member, the
+    members' kernels running side by side. Keeps the members alive."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        lib = load_library()
+        self.sims = list(sims)
+        if not self.sims:
+            raise LbmError("lbm_batch_create: no simulations")
+        self._lib = lib
+        dev = self.sims[0].device
+        with torch.cuda.device(dev):
+            self.stream = torch.cuda.current_stream(dev) if stream is None else stream
+            arr = (_P * len(self.sims))(*[s._h.value for s in self.sims])
+            h = _P()
+            _check(lib.lbm_batch_create(ctypes.cast(arr, _P), len(self.sims), _P(self.stream.cuda_stream),
+                                        ctypes.byref(h)), "lbm_batch_create")
+        self._h = h
+
+    def lbm_batch_step(self, n: int = 1):
+        _check(self._lib.lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    step = lbm_batch_step
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

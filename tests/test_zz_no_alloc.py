@@ -1,8 +1,8 @@
 """The allocation-free front-height entry point, ``lbm_front_heights_noalloc``.
 
-It serves callers that cannot allocate device memory (a thread capturing a
-CUDA graph, an application whose device memory is held by another allocator,
-a loop that must not stall on the allocator): its scratch is a fixed array
+It serves callers that cannot allocate device memory (an application whose
+device memory is held by another allocator, a loop that must not stall on the
+allocator): its scratch is a fixed array
 inside the library. Here it must reproduce what ``lbm_front_heights`` reports
 for a simulation after ``lbm_step`` (heights exactly, mean height and width
 to the last bit), on two calls in a row that reuse the same scratch, on a
