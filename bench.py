@@ -162,6 +162,53 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def measure_ensemble(n: int = 256, steps: int = 200, warm: int = 5) -> dict:
+    """The batched form: n uneven realisations (widths 256..2048, height =
+    width / 2, bulk or edge growth, FP32) advanced together by lbm_batch_step
+    (one graph replay per step or four), against the same simulations stepped
+    one after another with lbm_step. Aggregate active-window node updates per
+    second, device time by CUDA events around each region."""
+    import torch
+    from paper_2303_02210_gb300.lbm import Batch, Simulation
+    params = wl.ensemble(n)
+    sims = [Simulation(p, precision="fp32") for p in params]
+    batch = Batch(sims)
+    batch.step(warm)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def nodes():
+        return sum(s.stats()["node_updates"] for s in sims)
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n0 = nodes()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return (nodes() - n0) / (e0.elapsed_time(e1) * 1e-3) / 1e6, e0.elapsed_time(e1)
+
+    batched, ms_b = timed(lambda: batch.step(steps))
+
+    def one_by_one():
+        for s in sims:
+            s.step(steps)
+
+    single, ms_s = timed(one_by_one)
+    batch.close()
+    total = sum(p["width"] * p["height"] for p in params)
+    del batch, sims
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return {"workload": (f"{n} realisations, widths uniform in {{256, 512, 1024, 2048}}, height = width/2, "
+                         f"bulk or edge growth at random, FP32 ({total / 1e6:.0f}M lattice nodes)"),
+            "steps": steps, "value": batched, "unit": UNIT, "ms_per_step": ms_b / steps,
+            "one_at_a_time": single, "one_at_a_time_ms_per_step": ms_s / steps,
+            "speedup": batched / single if single > 0 else None}
+
+
 def oracle_rate(params: dict, steps: int):
     """The FP64 CPU oracle, as it stands, on `steps` steps of the workload.
     Returns (MLUPS counted over the same active window the GPU updates,
@@ -216,6 +263,7 @@ def main():
     ap.add_argument("--update-kernel", default="auto", choices=["auto", "plain", "tma", "tma1", "tma_sel"])
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -329,6 +377,8 @@ def main():
         "clocks": clk,
         "status": status,
     }
+    if world == 1 and not args.no_ensemble:
+        line["ensemble"] = measure_ensemble()
     if world == 1 and not args.no_cpu_baseline:
         rate, dt, window = oracle_rate(workload_params(), args.cpu_steps)
         line["cpu_baseline"] = {

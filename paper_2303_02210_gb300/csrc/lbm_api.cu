@@ -361,9 +361,12 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     d.update_grid = g0 >= ncx ? (g0 / ncx) * ncx : ncx;
     // the planner's blocks must all be resident at once (cooperative launch)
     const int pbs = s->kt->plan_blocks_per_sm();
-    // one block per SM at most, fewer when few divisions per step are possible
-    // (every grid barrier costs an arrival per block)
-    const int pg = (int)std::min<long long>(nsm, std::max<long long>(16, (L.ns_max + 2 * 512 - 1) / (2 * 512)));
+    // as few blocks as the work needs (every grid barrier costs an arrival per
+    // block, and small lattices in a batch share the GPU): one 32-column mask
+    // word per warp, about four candidates per thread at the largest n_s;
+    // at least two, at most one per SM
+    const long long want = std::max<long long>((L.MW + 15) / 16, (L.ns_max + 2047) / 2048);
+    const int pg = (int)std::min<long long>(nsm, std::max<long long>(2, want));
     d.plan_grid = pbs > 0 ? std::min(pg, kPlanMaxBlocks) : 0;
     if (d.plan_grid < 1) {
         if (s->own_arena) cudaFree(s->arena);
@@ -384,9 +387,12 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
                                        ty + 2);
         s->use_tma = ok;
         d.inject_in_update = ok && tma_inject ? 1 : 0;
-        // persistent CTAs, but no more than the lattice has tiles
+        // persistent CTAs, but no more than one per eight tiles of the whole
+        // lattice (small lattices then leave SMs to others in a batch); at
+        // least two, since the reciprocal below needs upd_ctas >= 2
         const long long tiles = (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) * ((p->height + ty - 1) / ty);
-        d.upd_ctas = (int)std::min<long long>(launch_update_tma_ctas(nsm, s->tma_variant), tiles);
+        d.upd_ctas = (int)std::max<long long>(
+            2, std::min<long long>(launch_update_tma_ctas(nsm, s->tma_variant), (tiles + 7) / 8));
         d.upd_magic = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d.upd_ctas - 1) / (uint64_t)d.upd_ctas);
         if (d.upd_ctas > kTmaMaxCtas ||
             (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) * ((p->height + ty - 1) / ty) >= (1LL << 22)) {

@@ -165,7 +165,7 @@ struct SimDev {
     int noise_on;        // sigma != 0
     int inject_in_update; // the selector only lists the divisions; the update kernel adds them
     int upd_ctas;         // CTAs of the TMA-staged update kernel (tiles dealt round-robin)
-    uint32_t upd_magic;   // ceil(2^32 / upd_ctas): tile / upd_ctas = umulhi(tile, magic)
+    uint32_t upd_magic;   // ceil(2^32 / upd_ctas), upd_ctas >= 2: tile / upd_ctas = umulhi(tile, magic)
     int upd_tyl2;         // log2 of the rows per tile of the TMA-staged update
     int *rec_owner;       // per division (selector order): owning CTA of its tile,
     int *rec_k;           // the tile's index among that CTA's tiles,

@@ -82,6 +82,28 @@ def lattice_edge(seed: int = 1, **kw) -> dict:
     return p
 
 
+def ensemble(n: int = 256, seed: int = 1, **kw) -> list:
+    """n independent realisations of uneven sizes, as roughness ensembles need:
+    widths drawn uniformly from {256, 512, 1024, 2048} with height = width / 2,
+    bulk or edge-restricted growth (depth 8) chosen at random per member,
+    tau = 0.8, g = 1e-4, flat front at a quarter of the height with seeded
+    noise, advancing rear wall for bulk growth, fixed for edge growth. Member
+    i has seed seed + i and its own simulation id."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        W = int(rng.choice([256, 512, 1024, 2048]))
+        edge = bool(rng.integers(0, 2))
+        p = base_params(width=W, height=W // 2, tau=0.8, growth_rate=1e-4,
+                        growth_mode="edge" if edge else "bulk", edge_depth=8,
+                        front_kind="flat", front_row=float(W // 8), front_amp=0.5,
+                        wall_mode="fixed" if edge else "advance", seed=seed + i, sim_id=i)
+        p.update(kw)
+        out.append(p)
+    return out
+
+
 WORKLOADS = {
     "lattice_small": lattice_small,
     "lattice_kpz": lattice_kpz,
