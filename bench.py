@@ -209,6 +209,25 @@ def measure_ensemble(n: int = 256, steps: int = 200, warm: int = 5) -> dict:
             "speedup": batched / single if single > 0 else None}
 
 
+def measure_serving(n: int = 100, rate: float = 200.0, steps=(500, 5000), budget_gb: float = 100.0) -> dict:
+    """The served form: a fixed trace of n requests (Poisson arrivals at
+    `rate` per second, widths log-uniform 128..4096, height = width / 2, bulk,
+    edge or density growth, g log-uniform 1e-5..1e-3, steps uniform in
+    `steps`, FP32) through the continuous-batching loop with an HBM budget;
+    time to result per request (arrival to result on the host) and the
+    aggregate node-update rate over the whole run (wall clock)."""
+    from paper_2303_02210_gb300 import serving
+    trace = wl.serving_trace(n, rate=rate, steps=steps)
+    reqs = [serving.Request(params=p, steps=k, arrival=t) for t, p, k in trace]
+    srv = serving.Server(hbm_budget=int(budget_gb * 2 ** 30), chunk=100)
+    srv.run(reqs)
+    out = serving.summary(reqs, srv)
+    out["workload"] = (f"{n} requests, Poisson arrivals at {rate:g}/s, widths log-uniform 128-4096, "
+                       f"height = width/2, bulk/edge/density growth, g log-uniform 1e-5..1e-3, "
+                       f"{steps[0]}-{steps[1]} steps, FP32, {budget_gb:g} GB budget, 100-step ticks")
+    return out
+
+
 def oracle_rate(params: dict, steps: int):
     """The FP64 CPU oracle, as it stands, on `steps` steps of the workload.
     Returns (MLUPS counted over the same active window the GPU updates,
@@ -263,7 +282,7 @@ def main():
     ap.add_argument("--update-kernel", default="auto", choices=["auto", "plain", "tma", "tma1", "tma_sel"])
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble measurement")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble and serving measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -379,6 +398,7 @@ def main():
     }
     if world == 1 and not args.no_ensemble:
         line["ensemble"] = measure_ensemble()
+        line["serving"] = measure_serving()
     if world == 1 and not args.no_cpu_baseline:
         rate, dt, window = oracle_rate(workload_params(), args.cpu_steps)
         line["cpu_baseline"] = {

@@ -1,0 +1,90 @@
+"""The serving loop (continuous batching): admission by footprint in arrival
+order, ticks over the resident simulations, release on completion — the
+loop's logic with stand-ins on the CPU, and on the GPU that every served
+result equals the same request run alone."""
+import numpy as np
+import pytest
+
+from paper_2303_02210_gb300 import serving
+from paper_2303_02210_gb300 import workloads as wl
+
+
+class FakeSim:
+    """Stands in for Simulation: counts steps, reports them as node updates."""
+    live = 0
+    peak = 0
+
+    def __init__(self, params, precision="fp32", stream=None):
+        self.params, self.n = params, 0
+        FakeSim.live += 1
+        FakeSim.peak = max(FakeSim.peak, FakeSim.live)
+
+    def step(self, n):
+        self.n += n
+
+    def stats(self):
+        return {"node_updates": self.n * self.params["width"], "step": self.n}
+
+    def front_heights(self):
+        return np.zeros(self.params["width"], np.int32), 0.0, 0.0
+
+    def close(self):
+        FakeSim.live -= 1
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 0.001  # every look at the clock advances it a millisecond
+        return self.t
+
+
+def test_loop_admits_by_footprint_in_arrival_order_and_finishes_all():
+    FakeSim.live = FakeSim.peak = 0
+    reqs = [serving.Request(params={"width": w, "height": w // 2}, steps=s, arrival=a)
+            for a, w, s in [(0.0, 64, 250), (0.0, 64, 100), (0.002, 128, 300), (0.003, 64, 50), (0.05, 32, 120)]]
+    srv = serving.Server(hbm_budget=200, chunk=100, clock=FakeClock(), simulation=FakeSim,
+                         footprint=lambda p, prec: p["width"], new_stream=lambda: None, synchronize=lambda: None)
+    srv.run(reqs)
+    assert FakeSim.live == 0 and FakeSim.peak <= 3  # never more than the budget holds (64+64+64 or 64+128)
+    for r in reqs:
+        assert r.result["stats"]["step"] == r.steps
+        assert r.admitted >= r.arrival and r.finished > r.admitted
+    # arrival order: the 128-wide request waited for room and nothing overtook it
+    assert reqs[3].admitted >= reqs[2].admitted
+    assert srv.node_updates == sum(r.steps * r.params["width"] for r in reqs)
+    s = serving.summary(reqs, srv)
+    assert s["p50_s"] <= s["p99_s"] and s["requests"] == 5
+
+
+def test_request_larger_than_the_budget_is_refused():
+    r = serving.Request(params={"width": 512, "height": 256}, steps=10)
+    srv = serving.Server(hbm_budget=100, simulation=FakeSim, footprint=lambda p, prec: p["width"],
+                         new_stream=lambda: None, synchronize=lambda: None)
+    with pytest.raises(ValueError):
+        srv.run([r])
+
+
+@pytest.mark.gpu
+def test_served_results_equal_requests_run_alone():
+    """Requests of mixed sizes, growth modes and rates served together with
+    a budget that forces queueing end exactly where each ends alone."""
+    from paper_2303_02210_gb300.lbm import Simulation, lbm_footprint
+    trace = wl.serving_trace(10, rate=500.0, steps=(100, 400), seed=7)
+    trace = [(t, dict(p, width=min(p["width"], 512), height=min(p["width"], 512) // 2,
+                      front_row=float(min(p["width"], 512) // 8)), n) for t, p, n in trace]
+    reqs = [serving.Request(params=p, steps=n, arrival=t, keep_populations=True) for t, p, n in trace]
+    budget = 3 * max(lbm_footprint(r.params, "fp32") for r in reqs)
+    srv = serving.Server(hbm_budget=budget, chunk=64)
+    srv.run(reqs)
+    for r in reqs:
+        alone = Simulation(r.params, precision="fp32")
+        alone.step(r.steps)
+        assert np.array_equal(alone.pops(), r.result["populations"])
+        assert alone.stats()["node_updates"] == r.result["stats"]["node_updates"]
+        assert np.array_equal(alone.heights(), r.result["heights"])
+        alone.close()
+    s = serving.summary(reqs, srv)
+    assert s["p50_s"] <= s["p99_s"] and s["aggregate_mlups"] > 0
