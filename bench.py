@@ -57,7 +57,12 @@ def workload_config(precision: str) -> dict:
         "lattice": [p["width"], p["height"]],
         "growth_mode": p["growth_mode"],
         "precision": precision,
-        "l2": "no flush: the active window's two FP32 population copies (~600 MB) exceed the 129 MB L2",
+        "l2": (f"no flush: each step reads one {precision} population copy of the active window "
+               f"(~{9 * p['width'] * 1026 * {'fp64': 8, 'fp32': 4}.get(precision, 2) / 1e6:.0f} MB) and "
+               f"writes the other; the 129 MB L2 holds less than that"
+               if precision != "fp16" and precision != "bf16" else
+               f"no flush; NOTE each step reads only ~{9 * p['width'] * 1026 * 2 / 1e6:.0f} MB of 16-bit "
+               f"populations, less than the 129 MB L2 (storage_16bit measures on a lattice twice as wide)"),
         "parallelism": "replicas",
     }
 
@@ -209,6 +214,55 @@ def measure_ensemble(n: int = 256, steps: int = 200, warm: int = 5) -> dict:
             "speedup": batched / single if single > 0 else None}
 
 
+def measure_storage(params: dict, precision: str, steps: int = 1000, warm: int = 10) -> dict:
+    """One storage precision on `params`: whole-step rate by CUDA events
+    over `steps` steps, and the update kernel's average launch time (one
+    launch in 16 timed) against the measured copy peak."""
+    import torch
+    from paper_2303_02210_gb300.lbm import Simulation
+    sim = Simulation(params, precision=precision)
+    stream = sim.stream
+    sim.step(warm)
+    sim.sync()
+    n0 = sim.stats()["node_updates"]
+    sim.lbm_timing_stride(16)
+    sim.lbm_timing_enable((steps + 15) // 16)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nodes = sim.stats()["node_updates"] - n0
+    k_launches, k_ms, k_nodes = sim.lbm_timing_read()
+    bpn = sim.lbm_bytes_per_node()
+    kernel = {1: "k_update", 2: "k_update_tma"}[sim.stats()["update_kernel"]]
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    peak, _ = measured_peak()
+    launch_ms = k_ms / max(k_launches, 1)
+    achieved = bpn * (k_nodes / steps) / (launch_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
+    return {"precision": precision, "value": nodes / (ms * 1e-3) / 1e6, "unit": UNIT,
+            "ms_per_step": ms / steps, "steps": steps, "bytes_per_node": bpn, "kernel": kernel,
+            "avg_launch_ms": launch_ms, "achieved_gbs": achieved, "frac": achieved / peak}
+
+
+def measure_storage_16bit() -> dict:
+    """FP32 against 16-bit storage on the headline workload made twice as
+    wide (8192 x 2048, front at row 1024: about 8.4M active nodes), so that
+    one 16-bit population copy of the window (about 151 MB, read every step)
+    is still larger than the 129 MB L2."""
+    p = wl.lattice_edge(seed=1, width=8192)
+    out = {"workload": (f"D2Q9 {p['width']}x{p['height']}, otherwise as the headline workload; per step "
+                        f"one population copy of the window is read: ~{9 * p['width'] * 1026 * 2 / 1e6:.0f} MB "
+                        f"16-bit, ~{9 * p['width'] * 1026 * 4 / 1e6:.0f} MB FP32, against the 129 MB L2")}
+    for pr in ("fp32", "fp16", "bf16"):
+        out[pr] = measure_storage(p, pr)
+    return out
+
+
 def measure_serving(n: int = 100, rate: float = 200.0, steps=(500, 5000), budget_gb: float = 100.0) -> dict:
     """The served form: a fixed trace of n requests (Poisson arrivals at
     `rate` per second, widths log-uniform 128..4096, height = width / 2, bulk,
@@ -278,11 +332,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--update-kernel", default="auto", choices=["auto", "plain", "tma", "tma1", "tma_sel"])
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble and serving measurements")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the batched-ensemble, serving and 16-bit storage measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -380,7 +435,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic", "config": workload_config(args.precision),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -399,6 +454,7 @@ def main():
     if world == 1 and not args.no_ensemble:
         line["ensemble"] = measure_ensemble()
         line["serving"] = measure_serving()
+        line["storage_16bit"] = measure_storage_16bit()
     if world == 1 and not args.no_cpu_baseline:
         rate, dt, window = oracle_rate(workload_params(), args.cpu_steps)
         line["cpu_baseline"] = {

@@ -52,7 +52,7 @@ enum {
 enum { LBM_FRONT_FLAT = 0, LBM_FRONT_SINUSOIDAL = 1, LBM_FRONT_FULL = 2 };
 enum { LBM_WALL_FIXED = 0, LBM_WALL_ADVANCE = 1 };
 enum { LBM_NEGFIX_LITERAL = 0, LBM_NEGFIX_RESCALE = 1 };
-enum { LBM_FP32 = 0, LBM_FP64 = 1 };
+enum { LBM_FP32 = 0, LBM_FP64 = 1, LBM_FP16 = 2, LBM_BF16 = 3 };
 
 /*
  * Model parameters (App. A parameter list; Sec. II for the model).
@@ -70,11 +70,16 @@ enum { LBM_FP32 = 0, LBM_FP64 = 1 };
  *  edge_depth, band_rows  growth-mode extents
  *  y_periodic   1: periodic in y too, no walls (test lattices)
  *  seed, sim_id Philox key and counter word 3
- *  precision    LBM_FP32 (fast path) or LBM_FP64 (debug path, bit-exact
- *               with the CPU oracle)
- *  update_kernel 0: choose (the TMA-staged kernel for FP32 with walls in y,
- *               else the plain-load kernel); 1: plain-load kernel; 2: TMA-staged
- *               kernel (FP32 and y_periodic = 0 only)
+ *  precision    LBM_FP32 (fast path), LBM_FP64 (debug path, bit-exact
+ *               with the CPU oracle), or LBM_FP16 / LBM_BF16: 16-bit storage
+ *               of the deviation f_i - c_i from the rest state, c_i =
+ *               w_i rho_init rounded to the 16-bit type (exact for the void
+ *               and for f_i = c_i), FP32 arithmetic, 36 bytes per node
+ *               update
+ *  update_kernel 0: choose (the TMA-staged kernel for FP32 and 16-bit
+ *               storage with walls in y, else the plain-load kernel);
+ *               1: plain-load kernel; 2: TMA-staged kernel (not FP64, and
+ *               y_periodic = 0 only)
  */
 typedef struct {
     double tau, mu, rho_c, rho_cell, sigma, rho0, growth_rate;

@@ -1,11 +1,12 @@
 """Builds the CUDA library ``liblbm_gb300.so`` in-tree for sm_103a (GB300).
 
-Four translation units compile in parallel and link into one shared library
+Five translation units compile in parallel and link into one shared library
 with the C ABI of ``include/lbm.h``:
 
 * ``lbm_fp32.cu``: FP32 kernels (fast path, FMA contraction allowed);
 * ``lbm_fp64.cu``: FP64 kernels with ``-fmad=false`` (debug path, rounds like
   the FP64 CPU oracle);
+* ``lbm_fp16.cu``: 16-bit (FP16, BF16) population storage, FP32 arithmetic;
 * ``lbm_api.cu``: the C ABI, host code built with ``-ffp-contract=off``;
 * ``lbm_noalloc.cu``: the allocation-free front-height entry point.
 
@@ -25,6 +26,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {
     "lbm_fp32": [],
     "lbm_fp64": ["-fmad=false"],
+    "lbm_fp16": [],
     "lbm_api": [],
     "lbm_noalloc": [],
 }

@@ -44,6 +44,47 @@ int cuda_fail(cudaError_t e)
 
 uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
 
+// 16-bit population storage on the host side: the shift c_k = w_k rho_init
+// rounded to the storage type (weight class k: 0 rest, 1 axis, 2 diagonal),
+// and the same decode (float(s) + c, in FP32) and encode (round f - c to
+// nearest) as the kernels.
+float pop_shift(int precision, int k, double rho_init)
+{
+    const double w = k == 0 ? 4.0 / 9.0 : (k == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+    const float c = (float)(w * rho_init);
+    if (precision == LBM_FP16) return __half2float(__float2half_rn(c));
+    if (precision == LBM_BF16) return __bfloat162float(__float2bfloat16_rn(c));
+    return 0.0f;
+}
+int plane_class(int i) { return i == 0 ? 0 : (i < 5 ? 1 : 2); }
+double decode16(int precision, uint16_t bits, float c)
+{
+    float v;
+    if (precision == LBM_FP16) {
+        __half h;
+        std::memcpy(&h, &bits, 2);
+        v = __half2float(h);
+    } else {
+        __nv_bfloat16 h;
+        std::memcpy(&h, &bits, 2);
+        v = __bfloat162float(h);
+    }
+    return (double)(v + c);
+}
+uint16_t encode16(int precision, double f, float c)
+{
+    const float v = (float)f - c;
+    uint16_t bits;
+    if (precision == LBM_FP16) {
+        const __half h = __float2half_rn(v);
+        std::memcpy(&bits, &h, 2);
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        std::memcpy(&bits, &h, 2);
+    }
+    return bits;
+}
+
 struct Layout {
     int Wp, MW, hcap, ns_max;
     long long P;
@@ -55,7 +96,7 @@ struct Layout {
 Layout make_layout(const lbm_params_t &p)
 {
     Layout L{};
-    L.elem = p.precision == LBM_FP64 ? 8 : 4;
+    L.elem = p.precision == LBM_FP64 ? 8 : (p.precision == LBM_FP32 ? 4 : 2);
     // stored row: kXO columns left of x = 0 (x = -1 the ghost of W - 1), the
     // W columns, the ghost of column 0 at x = W, padding to 128 bytes of FP32
     L.Wp = (p.width + 2 * kXO + 31) / 32 * 32;
@@ -162,15 +203,19 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 // (coordinate x_stored = x + kXO, so the ghost columns are inside) with row
 // pitch Wp and plane pitch P elements; `bx` x `by` x 9 boxes. Out-of-range
 // loads read zeros.
-bool encode_population_map(CUtensorMap *m, void *base, int Wp, int H, long long P, int bx, int by)
+bool encode_population_map(CUtensorMap *m, void *base, int Wp, int H, long long P, int bx, int by, int precision)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
+    const cuuint64_t el = precision == LBM_FP32 ? 4u : 2u;
+    const CUtensorMapDataType dt = precision == LBM_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : precision == LBM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)Wp, (cuuint64_t)H, 9};
-    const cuuint64_t strides[2] = {(cuuint64_t)Wp * 4u, (cuuint64_t)P * 4u};
+    const cuuint64_t strides[2] = {(cuuint64_t)Wp * el, (cuuint64_t)P * el};
     const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 9};
     const cuuint32_t estr[3] = {1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    return enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -223,10 +268,10 @@ int lbm_validate(const lbm_params_t *p)
         return LBM_ERR_INVALID_ARG;
     if (p->wall_mode != LBM_WALL_FIXED && p->wall_mode != LBM_WALL_ADVANCE) return LBM_ERR_INVALID_ARG;
     if (p->negfix_mode != LBM_NEGFIX_LITERAL && p->negfix_mode != LBM_NEGFIX_RESCALE) return LBM_ERR_INVALID_ARG;
-    if (p->precision != LBM_FP32 && p->precision != LBM_FP64) return LBM_ERR_INVALID_ARG;
+    if (p->precision < LBM_FP32 || p->precision > LBM_BF16) return LBM_ERR_INVALID_ARG;
     if (p->y_periodic != 0 && p->y_periodic != 1) return LBM_ERR_INVALID_ARG;
     if (p->update_kernel < 0 || p->update_kernel > 4) return LBM_ERR_INVALID_ARG;
-    if (p->update_kernel >= 2 && (p->precision != LBM_FP32 || p->y_periodic)) return LBM_ERR_INVALID_ARG;
+    if (p->update_kernel >= 2 && (p->precision == LBM_FP64 || p->y_periodic)) return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
 
@@ -264,7 +309,10 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     s->p = *p;
     s->device = dev;
     s->L = make_layout(*p);
-    s->kt = p->precision == LBM_FP64 ? &kTableF64 : &kTableF32;
+    s->kt = p->precision == LBM_FP64   ? &kTableF64
+            : p->precision == LBM_FP16 ? &kTableF16
+            : p->precision == LBM_BF16 ? &kTableBF16
+                                       : &kTableF32;
     s->stream = (cudaStream_t)stream;
     s->cur = 0;
     s->step = 0;
@@ -353,6 +401,7 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     d.f_ow1 = (float)(d.omega * (1.0 / 9.0));
     d.f_ow5 = (float)(d.omega * (1.0 / 36.0));
     d.f_two_sigma = (float)(2.0 * p->sigma);
+    for (int k = 0; k < 3; ++k) d.pop_shift[k] = pop_shift(p->precision, k, p->rho_init);
     const int bps = s->kt->update_blocks_per_sm();
     // persistent grid: as many blocks as fit on the SMs, rounded down to a
     // multiple of the column tiles (each block keeps one column tile)
@@ -377,14 +426,14 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     s->tma_grid = nsm;
     s->tma_variant = p->update_kernel == 3 ? 1 : 0;
     const bool tma_inject = p->update_kernel != 4; // 4: the selector injects into global memory
-    if (p->precision == LBM_FP32 && !p->y_periodic && p->update_kernel != 1) {
+    if (s->kt->tma_update && !p->y_periodic && p->update_kernel != 1) {
         const int ty = launch_update_tma_rows(s->tma_variant);
         d.upd_tyl2 = 0;
         while ((1 << d.upd_tyl2) < ty) ++d.upd_tyl2;
         bool ok = true;
         for (int b = 0; b < 2 && ok; ++b)
-            ok = encode_population_map(&s->maps[b], (char *)d.f[b] - (size_t)kXO * 4u, d.Wp, d.H, d.P, kTmaBoxX + 8,
-                                       ty + 2);
+            ok = encode_population_map(&s->maps[b], (char *)d.f[b] - (size_t)kXO * L.elem, d.Wp, d.H, d.P,
+                                       kTmaBoxX + 8, ty + 2, p->precision);
         s->use_tma = ok;
         d.inject_in_update = ok && tma_inject ? 1 : 0;
         // persistent CTAs, but no more than one per eight tiles of the whole
@@ -440,7 +489,7 @@ static cudaError_t launch_update(lbm_sim *s, cudaStream_t st, bool pdl = true)
         cudaError_t e = s->kt->inject(s->d, st);
         if (e != cudaSuccess) return e;
     }
-    return s->use_tma ? launch_update_tma_f32(s->d, s->maps, s->tma_variant, pdl, st) : s->kt->update(s->d, st);
+    return s->use_tma ? s->kt->tma_update(s->d, s->maps, s->tma_variant, pdl, st) : s->kt->update(s->d, st);
 }
 
 // Host-side mirror of one completed step (the kernels keep theirs on the device).
@@ -599,9 +648,14 @@ int lbm_populations(lbm_sim *s, double *f_host)
     const size_t n = (size_t)9 * W * H;
     if (el == 8) {
         std::memcpy(f_host, tmp.data(), n * 8);
-    } else {
+    } else if (el == 4) {
         const float *t = (const float *)tmp.data();
         for (size_t k = 0; k < n; ++k) f_host[k] = (double)t[k];
+    } else {
+        const uint16_t *t = (const uint16_t *)tmp.data();
+        const size_t plane = (size_t)W * H;
+        for (size_t k = 0; k < n; ++k)
+            f_host[k] = decode16(s->p.precision, t[k], s->d.pop_shift[plane_class((int)(k / plane))]);
     }
     return LBM_OK;
 }
@@ -618,9 +672,14 @@ int lbm_set_populations(lbm_sim *s, const double *f_host)
     std::vector<char> tmp(n * el);
     if (el == 8) {
         std::memcpy(tmp.data(), f_host, n * 8);
-    } else {
+    } else if (el == 4) {
         float *t = (float *)tmp.data();
         for (size_t k = 0; k < n; ++k) t[k] = (float)f_host[k];
+    } else {
+        uint16_t *t = (uint16_t *)tmp.data();
+        const size_t plane = (size_t)W * H;
+        for (size_t k = 0; k < n; ++k)
+            t[k] = encode16(s->p.precision, f_host[k], s->d.pop_shift[plane_class((int)(k / plane))]);
     }
     for (int b = 0; b < 2; ++b)
         for (int i = 0; i < 9; ++i) {
@@ -833,7 +892,7 @@ int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
     // one-time kernel attributes are set outside the capture
     for (int32_t i = 0; i < n && e == cudaSuccess; ++i)
-        if (sims[i]->use_tma) e = prepare_update_tma_f32(sims[i]->d, sims[i]->tma_variant);
+        if (sims[i]->use_tma) e = sims[i]->kt->tma_prepare(sims[i]->d, sims[i]->tma_variant);
     for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
         cudaStream_t st = nullptr;
         cudaEvent_t ev = nullptr;

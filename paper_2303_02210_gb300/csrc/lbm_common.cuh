@@ -7,6 +7,8 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -180,6 +182,9 @@ struct SimDev {
     // the same constants rounded to float once on the host, so that no kernel
     // evaluates double arithmetic per node (the FP64 pipe is narrow)
     float f_rho_c, f_omega, f_cmu, f_om1, f_ow0, f_ow1, f_ow5, f_two_sigma;
+    // 16-bit storage: the rest-state populations c_k = w_k rho_init, rounded
+    // to the 16-bit type (k: 0 rest, 1 axis, 2 diagonal); unused otherwise
+    float pop_shift[3];
     int update_grid;     // persistent grid of the update kernel
 };
 
@@ -201,17 +206,20 @@ struct KernelTable {
     int (*plan_blocks_per_sm)();
     int (*update_blocks_per_sm)();
     int update_tile_x; // columns per block of the update kernel
+    // TMA-staged update (lbm_update_tma.cuh; null for FP64 storage). maps[b]
+    // loads from copy b (box (kTmaBoxX + 8) x (rows per tile + 2) x 9, in
+    // stored-row coordinates). tma_prepare sets the kernel attributes a
+    // launch needs (the first launch does it too); pdl: launch as a
+    // programmatic dependent of the preceding planner kernel.
+    cudaError_t (*tma_prepare)(const SimDev &, int variant);
+    cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t);
 };
 
 extern const KernelTable kTableF32;
 extern const KernelTable kTableF64;
+extern const KernelTable kTableF16;
+extern const KernelTable kTableBF16;
 
-// TMA-staged FP32 update (lbm_update_tma.cuh). maps[b] loads from copy b
-// (box (kTmaBoxX + 8) x (rows per tile + 2) x 9, in stored-row coordinates).
-// Sets the kernel attributes a launch needs (done by the first launch too).
-cudaError_t prepare_update_tma_f32(const SimDev &d, int variant);
-// pdl: launch as a programmatic dependent of the preceding planner kernel.
-cudaError_t launch_update_tma_f32(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s);
 // CTAs the TMA-staged update kernel runs on this many SMs.
 int launch_update_tma_ctas(int nsm, int variant);
 
@@ -219,8 +227,9 @@ int launch_update_tma_ctas(int nsm, int variant);
 int lbm_record_cuda_error(cudaError_t e);
 // Rows per tile of a TMA-staged update variant.
 int launch_update_tma_rows(int variant);
-// Stored columns left of x = 0 (16 bytes of FP32, so that tile boxes start
-// aligned): x = -1 is the ghost of column W - 1.
+// Stored columns left of x = 0 (so that tile boxes start at stored column
+// 128 k, 16-byte aligned for every storage type): x = -1 is the ghost of
+// column W - 1.
 constexpr int kXO = 4;
 constexpr int kTmaBoxX = 128;
 constexpr int kTmaMaxCtas = 1024; // the reciprocal above is exact for tile < 2^22

@@ -3,15 +3,7 @@
 #include "lbm_update_tma.cuh"
 
 namespace lbm {
-const KernelTable kTableF32 = make_table<float>();
-
-
-cudaError_t prepare_update_tma_f32(const SimDev &d, int variant) { return prepare_update_tma(d, variant); }
-
-cudaError_t launch_update_tma_f32(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s)
-{
-    return launch_update_tma(d, maps, variant, pdl, s);
-}
+const KernelTable kTableF32 = make_table<float>(&prepare_update_tma<float>, &launch_update_tma<float>);
 
 int launch_update_tma_ctas(int nsm, int variant) { return tma_ctas_per_sm(variant) * nsm; }
 

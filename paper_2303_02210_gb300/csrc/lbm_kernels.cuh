@@ -49,6 +49,60 @@ __device__ __forceinline__ R rho_c_of(const SimDev &d)
         return d.f_rho_c;
 }
 
+// ===========================================================================
+// Population storage. FP32 and FP64 hold f_i as it is and compute in the
+// same type. The 16-bit forms (FP16, BF16) hold the deviation f_i - c_i from
+// the rest state of density rho_init, c_i = w_i rho_init rounded to the
+// 16-bit type, and compute in FP32: decode is float(s) + c_i, encode rounds
+// f_i - c_i to nearest. Because c_i is itself a 16-bit value, f_i = 0 (the
+// void) and f_i = c_i are both stored exactly, and rounding is monotone, so
+// a non-negative f_i never decodes below zero. c_i depends only on the
+// weight class of i, which i and opp(i) share, so a bounce-back load may
+// decode with the class of the plane it reads.
+__host__ __device__ constexpr int wclass(int q) { return q == 0 ? 0 : (q < 5 ? 1 : 2); }
+
+template <typename S>
+struct Pop {
+    using R = S; // arithmetic type
+    static constexpr bool kShifted = false;
+    __device__ explicit Pop(const SimDev &) {}
+    __device__ R ld(S v, int) const { return v; }
+    __device__ S st(R v, int) const { return v; }
+};
+
+template <typename S, typename Cvt>
+struct PopShifted {
+    using R = float;
+    static constexpr bool kShifted = true;
+    float c0, c1, c2;
+    __device__ explicit PopShifted(const SimDev &d) : c0(d.pop_shift[0]), c1(d.pop_shift[1]), c2(d.pop_shift[2]) {}
+    __device__ float shift(int q) const
+    {
+        const int k = wclass(q);
+        return k == 0 ? c0 : (k == 1 ? c1 : c2);
+    }
+    __device__ float ld(S v, int q) const { return Cvt::to_f(v) + shift(q); }
+    __device__ S st(float v, int q) const { return Cvt::from_f(v - shift(q)); }
+};
+struct CvtHalf {
+    static __device__ float to_f(__half v) { return __half2float(v); }
+    static __device__ __half from_f(float v) { return __float2half_rn(v); }
+};
+struct CvtBf16 {
+    static __device__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+};
+template <>
+struct Pop<__half> : PopShifted<__half, CvtHalf> {
+    __device__ explicit Pop(const SimDev &d) : PopShifted<__half, CvtHalf>(d) {}
+};
+template <>
+struct Pop<__nv_bfloat16> : PopShifted<__nv_bfloat16, CvtBf16> {
+    __device__ explicit Pop(const SimDev &d) : PopShifted<__nv_bfloat16, CvtBf16>(d) {}
+};
+template <typename S>
+using arith_t = typename Pop<S>::R;
+
 __device__ __forceinline__ long long warp_sum_ll(long long v)
 {
 #pragma unroll
@@ -94,11 +148,13 @@ __device__ __forceinline__ long long pull_slot(const SimDev &d, int y_r, int x, 
 // Initial state (App. A, first paragraph): rho = rho_init (optionally
 // jittered by U[1 - j, 1 + j]) below the front, zero above, u = 0,
 // f_i = f^SS_i(rho, 0) = w_i rho. Written into both population copies.
-template <typename R>
+template <typename S>
 __global__ void k_fill(SimDev d)
 {
-    R *f0 = (R *)d.f[0];
-    R *f1 = (R *)d.f[1];
+    using R = arith_t<S>;
+    const Pop<S> pc(d);
+    S *f0 = (S *)d.f[0];
+    S *f1 = (S *)d.f[1];
     if (blockIdx.x == 0 && threadIdx.x == 0) { // scalar block (zeroed before this launch)
         d.sc->maxmass_accum = -1;
         d.sc->low_acc = 0x7fffffff;
@@ -121,7 +177,7 @@ __global__ void k_fill(SimDev d)
         const long long o = (long long)y * d.Wp + xs;
 #pragma unroll
         for (int i = 0; i < NQ; ++i) {
-            const R v = (R)(wq<double>(i) * rho);
+            const S v = pc.st((R)(wq<double>(i) * rho), i);
             f0[i * d.P + o] = v;
             f1[i * d.P + o] = v;
         }
@@ -130,17 +186,17 @@ __global__ void k_fill(SimDev d)
 
 // Ghost columns x = -1 and x = W of every row of both copies from columns
 // W - 1 and 0 (after the caller has written the populations).
-template <typename R>
+template <typename S>
 __global__ void k_ghosts(SimDev d)
 {
     const long long total = 2LL * NQ * d.H;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < 2 * total;
          k += (long long)gridDim.x * blockDim.x) {
-        R *f = (R *)d.f[k >= total ? 1 : 0];
+        S *f = (S *)d.f[k >= total ? 1 : 0];
         const long long r = k >= total ? k - total : k;
         const int side = (int)(r & 1);
         const long long row = r >> 1; // plane * H + y
-        R *base = f + (row / d.H) * d.P + (row % d.H) * d.Wp;
+        S *base = f + (row / d.H) * d.P + (row % d.H) * d.Wp;
         if (side == 0)
             base[-1] = base[d.W - 1];
         else
@@ -150,10 +206,12 @@ __global__ void k_ghosts(SimDev d)
 
 // Occupancy mask, exact mass and highest mass row of rows [y_r, H) of copy
 // `cur` (initial state, or populations set by the caller).
-template <typename R>
+template <typename S>
 __global__ void k_scan(SimDev d, int cur)
 {
-    const R *f = (const R *)d.f[cur];
+    using R = arith_t<S>;
+    const Pop<S> pc(d);
+    const S *f = (const S *)d.f[cur];
     const int y_r = d.sc->y_r;
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -169,11 +227,11 @@ __global__ void k_scan(SimDev d, int cur)
         bool any = false;
         if (ok) {
             const long long n = (long long)y * d.Wp + x;
-            rho = f[n];
+            rho = pc.ld(f[n], 0);
             any = rho != R(0);
 #pragma unroll
             for (int i = 1; i < NQ; ++i) {
-                const R v = f[i * d.P + n];
+                const R v = pc.ld(f[i * d.P + n], i);
                 rho = rho + v;
                 any |= v != R(0);
             }
@@ -472,15 +530,17 @@ __device__ __forceinline__ R fix_negative(R *fo, int mode)
 // ===========================================================================
 // Fused update of the active window (App. A steps 1, 2, 4-7; the injection of
 // step 3 was already added to the pre-stream slots by k_plan).
-template <typename R, int TPB, int NR>
+template <typename S, int TPB, int NR>
 __global__ void __launch_bounds__(TPB) k_update(SimDev d)
 {
+    using R = arith_t<S>;
+    const Pop<S> pc(d);
     // the step is read from the device (so a captured step replays as is):
     // step t reads copy t & 1
     const uint32_t t = (uint32_t)d.sc->step;
     const int cur = (int)(t & 1u);
-    const R *__restrict__ fin = (const R *)d.f[cur];
-    R *__restrict__ fout = (R *)d.f[cur ^ 1];
+    const S *__restrict__ fin = (const S *)d.f[cur];
+    S *__restrict__ fout = (S *)d.f[cur ^ 1];
     const int y_r = d.sc->y_r, y_copy = d.sc->y_copy, y_hi = d.sc->y_hi;
     const int W = d.W, H = d.H, Wp = d.Wp;
     const long long P = d.P;
@@ -526,29 +586,31 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d)
                     const bool bb_hi = !periodic && y + 1 >= H;
                     const int ym = periodic ? (y == 0 ? H - 1 : y - 1) : y - 1;
                     const int yp = periodic ? (y == H - 1 ? 0 : y + 1) : y + 1;
-                    const R *rc = fin + (long long)y * Wp;
-                    const R *rm = fin + (long long)ym * Wp;
-                    const R *rp = fin + (long long)yp * Wp;
-                    fs[r][0] = rc[x];
-                    fs[r][1] = rc[P + xm];
-                    fs[r][3] = rc[3 * P + xp];
+                    const S *rc = fin + (long long)y * Wp;
+                    const S *rm = fin + (long long)ym * Wp;
+                    const S *rp = fin + (long long)yp * Wp;
+                    // (a bounce-back load decodes with the class of the plane
+                    // it reads, which is the class of the one it fills)
+                    fs[r][0] = pc.ld(rc[x], 0);
+                    fs[r][1] = pc.ld(rc[P + xm], 1);
+                    fs[r][3] = pc.ld(rc[3 * P + xp], 3);
                     if (bb_lo) {
-                        fs[r][2] = rc[4 * P + x];
-                        fs[r][5] = rc[7 * P + x];
-                        fs[r][6] = rc[8 * P + x];
+                        fs[r][2] = pc.ld(rc[4 * P + x], 4);
+                        fs[r][5] = pc.ld(rc[7 * P + x], 7);
+                        fs[r][6] = pc.ld(rc[8 * P + x], 8);
                     } else {
-                        fs[r][2] = rm[2 * P + x];
-                        fs[r][5] = rm[5 * P + xm];
-                        fs[r][6] = rm[6 * P + xp];
+                        fs[r][2] = pc.ld(rm[2 * P + x], 2);
+                        fs[r][5] = pc.ld(rm[5 * P + xm], 5);
+                        fs[r][6] = pc.ld(rm[6 * P + xp], 6);
                     }
                     if (bb_hi) {
-                        fs[r][4] = rc[2 * P + x];
-                        fs[r][7] = rc[5 * P + x];
-                        fs[r][8] = rc[6 * P + x];
+                        fs[r][4] = pc.ld(rc[2 * P + x], 2);
+                        fs[r][7] = pc.ld(rc[5 * P + x], 5);
+                        fs[r][8] = pc.ld(rc[6 * P + x], 6);
                     } else {
-                        fs[r][4] = rp[4 * P + x];
-                        fs[r][7] = rp[7 * P + xp];
-                        fs[r][8] = rp[8 * P + xm];
+                        fs[r][4] = pc.ld(rp[4 * P + x], 4);
+                        fs[r][7] = pc.ld(rp[7 * P + xp], 7);
+                        fs[r][8] = pc.ld(rp[8 * P + xm], 8);
                     }
                 }
             }
@@ -576,12 +638,25 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d)
                 const int wx0 = x - lane;
                 if (lane == 0 && wx0 < W) d.mask[(long long)y * d.MW + (wx0 >> 5)] = bits;
                 if (colok) {
-                    R *o = fout + (long long)y * Wp + x;
+                    S *o = fout + (long long)y * Wp + x;
+                    R ro;
+                    if constexpr (Pop<S>::kShifted) {
+                        // the node's mass is that of what is stored: the
+                        // decoded 16-bit values, summed in index order
+                        ro = R(0);
 #pragma unroll
-                    for (int i = 0; i < NQ; ++i) o[i * P] = fo[i];
+                        for (int i = 0; i < NQ; ++i) {
+                            const S v = pc.st(fo[i], i);
+                            o[i * P] = v;
+                            ro = i == 0 ? pc.ld(v, 0) : ro + pc.ld(v, i);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < NQ; ++i) o[i * P] = fo[i];
+                        ro = node_mass<R>(fo, rho, added);
+                    }
                     // populations are non-negative after every step, so the
                     // node holds mass iff their sum is non-zero
-                    const R ro = node_mass<R>(fo, rho, added);
                     mass += fix24<R>(ro);
                     if (ro != R(0)) maxrow = y;
                 }
@@ -605,15 +680,17 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d)
 // open-addressing table that merges repeated (node, pair) draws, and the
 // per-division records of the TMA-staged update.
 
-template <typename R>
-__device__ __forceinline__ R rho_star(const SimDev &d, const R *f, int y_r, int x, int y)
+template <typename S>
+__device__ __forceinline__ arith_t<S> rho_star(const SimDev &d, const S *f, int y_r, int x, int y)
 {
+    using R = arith_t<S>;
+    const Pop<S> pc(d);
     long long o[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) o[q] = pull_slot(d, y_r, x, y, q);
     R v[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] = f[o[q]];
+    for (int q = 0; q < NQ; ++q) v[q] = pc.ld(f[o[q]], q);
     R r = v[0];
 #pragma unroll
     for (int q = 1; q < NQ; ++q) r = r + v[q];
@@ -695,10 +772,11 @@ __device__ __forceinline__ void division_record(const SimDev &d, int e, uint32_t
 }
 
 // rho and u of copy `cur` into device arrays of W*H doubles (Eq. 1).
-template <typename R>
+template <typename S>
 __global__ void k_fields(SimDev d, int cur, double *rho, double *ux, double *uy)
 {
-    const R *f = (const R *)d.f[cur];
+    const Pop<S> pc(d);
+    const S *f = (const S *)d.f[cur];
     const long long total = (long long)d.W * d.H;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
          k += (long long)gridDim.x * blockDim.x) {
@@ -706,7 +784,7 @@ __global__ void k_fields(SimDev d, int cur, double *rho, double *ux, double *uy)
         const long long o = (long long)y * d.Wp + x;
         double g[NQ];
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) g[i] = (double)f[i * d.P + o];
+        for (int i = 0; i < NQ; ++i) g[i] = (double)pc.ld(f[i * d.P + o], i);
         double r = g[0];
 #pragma unroll
         for (int i = 1; i < NQ; ++i) r = r + g[i];

@@ -1,4 +1,5 @@
-// Launchers of one storage type, collected in the table the C ABI dispatches
+// Launchers of one population storage type (float, double, __half or
+// __nv_bfloat16), collected in the table the C ABI dispatches
 // through.
 #pragma once
 
@@ -7,62 +8,64 @@
 
 namespace lbm {
 
-template <typename R>
+template <typename S>
 struct Launch {
     static constexpr int UPD_TPB = 128;
-    static constexpr int UPD_NR = sizeof(R) == 4 ? 2 : 1;
+    static constexpr int UPD_NR = sizeof(S) == 8 ? 1 : 2;
 
     static cudaError_t fill(const SimDev &d, cudaStream_t s)
     {
-        k_fill<R><<<4 * 152, 256, 0, s>>>(d);
+        k_fill<S><<<4 * 152, 256, 0, s>>>(d);
         return cudaGetLastError();
     }
     static cudaError_t ghosts(const SimDev &d, cudaStream_t s)
     {
-        k_ghosts<R><<<152, 256, 0, s>>>(d);
+        k_ghosts<S><<<152, 256, 0, s>>>(d);
         return cudaGetLastError();
     }
     static cudaError_t scan(const SimDev &d, int cur, cudaStream_t s)
     {
-        k_scan<R><<<4 * 152, 256, 0, s>>>(d, cur);
+        k_scan<S><<<4 * 152, 256, 0, s>>>(d, cur);
         return cudaGetLastError();
     }
     static cudaError_t plan(const SimDev &d, int init, cudaStream_t s)
     {
-        return launch_plan<R>(d, init, s);
+        return launch_plan<S>(d, init, s);
     }
     static cudaError_t inject(const SimDev &d, cudaStream_t s)
     {
-        k_inject<R><<<152, 128, 0, s>>>(d);
+        k_inject<S><<<152, 128, 0, s>>>(d);
         return cudaGetLastError();
     }
     static cudaError_t update(const SimDev &d, cudaStream_t s)
     {
-        k_update<R, UPD_TPB, UPD_NR><<<d.update_grid, UPD_TPB, 0, s>>>(d);
+        k_update<S, UPD_TPB, UPD_NR><<<d.update_grid, UPD_TPB, 0, s>>>(d);
         return cudaGetLastError();
     }
     static cudaError_t fields(const SimDev &d, int cur, double *rho, double *ux, double *uy, cudaStream_t s)
     {
-        k_fields<R><<<4 * 152, 256, 0, s>>>(d, cur, rho, ux, uy);
+        k_fields<S><<<4 * 152, 256, 0, s>>>(d, cur, rho, ux, uy);
         return cudaGetLastError();
     }
     static int update_blocks_per_sm()
     {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<R, UPD_TPB, UPD_NR>, UPD_TPB, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update<S, UPD_TPB, UPD_NR>, UPD_TPB, 0) != cudaSuccess)
             return 0;
         return n;
     }
 };
 
-template <typename R>
-constexpr KernelTable make_table()
+template <typename S>
+constexpr KernelTable make_table(cudaError_t (*tma_prepare)(const SimDev &, int) = nullptr,
+                                 cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *, int, bool,
+                                                           cudaStream_t) = nullptr)
 {
-    return KernelTable{(int)sizeof(R),       &Launch<R>::fill,          &Launch<R>::ghosts,
-                       &Launch<R>::scan,     &Launch<R>::plan,          &Launch<R>::inject,
-                       &Launch<R>::update,
-                       &Launch<R>::fields,   &plan_blocks_per_sm<R>,    &Launch<R>::update_blocks_per_sm,
-                       Launch<R>::UPD_TPB};
+    return KernelTable{(int)sizeof(S),       &Launch<S>::fill,          &Launch<S>::ghosts,
+                       &Launch<S>::scan,     &Launch<S>::plan,          &Launch<S>::inject,
+                       &Launch<S>::update,
+                       &Launch<S>::fields,   &plan_blocks_per_sm<S>,    &Launch<S>::update_blocks_per_sm,
+                       Launch<S>::UPD_TPB,   tma_prepare,               tma_update};
 }
 
 } // namespace lbm

@@ -127,10 +127,11 @@ __device__ __forceinline__ void plan_select(const SimDev &d, uint32_t key, int r
 
 // Acceptance of a candidate (as `accept`, with the heights of this launch
 // read from L2: other blocks wrote them before the last grid barrier).
-template <typename R>
-__device__ __forceinline__ bool plan_accept(const SimDev &d, const R *f, int y_r, const Candidate &c)
+template <typename S>
+__device__ __forceinline__ bool plan_accept(const SimDev &d, const S *f, int y_r, const Candidate &c)
 {
-    const R rs = rho_star<R>(d, f, y_r, c.x, c.y);
+    using R = arith_t<S>;
+    const R rs = rho_star<S>(d, f, y_r, c.x, c.y);
     switch (d.growth_mode) {
     case GROW_BULK:
     case GROW_BAND: return rs >= rho_c_of<R>(d);
@@ -157,15 +158,16 @@ static __device__ __noinline__ void plan_ns(double growth_rate, double rho_cell,
     *kcf = ceil((double)*ns_req * ratio * 1.15) + 64.0;
 }
 
-template <typename R>
+template <typename S>
 __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
 {
+    using R = arith_t<S>;
     DevScalars *sc = d.sc;
     // the state to observe is copy tn & 1, tn the step the selection is for:
     // the current step count for the initial state, else the next one
     const uint32_t tn = (uint32_t)sc->step + (init ? 0u : 1u);
     const int cur = (int)(tn & 1u);
-    R *f = (R *)d.f[cur];
+    S *f = (S *)d.f[cur];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = (int)gridDim.x, blk = (int)blockIdx.x;
     __shared__ long long s_ll[PLAN_WARPS];
@@ -328,9 +330,10 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
         for (long long k = (long long)blk * PLAN_NT + tid; k < n; k += (long long)G * PLAN_NT) {
             const int y = y_r + (int)(k / d.W), x = (int)(k % d.W);
             const long long o = (long long)y * d.Wp + x;
-            R r = f[o];
+            const Pop<S> pc(d);
+            R r = pc.ld(f[o], 0);
 #pragma unroll
-            for (int i = 1; i < NQ; ++i) r = r + f[i * d.P + o];
+            for (int i = 1; i < NQ; ++i) r = r + pc.ld(f[i * d.P + o], i);
             fm += fix24<R>(r);
         }
         fm = plan_block_sum(fm, s_ll);
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
             uint32_t key = 0u;
             if (j < C && k < kc) {
                 const Candidate c = draw_candidate(d, k, tn, ylo, nwin);
-                a = plan_accept<R>(d, f, nyr, c);
+                a = plan_accept<S>(d, f, nyr, c);
                 key = pack_key(c.x, c.y, c.pair);
             }
             int t_i;
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
             uint32_t key = 0u;
             if (k < cap) {
                 const Candidate c = draw_candidate(d, k, tn, ylo, nwin);
-                a = plan_accept<R>(d, f, nyr, c);
+                a = plan_accept<S>(d, f, nyr, c);
                 key = pack_key(c.x, c.y, c.pair);
             }
             int tot_r;
@@ -559,12 +562,14 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
 // (node, pair) of step t, right before the update of step t. Distinct
 // (node, pair) never share a slot (each slot streams into exactly one
 // direction of one node).
-template <typename R>
+template <typename S>
 __global__ void k_inject(SimDev d)
 {
+    using R = arith_t<S>;
+    const Pop<S> pc(d);
     const uint32_t t = (uint32_t)d.sc->step;
     const int cur = (int)(t & 1u);
-    R *f = (R *)d.f[cur];
+    S *f = (S *)d.f[cur];
     const int n = d.sc->rec_n, y_r = d.sc->y_r;
     const size_t buf = (size_t)(t & 1u) * (size_t)d.ns_max;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -575,8 +580,10 @@ __global__ void k_inject(SimDev d)
         const R add = (R)((double)cnt * d.half_cell);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const long long o = pull_slot(d, y_r, x, y, h == 0 ? pair_a(p) : pair_b(p));
-            const R v = f[o] + add;
+            const int q = h == 0 ? pair_a(p) : pair_b(p);
+            const long long o = pull_slot(d, y_r, x, y, q);
+            // (the slot is in plane q or opp(q): one weight class)
+            const S v = pc.st(pc.ld(f[o], q) + add, q);
             f[o] = v;
             // the ghost copy of an edge column (read by the TMA-staged update)
             const int xc = (int)((o % d.P) % d.Wp);
@@ -586,7 +593,7 @@ __global__ void k_inject(SimDev d)
     }
 }
 
-template <typename R>
+template <typename S>
 cudaError_t launch_plan(const SimDev &d, int init, cudaStream_t s)
 {
     // a cooperative launch: every block resident at once (the grid barriers
@@ -600,14 +607,14 @@ cudaError_t launch_plan(const SimDev &d, int init, cudaStream_t s)
     la[0].val.cooperative = 1;
     cfg.attrs = la;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_plan<R>, d, init);
+    return cudaLaunchKernelEx(&cfg, k_plan<S>, d, init);
 }
 
-template <typename R>
+template <typename S>
 int plan_blocks_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plan<R>, PLAN_NT, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plan<S>, PLAN_NT, 0) != cudaSuccess) return 0;
     return n;
 }
 

@@ -1,11 +1,11 @@
-// TMA-staged fused update (FP32 storage, walls in y), the fast path of
-// App. A steps 1-7 (step 3's divisions are added to the staged tile): the same
-// per-node arithmetic as k_update<float>, different data movement.
+// TMA-staged fused update (FP32 or 16-bit storage, walls in y), the fast path
+// of App. A steps 1-7 (step 3's divisions are added to the staged tile): the
+// same per-node arithmetic as k_update, different data movement.
 //
 // Each CTA (persistent, CTAS per SM) walks tiles of 128 columns x TY rows of
 // the active window, dealt round-robin over the grid. A tile's pre-stream
 // populations arrive in shared memory as one 3-D bulk tensor copy of box
-// 136 x (TY + 2) x 9: the tile plus 4 stored columns on each side and one row
+// 136 x (TY + 2) x 9 elements: the tile plus 4 stored columns on each side and one row
 // above and below, for all nine planes. The stored rows carry ghost copies of
 // the periodic neighbours (x = -1 holds column W - 1, x = W holds column 0), so
 // the box needs no patching and never starts outside the stored row.
@@ -17,11 +17,20 @@
 // otherwise (a CTA-wide barrier only on the tiles that receive divisions).
 //
 // Thread layout: two warps per tile row, each lane two adjacent columns
-// (2 lane, 2 lane + 1 of its warp's 64): unshifted planes are one 8-byte
-// shared load for both nodes, planes shifted in x two 4-byte loads; results
-// are 8-byte stores (256 contiguous bytes per warp and plane). Both nodes'
+// (2 lane, 2 lane + 1 of its warp's 64): unshifted planes are one paired
+// shared load for both nodes, planes shifted in x two scalar loads; results
+// are paired stores (64 contiguous elements per warp and plane). Both nodes'
 // Philox blocks are drawn together before either node is relaxed.
+//
+// 16-bit storage (FP16, BF16; the deviation from the rest state, see Pop):
+// the staged values are decoded to FP32 as they are read, the results are
+// encoded two at a time (one packed conversion per plane and node pair), and
+// a division is added to a staged slot as decode, FP32 add, encode, which
+// rounds exactly as k_inject does in global memory. The boxes are half as
+// large, so twice as many are kept in flight per CTA.
 #pragma once
+
+#include <type_traits>
 
 #include "lbm_kernels.cuh"
 #include "lbm_tma.cuh"
@@ -39,49 +48,113 @@ static_assert(kBucketCap <= TMA_EV_CAP, "a full bucket fits in shared memory");
 constexpr long long TMA_WAIT_BUDGET = 4000000000ll;
 static_assert(kXO % 4 == 0, "tile boxes start on 16-byte boundaries");
 
-template <int TY>
+template <typename S, int TY>
 struct TmaGeom {
-    static constexpr int NT = 64 * TY;                          // threads: two warps per row
+    static constexpr int NT = 64 * TY;                                 // threads: two warps per row
     static constexpr int WARPS = NT / 32;
     static constexpr int LY = TY + 2;
-    static constexpr int PLANE = LY * TMA_LX;                   // floats per staged plane
-    static constexpr int IN_FLOATS = 9 * PLANE;                 // one box
-    static constexpr int STRIDE = (IN_FLOATS + 31) / 32 * 32;   // stage pitch, 128-byte multiple
-    static constexpr uint32_t BYTES = (uint32_t)IN_FLOATS * 4u; // bytes one box copy delivers
+    static constexpr int PLANE = LY * TMA_LX;                          // elements per staged plane
+    static constexpr int IN_ELEMS = 9 * PLANE;                         // one box
+    static constexpr int STRIDE = (IN_ELEMS * (int)sizeof(S) + 127) / 128 * 128 / (int)sizeof(S); // stage pitch
+    static constexpr uint32_t BYTES = (uint32_t)IN_ELEMS * (uint32_t)sizeof(S); // one box copy delivers
 };
 
-template <int TY, int STAGES>
+template <typename S, int TY, int STAGES>
 constexpr size_t tma_smem_bytes()
 {
-    return 128 + (size_t)STAGES * TmaGeom<TY>::STRIDE * 4 + 16 * STAGES + (size_t)TMA_EV_CAP * 16 +
+    return 128 + (size_t)STAGES * TmaGeom<S, TY>::STRIDE * sizeof(S) + 16 * STAGES + (size_t)TMA_EV_CAP * 16 +
            TMA_KFLAG_WORDS * 4;
 }
-static_assert(3 * (tma_smem_bytes<4, 2>() + 1024) <= 228 * 1024, "three CTAs per SM by shared memory");
-static_assert(2 * (tma_smem_bytes<4, 3>() + 1024) <= 228 * 1024, "two CTAs per SM by shared memory");
 
-__device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+// Configurations: variant 0 three CTAs per SM, variant 1 two; tiles of four
+// rows; as many staged boxes per CTA as keep about the same bytes in flight
+// for every storage type.
+template <typename S>
+struct TmaCfg {
+    static constexpr int TY = 4;
+    static constexpr int STAGES0 = sizeof(S) == 4 ? 2 : 4;
+    static constexpr int STAGES1 = sizeof(S) == 4 ? 3 : 6;
+};
+static_assert(3 * (tma_smem_bytes<float, 4, 2>() + 1024) <= 228 * 1024, "three CTAs per SM by shared memory");
+static_assert(2 * (tma_smem_bytes<float, 4, 3>() + 1024) <= 228 * 1024, "two CTAs per SM by shared memory");
+static_assert(3 * (tma_smem_bytes<__half, 4, 4>() + 1024) <= 228 * 1024, "three CTAs per SM by shared memory");
+static_assert(2 * (tma_smem_bytes<__half, 4, 6>() + 1024) <= 228 * 1024, "two CTAs per SM by shared memory");
+
+// Two adjacent stored elements as one access.
+template <typename S> struct Pair2;
+template <> struct Pair2<float> { using T = float2; };
+template <> struct Pair2<__half> { using T = __half2; };
+template <> struct Pair2<__nv_bfloat16> { using T = __nv_bfloat162; };
+
+// Decodes the pair at `p` (aligned to the pair) of plane class q.
+template <typename S>
+__device__ __forceinline__ void ld_pair(const S *p, int q, const Pop<S> &pc, float &a, float &b)
+{
+    const typename Pair2<S>::T v = *reinterpret_cast<const typename Pair2<S>::T *>(p);
+    a = pc.ld(v.x, q);
+    b = pc.ld(v.y, q);
+}
+
+// Encodes (a, b) of plane q as one pair (one packed conversion for 16 bits;
+// each element rounds as Pop::st would).
+template <typename S>
+__device__ __forceinline__ typename Pair2<S>::T enc_pair(float a, float b, int q, const Pop<S> &pc)
+{
+    if constexpr (sizeof(S) == 4) {
+        return make_float2(a, b);
+    } else if constexpr (std::is_same<S, __half>::value) {
+        return __floats2half2_rn(a - pc.shift(q), b - pc.shift(q));
+    } else {
+        return __floats2bfloat162_rn(a - pc.shift(q), b - pc.shift(q));
+    }
+}
 
 // The populations two adjacent nodes pull: `b` points at the first node's
-// staged plane-0 value (8-byte aligned). Across the rear (REAR) or top (TOP)
-// wall a node takes its own opposite population (half-way bounce-back).
-template <int PLANE, bool REAR, bool TOP>
-__device__ __forceinline__ void pull2(const float *b, float ga[NQ], float gb[NQ])
+// staged plane-0 value (aligned to a pair). Across the rear (REAR) or top
+// (TOP) wall a node takes its own opposite population (half-way bounce-back).
+template <typename S, int PLANE, bool REAR, bool TOP>
+__device__ __forceinline__ void pull2(const S *b, float ga[NQ], float gb[NQ], const Pop<S> &pc)
 {
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
         const bool own = (ey(i) == 1 && REAR) || (ey(i) == -1 && TOP);
         if (own) {
-            const float2 v = lds2(b + opp(i) * PLANE);
-            ga[i] = v.x;
-            gb[i] = v.y;
+            ld_pair<S>(b + opp(i) * PLANE, i, pc, ga[i], gb[i]);
         } else if (ex(i) == 0) {
-            const float2 v = lds2(b + i * PLANE - ey(i) * TMA_LX);
-            ga[i] = v.x;
-            gb[i] = v.y;
+            ld_pair<S>(b + i * PLANE - ey(i) * TMA_LX, i, pc, ga[i], gb[i]);
         } else {
-            const float *p = b + i * PLANE - ey(i) * TMA_LX - ex(i);
-            ga[i] = p[0];
-            gb[i] = p[1];
+            const S *p = b + i * PLANE - ey(i) * TMA_LX - ex(i);
+            ga[i] = pc.ld(p[0], i);
+            gb[i] = pc.ld(p[1], i);
+        }
+    }
+}
+
+// Stores the results of a node pair (columns x, x + 1 at `o`), or of the first
+// node alone if !both. With 16-bit storage, ma and mb are the nodes' masses as
+// stored: the decoded values summed in index order (as in k_update).
+template <typename S>
+__device__ __forceinline__ void store_nodes(S *o, long long P, const float fa[NQ], const float fb[NQ], bool both,
+                                            const Pop<S> &pc, float &ma, float &mb)
+{
+    ma = mb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        if (both) {
+            const typename Pair2<S>::T v = enc_pair<S>(fa[i], fb[i], i, pc);
+            *reinterpret_cast<typename Pair2<S>::T *>(o + i * P) = v;
+            if constexpr (Pop<S>::kShifted) {
+                const float da = pc.ld(v.x, i), db = pc.ld(v.y, i);
+                ma = i == 0 ? da : ma + da;
+                mb = i == 0 ? db : mb + db;
+            }
+        } else {
+            const S v = pc.st(fa[i], i);
+            o[i * P] = v;
+            if constexpr (Pop<S>::kShifted) {
+                const float da = pc.ld(v, i);
+                ma = i == 0 ? da : ma + da;
+            }
         }
     }
 }
@@ -103,16 +176,17 @@ __device__ __forceinline__ float update_node(const float g[NQ], float rho, bool 
 }
 
 // CTAS CTAs per SM (registers are capped so that they fit); NOISE: sigma != 0.
-template <int TY, int STAGES, int CTAS, bool NOISE>
-__global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
+template <typename S, int TY, int STAGES, int CTAS, bool NOISE>
+__global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
     k_update_tma(SimDev d, const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1)
 {
-    using G = TmaGeom<TY>;
+    using G = TmaGeom<S, TY>;
     constexpr int NT = G::NT, PLANE = G::PLANE;
+    const Pop<S> pc(d);
     extern __shared__ __align__(128) float smem_f[];
     // stages on a 128-byte boundary (offset from the array itself, so that
     // every access stays a shared-memory access)
-    float *s_in = smem_f + ((128u - (smem_u32(smem_f) & 127u)) & 127u) / 4u;
+    S *s_in = reinterpret_cast<S *>(smem_f + ((128u - (smem_u32(smem_f) & 127u)) & 127u) / 4u);
     uint64_t *full = reinterpret_cast<uint64_t *>(s_in + STAGES * G::STRIDE);
     uint64_t *empty = full + STAGES;
     // divisions of this CTA's tiles: local tile index, two staged offsets, amount
@@ -149,8 +223,8 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
     const uint32_t t = (uint32_t)d.sc->step;
     const int cur = (int)(t & 1u);
     const CUtensorMap *tm = cur ? &tm1 : &tm0;
-    const float *__restrict__ fin = (const float *)d.f[cur];
-    float *__restrict__ fout = (float *)d.f[cur ^ 1];
+    const S *__restrict__ fin = (const S *)d.f[cur];
+    S *__restrict__ fout = (S *)d.f[cur ^ 1];
     const int y_r = d.sc->y_r, y_copy = d.sc->y_copy, y_hi = d.sc->y_hi;
 
     // rows the rear wall has just frozen: bring this copy up to date (whole
@@ -252,7 +326,7 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
         const int s = k % STAGES;
         const uint32_t parity = (uint32_t)((k / STAGES) & 1);
         const int x0 = tx * TMA_TX, y0 = y_r + ty * TY;
-        float *stage = s_in + s * G::STRIDE;
+        S *stage = s_in + s * G::STRIDE;
         if (!dead && !mbar_wait_bounded(&full[s], parity, TMA_WAIT_BUDGET)) {
             dead = true;
             atomicOr(&s_abort, 1);
@@ -261,17 +335,21 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
         const bool has_ev =
             nev > 0 && (ev_overflow || k >= 32 * TMA_KFLAG_WORDS || ((kflag[k >> 5] >> (k & 31)) & 1u));
         if (has_ev) { // uniform across the CTA
+            // (slot offset / PLANE is the plane, hence the weight class)
+            auto add_slot = [&](int off, float a) {
+                stage[off] = pc.st(pc.ld(stage[off], off / PLANE) + a, off / PLANE);
+            };
             if (!ev_overflow) {
                 for (int i = tid; i < nev; i += NT)
                     if (ev_k[i] == k) {
-                        stage[ev_off[2 * i]] += ev_add[i];
-                        stage[ev_off[2 * i + 1]] += ev_add[i];
+                        add_slot(ev_off[2 * i], ev_add[i]);
+                        add_slot(ev_off[2 * i + 1], ev_add[i]);
                     }
             } else {
                 for (int e = tid; e < nev_all; e += NT)
                     if (d.rec_owner[e] == (int)blockIdx.x && d.rec_k[e] == k) {
-                        stage[d.rec_off[2 * e]] += d.rec_add[e];
-                        stage[d.rec_off[2 * e + 1]] += d.rec_add[e];
+                        add_slot(d.rec_off[2 * e], d.rec_add[e]);
+                        add_slot(d.rec_off[2 * e + 1], d.rec_add[e]);
                     }
             }
             fence_proxy_async_smem(); // before a later bulk copy overwrites them
@@ -283,16 +361,16 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
         const bool active = y < y_hi;
         float ga[NQ], gb[NQ];
         if (active) {
-            const float *b = stage + (row + 1) * TMA_LX + cl + 4;
+            const S *b = stage + (row + 1) * TMA_LX + cl + 4;
             const bool rear = y - 1 < y_r, top = y + 1 >= H; // half-way bounce-back walls
             if (!rear && !top)
-                pull2<PLANE, false, false>(b, ga, gb);
+                pull2<S, PLANE, false, false>(b, ga, gb, pc);
             else if (!top)
-                pull2<PLANE, true, false>(b, ga, gb);
+                pull2<S, PLANE, true, false>(b, ga, gb, pc);
             else if (!rear)
-                pull2<PLANE, false, true>(b, ga, gb);
+                pull2<S, PLANE, false, true>(b, ga, gb, pc);
             else
-                pull2<PLANE, true, true>(b, ga, gb);
+                pull2<S, PLANE, true, true>(b, ga, gb, pc);
         }
         // the stage may be refilled (by the async proxy) once every warp has
         // arrived: order this thread's shared-memory reads before that
@@ -334,21 +412,22 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
                     clip += adda + addb;
                 }
                 if ((lane & 15) == 0) d.mask[(long long)y * d.MW + (x0 >> 5) + 2 * half + (lane >> 4)] = 0xffffffffu;
-                float *o = fout + (long long)y * Wp + x;
-#pragma unroll
-                for (int i = 0; i < NQ; ++i) *reinterpret_cast<float2 *>(o + i * P) = make_float2(fa[i], fb[i]);
+                S *o = fout + (long long)y * Wp + x;
+                float ma, mb;
+                store_nodes<S>(o, P, fa, fb, true, pc, ma, mb);
                 const int xw = x0 + 64 * half; // first column of the warp
                 if (xw == 0 || xw + 63 == W - 1) { // a warp at the lattice edge: ghost copies
                     if (x == 0) {
 #pragma unroll
-                        for (int i = 0; i < NQ; ++i) o[i * P + W] = fa[i];
+                        for (int i = 0; i < NQ; ++i) o[i * P + W] = pc.st(fa[i], i);
                     }
                     if (x + 1 == W - 1) {
 #pragma unroll
-                        for (int i = 0; i < NQ; ++i) o[i * P + 1 - W] = fb[i];
+                        for (int i = 0; i < NQ; ++i) o[i * P + 1 - W] = pc.st(fb[i], i);
                     }
                 }
-                const float roa = rhoa + adda, rob = rhob + addb;
+                const float roa = Pop<S>::kShifted ? ma : rhoa + adda;
+                const float rob = Pop<S>::kShifted ? mb : rhob + addb;
                 mass += fix24<float>(roa) + fix24<float>(rob);
                 if (roa != 0.0f || rob != 0.0f) maxrow = y;
             } else {
@@ -369,38 +448,35 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
                 v |= __shfl_xor_sync(0xffffffffu, v, 8);
                 const int word = (x0 >> 5) + 2 * half + (lane >> 4);
                 if ((lane & 15) == 0 && word < d.MW) d.mask[(long long)y * d.MW + word] = v;
-                float *o = fout + (long long)y * Wp + x;
-                if (okb) {
-    #pragma unroll
-                    for (int i = 0; i < NQ; ++i) *reinterpret_cast<float2 *>(o + i * P) = make_float2(fa[i], fb[i]);
-                } else if (oka) { // odd W: the last column alone (x = W is the ghost)
-    #pragma unroll
-                    for (int i = 0; i < NQ; ++i) o[i * P] = fa[i];
-                }
+                S *o = fout + (long long)y * Wp + x;
+                float ma = 0.0f, mb = 0.0f;
+                // (odd W: the last column alone, x = W is the ghost)
+                if (oka) store_nodes<S>(o, P, fa, fb, okb, pc, ma, mb);
                 // ghost copies of the edge columns for the next step's boxes
                 if (x == 0) {
     #pragma unroll
-                    for (int i = 0; i < NQ; ++i) o[i * P + W] = fa[i];
+                    for (int i = 0; i < NQ; ++i) o[i * P + W] = pc.st(fa[i], i);
                 }
                 if (x == W - 1) {
     #pragma unroll
-                    for (int i = 0; i < NQ; ++i) o[i * P - W] = fa[i];
+                    for (int i = 0; i < NQ; ++i) o[i * P - W] = pc.st(fa[i], i);
                 }
                 if (x + 1 == W - 1) {
     #pragma unroll
-                    for (int i = 0; i < NQ; ++i) o[i * P + 1 - W] = fb[i];
+                    for (int i = 0; i < NQ; ++i) o[i * P + 1 - W] = pc.st(fb[i], i);
                 }
                 // populations are non-negative after every step, so a node holds
-                // mass iff their sum (rho + what the fix added) is non-zero
+                // mass iff their sum (rho + what the fix added; with 16-bit
+                // storage the stored values' sum) is non-zero
                 if (oka) {
                     clip += adda;
-                    const float ro = rhoa + adda;
+                    const float ro = Pop<S>::kShifted ? ma : rhoa + adda;
                     mass += fix24<float>(ro);
                     if (ro != 0.0f) maxrow = y;
                 }
                 if (okb) {
                     clip += addb;
-                    const float ro = rhob + addb;
+                    const float ro = Pop<S>::kShifted ? mb : rhob + addb;
                     mass += fix24<float>(ro);
                     if (ro != 0.0f) maxrow = y;
                 }
@@ -430,7 +506,7 @@ __global__ void __launch_bounds__(TmaGeom<TY>::NT, CTAS)
 }
 
 // The kernel's shared-memory opt-in (once per device).
-template <int TY, int STAGES, int CTAS, bool NOISE>
+template <typename S, int TY, int STAGES, int CTAS, bool NOISE>
 cudaError_t prepare_update_tma_variant()
 {
     static bool attr[64] = {};
@@ -438,54 +514,60 @@ cudaError_t prepare_update_tma_variant()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64 || !attr[dev]) {
-        e = cudaFuncSetAttribute(k_update_tma<TY, STAGES, CTAS, NOISE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tma_smem_bytes<TY, STAGES>());
+        e = cudaFuncSetAttribute(k_update_tma<S, TY, STAGES, CTAS, NOISE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tma_smem_bytes<S, TY, STAGES>());
         if (e != cudaSuccess) return e;
         if (dev < 64) attr[dev] = true;
     }
     return cudaSuccess;
 }
 
-inline cudaError_t prepare_update_tma(const SimDev &d, int variant)
+template <typename S>
+cudaError_t prepare_update_tma(const SimDev &d, int variant)
 {
+    using C = TmaCfg<S>;
     if (variant == 1)
-        return d.noise_on ? prepare_update_tma_variant<4, 3, 2, true>() : prepare_update_tma_variant<4, 3, 2, false>();
-    return d.noise_on ? prepare_update_tma_variant<4, 2, 3, true>() : prepare_update_tma_variant<4, 2, 3, false>();
+        return d.noise_on ? prepare_update_tma_variant<S, C::TY, C::STAGES1, 2, true>()
+                          : prepare_update_tma_variant<S, C::TY, C::STAGES1, 2, false>();
+    return d.noise_on ? prepare_update_tma_variant<S, C::TY, C::STAGES0, 3, true>()
+                      : prepare_update_tma_variant<S, C::TY, C::STAGES0, 3, false>();
 }
 
-template <int TY, int STAGES, int CTAS, bool NOISE>
+template <typename S, int TY, int STAGES, int CTAS, bool NOISE>
 cudaError_t launch_update_tma_variant(const SimDev &d, const CUtensorMap *maps, bool pdl, cudaStream_t s)
 {
-    cudaError_t e = prepare_update_tma_variant<TY, STAGES, CTAS, NOISE>();
+    cudaError_t e = prepare_update_tma_variant<S, TY, STAGES, CTAS, NOISE>();
     if (e != cudaSuccess) return e;
     // maps[b] loads from population copy b. Launched as a programmatic
     // dependent of the planner: its CTAs may start (and run the prologue)
     // before the planner has finished, and wait for it in grid_dependency_wait.
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)d.upd_ctas); // at most CTAS per SM
-    cfg.blockDim = dim3(TmaGeom<TY>::NT);
-    cfg.dynamicSmemBytes = tma_smem_bytes<TY, STAGES>();
+    cfg.blockDim = dim3(TmaGeom<S, TY>::NT);
+    cfg.dynamicSmemBytes = tma_smem_bytes<S, TY, STAGES>();
     cfg.stream = s;
     cudaLaunchAttribute la[1];
     la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     la[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = la;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_update_tma<TY, STAGES, CTAS, NOISE>, d, maps[0], maps[1]);
+    return cudaLaunchKernelEx(&cfg, k_update_tma<S, TY, STAGES, CTAS, NOISE>, d, maps[0], maps[1]);
 }
 
-// variant 0: two staged tiles per CTA, three CTAs per SM; variant 1: three
-// staged tiles per CTA, two CTAs per SM. Both use tiles of 4 rows.
+// variant 0: three CTAs per SM; variant 1: two CTAs per SM with more staged
+// boxes each. Both use tiles of 4 rows.
 constexpr int tma_rows(int /*variant*/) { return 4; }
 constexpr int tma_ctas_per_sm(int variant) { return variant == 1 ? 2 : 3; }
 
-inline cudaError_t launch_update_tma(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s)
+template <typename S>
+cudaError_t launch_update_tma(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s)
 {
+    using C = TmaCfg<S>;
     if (variant == 1)
-        return d.noise_on ? launch_update_tma_variant<4, 3, 2, true>(d, maps, pdl, s)
-                          : launch_update_tma_variant<4, 3, 2, false>(d, maps, pdl, s);
-    return d.noise_on ? launch_update_tma_variant<4, 2, 3, true>(d, maps, pdl, s)
-                      : launch_update_tma_variant<4, 2, 3, false>(d, maps, pdl, s);
+        return d.noise_on ? launch_update_tma_variant<S, C::TY, C::STAGES1, 2, true>(d, maps, pdl, s)
+                          : launch_update_tma_variant<S, C::TY, C::STAGES1, 2, false>(d, maps, pdl, s);
+    return d.noise_on ? launch_update_tma_variant<S, C::TY, C::STAGES0, 3, true>(d, maps, pdl, s)
+                      : launch_update_tma_variant<S, C::TY, C::STAGES0, 3, false>(d, maps, pdl, s);
 }
 
 } // namespace lbm

@@ -25,7 +25,7 @@ GROWTH_MODES = {"none": 0, "bulk": 1, "density": 2, "edge": 3, "band": 4}
 FRONT_KINDS = {"flat": 0, "sinusoidal": 1, "full": 2}
 WALL_MODES = {"fixed": 0, "advance": 1}
 NEGFIX_MODES = {"literal": 0, "rescale": 1}
-PRECISIONS = {"fp32": 0, "fp64": 1}
+PRECISIONS = {"fp32": 0, "fp64": 1, "fp16": 2, "bf16": 3}
 
 LBM_OK = 0
 STATUS_FRONT_AT_TOP = 1

@@ -1,0 +1,238 @@
+"""16-bit population storage (FP16, BF16) against the FP64 CPU oracle.
+
+The 16-bit forms store the deviation f_i - c_i from the rest state (c_i =
+w_i rho_init rounded to the 16-bit type) and compute in FP32, so they are
+not bit-exact with the oracle. What is checked:
+
+* the codec: the void (f = 0) and the rest state are stored exactly, a
+  decoded state encodes back to the same bits, nothing decodes negative;
+* the TMA-staged and the plain-load update run the same arithmetic and
+  rounding: bit-exact with each other on every TMA case;
+* one step from an identical state (a 16-bit state, set into both): every
+  population within the rounding bound of one 16-bit store, half an ulp
+  of the stored deviation, 2^-(m+1) |f - c_i| with m = 10 (FP16) or 7
+  (BF16) mantissa bits, plus the FP32 arithmetic error of one step; at a
+  node that receives a division, also the rounding of its two pre-stream
+  slots, which hold the sum in 16 bits before the update reads them (App. A
+  step 3 on the stored state), carried through the collision; mask,
+  heights and division schedule identical. At 128 x 64 and at the full
+  4096 x 2048 size in the benchmark's launch configuration;
+* 1000 steps of the 128 x 64 bulk workload: no occupancy or height flips,
+  the same division schedule, and the field errors printed and held to the
+  envelope stated in test_1000_steps_bulk_envelope.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleSim
+from paper_2303_02210_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = ["fp16", "bf16"]
+MANTISSA = {"fp16": 10, "bf16": 7}
+WEIGHTS = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+EXACT_STATS = ["step", "ns_last", "ns_total", "div_total", "starved_steps", "cand_last", "events_last",
+               "mass_fix", "quiescent_fix", "S1", "S2", "y_r", "H_top", "hmin", "status", "carry",
+               "hbar", "w"]
+
+
+def sim(p, precision, kernel="auto"):
+    from paper_2303_02210_gb300.lbm import Simulation
+    return Simulation(p, precision=precision, update_kernel=kernel)
+
+
+def shifts(p, precision):
+    """c_i = w_i rho_init rounded to the storage type (numpy's float16 is IEEE
+    binary16; bfloat16 is the top 16 bits of binary32, rounded to nearest
+    even)."""
+    c = (WEIGHTS * p["rho_init"]).astype(np.float32)
+    if precision == "fp16":
+        return c.astype(np.float16).astype(np.float64)
+    b = c.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def one_step_bound(o, p, c, m):
+    """Largest |f_gpu - f_oracle| one step from an identical state allows:
+    half an ulp of the stored deviation (its FP32 value within the FP32
+    error of the exact one), the FP32 decode add, and the smallest
+    subnormal step of FP16. At a node that received a division, each of the
+    two slots was rounded once more after the add: by at most
+    2^-(m+1) (|f_slot - c| + add) <= 2^-(m+1) (max(rho, c_0) + add), rho the
+    node's density after the step (a population never exceeds its node's
+    density, and the collision keeps the density); the collision passes an
+    input error on to each output at most three times over (|1 - omega|
+    + omega (|w_i d f^SS_i / d f_j| summed) <= 3 for omega <= 2 and |u| << 1)."""
+    f_o = o.pops()
+    rho = f_o.sum(0)
+    dev = np.abs(f_o - c[:, None, None])
+    eps32 = 4e-6 * rho.max()
+    bound = 2.0 ** -(m + 1) * (dev + eps32) + eps32 + 2.0 ** -22 * np.abs(f_o) + 2.0 ** -24
+    node, _, cnt = o.last_events()
+    H, W = rho.shape
+    extra = np.zeros((H, W))
+    for n, k in zip(node.tolist(), cnt.tolist()):
+        y, x = divmod(n, W)
+        e = 6.0 * 2.0 ** -(m + 1) * (max(rho[y, x], c[0]) + k * p["rho_cell"] / 2)
+        extra[y, x] = max(extra[y, x], e)
+    return bound + extra[None], extra > 0
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_codec_void_rest_and_round_trip(precision):
+    p = wl.lattice_small(seed=1)
+    g = sim(p, precision)
+    f = g.pops()
+    # above the front: the void, stored exactly
+    assert (f[:, 40:, :] == 0.0).all()
+    # the initial tissue is the rest state w_i rho_init within one rounding
+    c = shifts(p, precision)
+    tissue = f[:, :8, :]
+    tol = 2.0 ** -(MANTISSA[precision] + 1) * np.abs(WEIGHTS * p["rho_init"] - c)[:, None, None] + 1e-7
+    assert (np.abs(tissue - (WEIGHTS * p["rho_init"])[:, None, None]) <= tol).all()
+    g.step(200)
+    f = g.pops()
+    assert (f >= 0.0).all()
+    st = g.stats()
+    g.set_pops(f)  # decoded values encode back to the same bits
+    assert np.array_equal(g.pops(), f)
+    assert g.stats()["mass_fix"] == st["mass_fix"]
+
+
+TMA16_CASES = {
+    "bulk_s1": wl.lattice_small(seed=1),
+    "edge": wl.lattice_small(seed=5, growth_mode="edge", edge_depth=4, growth_rate=3e-3,
+                             front_kind="sinusoidal", front_amp=3.0, front_kmax=8),
+    "band_wall": wl.lattice_small(seed=6, growth_mode="band", band_rows=10, growth_rate=3e-3,
+                                  height=96, front_row=40.0, wall_min_gap=12.0),
+    "density": wl.lattice_small(seed=4, growth_mode="density", growth_rate=3e-3),
+    "rescale_strong_noise": wl.lattice_small(seed=8, sigma=0.08, negfix_mode="rescale"),
+    "ragged_37x29": wl.lattice_small(seed=10, width=37, height=29, front_row=9.0, growth_rate=3e-3),
+    "width_1": wl.lattice_small(seed=11, width=1, height=24, front_row=8.0, growth_rate=3e-3),
+    "paper_params": wl.paper_params(width=96, height=64, front_row=16.0, seed=14),
+    "fills_to_top": wl.lattice_small(seed=17, height=24, growth_rate=5e-3, wall_mode="fixed"),
+    "edge_full_width": wl.lattice_small(seed=21, width=384, height=96, front_row=40.0,
+                                        growth_mode="edge", growth_rate=3e-3,
+                                        front_kind="sinusoidal", front_amp=2.0),
+    "ragged_300": wl.lattice_small(seed=22, width=300, height=70, front_row=30.0,
+                                   growth_rate=3e-3, sigma=0.05),
+}
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("name", sorted(TMA16_CASES))
+def test_tma_bit_exact_with_plain(name, precision):
+    p = TMA16_CASES[name]
+    a = sim(p, precision, "plain")
+    b = sim(p, precision, "tma1" if name == "edge_full_width" else "tma")
+    assert a.stats()["update_kernel"] == 1 and b.stats()["update_kernel"] == 2
+    for chunk in (1, 9, 90, 200):
+        a.step(chunk)
+        b.step(chunk)
+        sa, sb = a.stats(), b.stats()
+        for k in EXACT_STATS + ["node_updates", "y_hi"]:
+            assert sa[k] == sb[k], (k, sa[k], sb[k])
+        assert np.array_equal(a.pops(), b.pops())
+        assert np.array_equal(a.mask(), b.mask())
+        assert np.array_equal(a.heights(), b.heights())
+
+
+def _one_step(p, precision, warm):
+    """A 16-bit state after `warm` steps, set into a fresh simulation and a
+    fresh oracle (both at step 0), advanced one step."""
+    g0 = sim(p, precision)
+    if warm:
+        g0.step(warm)
+    f0 = g0.pops()
+    del g0
+    g = sim(p, precision)
+    g.set_pops(f0)
+    o = OracleSim(p)
+    o.set_pops(f0)
+    g.step(1)
+    o.step(1)
+    return g, o
+
+
+ONE_STEP_CASES = ["bulk_s1", "edge", "paper_params", "rescale_strong_noise", "ragged_300"]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("name", ONE_STEP_CASES)
+def test_one_step_within_rounding_bound(name, precision):
+    p = TMA16_CASES[name]
+    g, o = _one_step(p, precision, 300)
+    fg, fo = g.pops(), o.pops()
+    c = shifts(p, precision)
+    bound, div = one_step_bound(o, p, c, MANTISSA[precision])
+    err = np.abs(fg - fo)
+    r = err / bound
+    print(f"{name} {precision}: max |df| {err.max():.3e}, worst fraction of the bound "
+          f"{float(r[:, ~div].max()):.3f} ({float(r[:, div].max()) if div.any() else 0.0:.3f} at "
+          f"{int(div.sum())} division nodes)")
+    assert (err <= bound).all(), np.argwhere(err > bound)[:5].tolist()
+    assert np.array_equal(g.mask(), o.mask())
+    assert np.array_equal(g.heights(), o.heights())
+    sg, so = g.stats(), o.stats()
+    for k in ("ns_last", "ns_total", "div_total", "cand_last", "events_last", "y_r", "H_top"):
+        assert sg[k] == so[k], (k, sg[k], so[k])
+    for a, b in zip(g.last_events(), o.last_events()):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_one_step_full_size_edge_workload(precision):
+    """4096 x 2048, edge growth, the benchmark's launch configuration (the
+    TMA-staged kernel): one step from the 16-bit initial state."""
+    p = wl.lattice_edge(seed=1)
+    g, o = _one_step(p, precision, 0)
+    assert g.stats()["update_kernel"] == 2
+    fg, fo = g.pops(), o.pops()
+    c = shifts(p, precision)
+    bound, div = one_step_bound(o, p, c, MANTISSA[precision])
+    err = np.abs(fg - fo)
+    r = err / bound
+    print(f"full size {precision}: max |df| {err.max():.3e}, worst fraction {float(r[:, ~div].max()):.3f}"
+          f" ({float(r[:, div].max()) if div.any() else 0.0:.3f} at {int(div.sum())} division nodes)")
+    assert (err <= bound).all()
+    assert np.array_equal(g.mask(), o.mask())
+    assert np.array_equal(g.heights(), o.heights())
+    assert g.stats()["ns_total"] == o.stats()["ns_total"]
+    assert g.stats()["events_last"] == o.stats()["events_last"]
+
+
+# Envelope of the 1000-step field errors (density: max-abs relative to the
+# largest density; velocity: 2-norm over occupied nodes relative to the
+# oracle's 2-norm). Measured maxima over the two seeds, checked every 100
+# steps: FP16 4.5e-4 and 3.1e-3, BF16 2.4e-3 and 7.8e-3. The bounds are
+# four times those: the per-step rounding (2^-11 or 2^-8 of deviations up
+# to c_0 = 0.44 at the front, and of every slot a division lands in)
+# accumulates as a random walk, so the error of a single run fluctuates by
+# that much.
+ENVELOPE = {"fp16": (2e-3, 1.2e-2), "bf16": (1e-2, 3.2e-2)}
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_1000_steps_bulk_envelope(precision):
+    for seed in (1, 2):
+        p = wl.lattice_small(seed=seed)
+        o = OracleSim(p)
+        g = sim(p, precision)
+        worst_rho = worst_u = 0.0
+        for _ in range(10):
+            o.step(100)
+            g.step(100)
+            assert g.stats()["ns_total"] == o.stats()["ns_total"]
+            assert np.array_equal(g.mask(), o.mask())
+            assert np.array_equal(g.heights(), o.heights())
+            rg, uxg, uyg = g.fields()
+            ro, uxo, uyo = o.fields()
+            e_rho = np.abs(rg - ro).max() / np.abs(ro).max()
+            du = np.hypot(uxg - uxo, uyg - uyo)
+            occ = o.mask()
+            e_u = np.linalg.norm(du[occ]) / np.linalg.norm(np.hypot(uxo, uyo)[occ])
+            worst_rho, worst_u = max(worst_rho, e_rho), max(worst_u, e_u)
+        print(f"{precision} seed {seed}: rho {worst_rho:.2e} u {worst_u:.2e}")
+        assert worst_rho <= ENVELOPE[precision][0] and worst_u <= ENVELOPE[precision][1]
