@@ -267,18 +267,20 @@ def measure_serving(n: int = 100, rate: float = 200.0, steps=(500, 5000), budget
     """The served form: a fixed trace of n requests (Poisson arrivals at
     `rate` per second, widths log-uniform 128..4096, height = width / 2, bulk,
     edge or density growth, g log-uniform 1e-5..1e-3, steps uniform in
-    `steps`, FP32) through the continuous-batching loop with an HBM budget;
+    `steps`, FP32 or FP16 storage 50/50) through the continuous-batching
+    loop with an HBM budget;
     time to result per request (arrival to result on the host) and the
     aggregate node-update rate over the whole run (wall clock)."""
     from paper_2303_02210_gb300 import serving
     trace = wl.serving_trace(n, rate=rate, steps=steps)
-    reqs = [serving.Request(params=p, steps=k, arrival=t) for t, p, k in trace]
+    reqs = [serving.Request(params=p, steps=k, arrival=t, precision=pr) for t, p, k, pr in trace]
     srv = serving.Server(hbm_budget=int(budget_gb * 2 ** 30), chunk=100)
     srv.run(reqs)
     out = serving.summary(reqs, srv)
     out["workload"] = (f"{n} requests, Poisson arrivals at {rate:g}/s, widths log-uniform 128-4096, "
                        f"height = width/2, bulk/edge/density growth, g log-uniform 1e-5..1e-3, "
-                       f"{steps[0]}-{steps[1]} steps, FP32, {budget_gb:g} GB budget, 100-step ticks")
+                       f"{steps[0]}-{steps[1]} steps, FP32 or FP16 storage 50/50, {budget_gb:g} GB budget, "
+                       f"100-step ticks")
     return out
 
 

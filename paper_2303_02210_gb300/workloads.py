@@ -104,12 +104,15 @@ def ensemble(n: int = 256, seed: int = 1, **kw) -> list:
     return out
 
 
-def serving_trace(n: int = 200, rate: float = 200.0, steps=(1000, 20000), seed: int = 1, **kw) -> list:
+def serving_trace(n: int = 200, rate: float = 200.0, steps=(1000, 20000), seed: int = 1,
+                  fp16_share: float = 0.5, **kw) -> list:
     """A stream of requests: Poisson arrivals at `rate` per second, widths
     log-uniform in [128, 4096] (multiples of 32) with height = width / 2,
     bulk, edge or density-dependent growth at random, g log-uniform in
-    [1e-5, 1e-3], step counts uniform in `steps`. Returns (arrival seconds,
-    parameters, steps) triples; request i has seed seed + i and its own id."""
+    [1e-5, 1e-3], step counts uniform in `steps`, a share `fp16_share` of
+    them with FP16 population storage and the rest FP32. Returns (arrival
+    seconds, parameters, steps, precision) tuples; request i has seed
+    seed + i and its own id."""
     import numpy as np
     rng = np.random.default_rng(seed)
     t = 0.0
@@ -120,11 +123,12 @@ def serving_trace(n: int = 200, rate: float = 200.0, steps=(1000, 20000), seed: 
         mode = str(rng.choice(["bulk", "edge", "density"]))
         g = float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-3))))
         nsteps = int(rng.integers(steps[0], steps[1] + 1))
+        precision = "fp16" if float(rng.uniform()) < fp16_share else "fp32"
         p = base_params(width=W, height=W // 2, tau=0.8, growth_rate=g, growth_mode=mode, edge_depth=8,
                         front_kind="flat", front_row=float(W // 8), front_amp=0.5,
                         wall_mode="fixed" if mode == "edge" else "advance", seed=seed + i, sim_id=i)
         p.update(kw)
-        out.append((t, p, nsteps))
+        out.append((t, p, nsteps, precision))
     return out
 
 

@@ -74,13 +74,15 @@ def test_served_results_equal_requests_run_alone():
     from paper_2303_02210_gb300.lbm import Simulation, lbm_footprint
     trace = wl.serving_trace(10, rate=500.0, steps=(100, 400), seed=7)
     trace = [(t, dict(p, width=min(p["width"], 512), height=min(p["width"], 512) // 2,
-                      front_row=float(min(p["width"], 512) // 8)), n) for t, p, n in trace]
-    reqs = [serving.Request(params=p, steps=n, arrival=t, keep_populations=True) for t, p, n in trace]
+                      front_row=float(min(p["width"], 512) // 8)), n, pr) for t, p, n, pr in trace]
+    assert {pr for *_, pr in trace} == {"fp16", "fp32"}
+    reqs = [serving.Request(params=p, steps=n, arrival=t, precision=pr, keep_populations=True)
+            for t, p, n, pr in trace]
     budget = 3 * max(lbm_footprint(r.params, "fp32") for r in reqs)
     srv = serving.Server(hbm_budget=budget, chunk=64)
     srv.run(reqs)
     for r in reqs:
-        alone = Simulation(r.params, precision="fp32")
+        alone = Simulation(r.params, precision=r.precision)
         alone.step(r.steps)
         assert np.array_equal(alone.pops(), r.result["populations"])
         assert alone.stats()["node_updates"] == r.result["stats"]["node_updates"]
