@@ -89,8 +89,8 @@ struct Layout {
     int Wp, MW, hcap, ns_max;
     long long P;
     int elem;
-    uint64_t off_f0, off_f1, off_mask, off_heights, off_rows0, off_sc, off_hkeys, off_hcnt, off_hlist, off_evk,
-        off_evc, off_rown, off_rk, off_roff, off_radd, off_bcnt, off_bucket, off_pl64, off_pl32, total;
+    uint64_t off_f0, off_f1, off_mask, off_heights, off_rows0, off_sc, off_htab, off_hlist, off_evk,
+        off_evc, off_rown, off_rk, off_roff, off_bcnt, off_bucket, off_pl64, off_pl32, total;
 };
 
 Layout make_layout(const lbm_params_t &p)
@@ -122,8 +122,7 @@ Layout make_layout(const lbm_params_t &p)
     L.off_heights = o; o = align256(o + (uint64_t)p.width * 4u);
     L.off_rows0 = o; o = align256(o + (uint64_t)p.width * 4u);
     L.off_sc = o; o = align256(o + sizeof(DevScalars));
-    L.off_hkeys = o; o = align256(o + (uint64_t)L.hcap * 4u);
-    L.off_hcnt = o; o = align256(o + (uint64_t)L.hcap * 4u);
+    L.off_htab = o; o = align256(o + (uint64_t)L.hcap * 8u);
     L.off_hlist = o; o = align256(o + (uint64_t)L.ns_max * 4u);
     // event lists of two consecutive steps (the planner selects one step ahead)
     L.off_evk = o; o = align256(o + (uint64_t)L.ns_max * 8u);
@@ -131,7 +130,6 @@ Layout make_layout(const lbm_params_t &p)
     L.off_rown = o; o = align256(o + (uint64_t)L.ns_max * 4u);
     L.off_rk = o; o = align256(o + (uint64_t)L.ns_max * 4u);
     L.off_roff = o; o = align256(o + (uint64_t)L.ns_max * 8u);
-    L.off_radd = o; o = align256(o + (uint64_t)L.ns_max * 4u);
     L.off_bcnt = o; o = align256(o + (uint64_t)kTmaMaxCtas * 4u);
     L.off_bucket = o; o = align256(o + (uint64_t)kTmaMaxCtas * kBucketCap * 4u);
     // planner partials: S1, S2, frozen mass (int64); top, low, two count buffers (int32)
@@ -346,15 +344,13 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     d.heights = (int32_t *)(base + L.off_heights);
     d.rows0 = (int32_t *)(base + L.off_rows0);
     d.sc = (DevScalars *)(base + L.off_sc);
-    d.hkeys = (uint32_t *)(base + L.off_hkeys);
-    d.hcnt = (uint32_t *)(base + L.off_hcnt);
+    d.htab = (unsigned long long *)(base + L.off_htab);
     d.hlist = (int32_t *)(base + L.off_hlist);
     d.ev_key = (uint32_t *)(base + L.off_evk);
     d.ev_count = (int32_t *)(base + L.off_evc);
     d.rec_owner = (int *)(base + L.off_rown);
     d.rec_k = (int *)(base + L.off_rk);
     d.rec_off = (int *)(base + L.off_roff);
-    d.rec_add = (float *)(base + L.off_radd);
     d.bucket_cnt = (int *)(base + L.off_bcnt);
     d.bucket = (int *)(base + L.off_bucket);
     d.pl_s1 = (long long *)(base + L.off_pl64);
@@ -459,8 +455,8 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     do {
         cudaError_t e = cudaMemsetAsync(s->arena, 0, L.total, s->stream);
         if (e != cudaSuccess) { rc = cuda_fail(e); break; }
-        // the large-n_s event table starts empty (all keys 0xFFFFFFFF)
-        e = cudaMemsetAsync(d.hkeys, 0xFF, (size_t)L.hcap * 4u, s->stream);
+        // the division table starts empty (every entry all ones)
+        e = cudaMemsetAsync(d.htab, 0xFF, (size_t)L.hcap * 8u, s->stream);
         if (e != cudaSuccess) { rc = cuda_fail(e); break; }
         std::vector<int32_t> rows;
         front_rows(*p, rows);

@@ -131,7 +131,6 @@ struct DevScalars {
     int pend_starved;     // the selection came up short
     int rec_n;            // division records of the next update
     int pad1;
-    long long sel_kstop;  // candidate index + 1 of the n_s-th accept
     unsigned long long bar_ctr; // grid-barrier arrivals of k_plan (grows by the grid size per barrier)
     // k_plan scratch: n_s from the mass before any freezing, computed by one
     // block while the others scan the front
@@ -148,8 +147,8 @@ struct SimDev {
     int32_t *heights;    // h(x), W entries
     DevScalars *sc;
     // proliferation planner
-    uint32_t *hkeys;     // open-addressing table of the selected (node, pair), EMPTY when unused
-    uint32_t *hcnt;
+    unsigned long long *htab; // open-addressing table of the selected (node, pair): packed key
+                              // in the high word, draw count in the low word; all ones when unused
     int32_t *hlist;      // per selected division (draw rank): its table slot if it was the
                          // first draw of its (node, pair), else -1
     uint32_t *ev_key;    // divisions of step t at [(t & 1) ns_max, ...) by draw rank: packed (node, pair)
@@ -171,8 +170,8 @@ struct SimDev {
     int upd_tyl2;         // log2 of the rows per tile of the TMA-staged update
     int *rec_owner;       // per division (selector order): owning CTA of its tile,
     int *rec_k;           // the tile's index among that CTA's tiles,
-    int *rec_off;         // the two pre-stream slots' offsets in the staged box,
-    float *rec_add;       // and count * rho_cell / 2
+    int *rec_off;         // and the two pre-stream slots' offsets in the staged box
+                          // (the amount is ev_count * rho_cell / 2)
     int *bucket_cnt;      // divisions per CTA of the TMA-staged update (kTmaMaxCtas)
     int *bucket;          // their record indices, kBucketCap per CTA
     // per-block partials of the fused planner (kPlanMaxBlocks each)

@@ -718,26 +718,33 @@ __device__ __forceinline__ Candidate draw_candidate(const SimDev &d, long long k
 }
 
 constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;
+constexpr unsigned long long EMPTY_ENTRY = ~0ull; // key EMPTY_KEY: never a real key
 
 struct EventTable {
-    uint32_t *keys;
-    uint32_t *cnt;
-    int32_t *list;
-    unsigned mask; // slots - 1
+    unsigned long long *e; // (key << 32) | draw rank of the key's first draw
+    unsigned mask;         // slots - 1
 };
 
-// Counts one draw of `key`; returns the slot if the key is new, else -1.
-__device__ __forceinline__ int table_insert(const EventTable &tb, uint32_t key)
+// Draw rank `rank` of `key`: returns the slot if the key is new (its entry
+// then holds the key and this rank), else -1; *first is the rank of the
+// key's first draw. One compare-and-swap either way.
+__device__ __forceinline__ int table_insert(const EventTable &tb, uint32_t key, int rank, int *first)
 {
+    const unsigned long long mine = ((unsigned long long)key << 32) | (uint32_t)rank;
     unsigned slot = (unsigned)(((unsigned long long)key * 0x9E3779B97F4A7C15ull) >> 32) & tb.mask;
     for (unsigned probe = 0; probe <= tb.mask; ++probe) {
-        const uint32_t old = atomicCAS(&tb.keys[slot], EMPTY_KEY, key);
-        if (old == EMPTY_KEY || old == key) {
-            atomicAdd(&tb.cnt[slot], 1u);
-            return old == EMPTY_KEY ? (int)slot : -1;
+        const unsigned long long old = atomicCAS(&tb.e[slot], EMPTY_ENTRY, mine);
+        if (old == EMPTY_ENTRY) {
+            *first = rank;
+            return (int)slot;
+        }
+        if ((uint32_t)(old >> 32) == key) {
+            *first = (int)(uint32_t)old;
+            return -1;
         }
         slot = (slot + 1u) & tb.mask;
     }
+    *first = -1; // full (never: the table has at least 2 n_s,max slots)
     return -1;
 }
 
@@ -748,8 +755,9 @@ __device__ __forceinline__ int table_insert(const EventTable &tb, uint32_t key)
 // ((kTmaBoxX + 8) x (2^upd_tyl2 + 2) x 9 with the tile at column 4, row 1):
 // the source (x - ex_q, y - ey_q) unwrapped in x (the box holds the ghost
 // columns -1 and W), or across a wall the node's own population opp(q).
+// Returns the owner CTA.
 template <typename R>
-__device__ __forceinline__ void division_record(const SimDev &d, int e, uint32_t key, int cnt, int y_r)
+__device__ __forceinline__ int division_record(const SimDev &d, int e, uint32_t key, int y_r)
 {
     constexpr int LX = kTmaBoxX + 8;
     const int TY = 1 << d.upd_tyl2, PL = (TY + 2) * LX;
@@ -759,7 +767,8 @@ __device__ __forceinline__ void division_record(const SimDev &d, int e, uint32_t
     const uint32_t tile = (uint32_t)(ty * ncx + tx);
     const uint32_t q = __umulhi(tile, d.upd_magic);
     const int x0 = tx * kTmaBoxX, y0 = y_r + ty * TY;
-    d.rec_owner[e] = (int)(tile - q * (uint32_t)d.upd_ctas);
+    const int owner = (int)(tile - q * (uint32_t)d.upd_ctas);
+    d.rec_owner[e] = owner;
     d.rec_k[e] = (int)q;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -768,7 +777,7 @@ __device__ __forceinline__ void division_record(const SimDev &d, int e, uint32_t
         d.rec_off[2 * e + h] = (ys < y_r || ys >= d.H) ? opp(qd) * PL + (y - y0 + 1) * LX + (x - x0 + 4)
                                                        : qd * PL + (ys - y0 + 1) * LX + (x - ex(qd) - x0 + 4);
     }
-    d.rec_add[e] = (float)((double)cnt * d.half_cell);
+    return owner;
 }
 
 // rho and u of copy `cur` into device arrays of W*H doubles (Eq. 1).

@@ -110,19 +110,32 @@ __device__ __forceinline__ int plan_block_exscan(int v, int *total, int *s_i)
     return before + incl - v;
 }
 
-// The division of draw rank `rank`: counted in the table keyed by (node,
-// pair); the rank's list entry is the table slot if this draw was the first of
-// its (node, pair), else -1.
-__device__ __forceinline__ void plan_select(const SimDev &d, uint32_t key, int rank, size_t buf)
+// The division of draw rank `rank`: merged in the table keyed by (node,
+// pair) and counted at the rank of the pair's first draw (ev_count of a
+// repeat stays 0; the counts were zeroed for this selection). The rank's list
+// entry is the table slot if this draw was the first of its (node, pair),
+// else -1. For the TMA-staged update, a first draw also gets its record and
+// a place in its owner CTA's bucket (y_r: the rear wall of the coming step).
+template <typename R>
+__device__ __forceinline__ void plan_select(const SimDev &d, uint32_t key, int rank, size_t buf, int y_r)
 {
     EventTable tb;
-    tb.keys = d.hkeys;
-    tb.cnt = d.hcnt;
-    tb.list = d.hlist;
+    tb.e = d.htab;
     tb.mask = (unsigned)d.hcap - 1u;
-    const int slot = table_insert(tb, key);
+    int first;
+    const int slot = table_insert(tb, key, rank, &first);
     d.hlist[rank] = slot;
     d.ev_key[buf + rank] = key;
+    if (first >= 0) atomicAdd(&d.ev_count[buf + first], 1);
+    if (d.inject_in_update) {
+        if (slot >= 0) {
+            const int owner = division_record<R>(d, rank, key, y_r);
+            const int at = atomicAdd(&d.bucket_cnt[owner], 1);
+            if (at < kBucketCap) d.bucket[owner * kBucketCap + at] = rank;
+        } else {
+            d.rec_owner[rank] = -1;
+        }
+    }
 }
 
 // Acceptance of a candidate (as `accept`, with the heights of this launch
@@ -191,6 +204,24 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
     const double carry_in = init ? sc->carry : sc->pend_carry;
     const double ratio_in = sc->acc_ratio;
     const bool grow = d.growth_mode != GROW_NONE;
+    // what block 0 commits at the end about the step that ran: its pending
+    // statistics and the running totals, read before any block may write them
+    __shared__ long long s_cm[11];
+    __shared__ double s_cm_carry;
+    if (blk == 0 && tid == 0) {
+        s_cm[0] = sc->pend_req;
+        s_cm[1] = sc->pend_acc;
+        s_cm[2] = sc->pend_nev;
+        s_cm[3] = sc->pend_cand;
+        s_cm[4] = sc->ns_total;
+        s_cm[5] = sc->div_total;
+        s_cm[6] = sc->starved_steps;
+        s_cm[7] = sc->node_updates;
+        s_cm[8] = sc->step;
+        s_cm[9] = sc->quiescent_fix;
+        s_cm[10] = sc->pend_starved;
+        s_cm_carry = sc->pend_carry;
+    }
     if (tid == 0) {
         s_dead = 0;
         s_kstop = 0ull;
@@ -218,19 +249,24 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
         unsigned pending = __ballot_sync(0xffffffffu, x < d.W);
         int h = 0;
         for (int yb = ytop; yb >= 0 && pending; yb -= 32) {
+            // lane l loads row yb - l of the word; a 32 x 32 bit transpose
+            // (five butterfly exchanges) gives lane c its column: bit l set
+            // iff node (32 m + c, yb - l) is occupied
             const int y = yb - lane;
-            const unsigned word = y >= 0 ? d.mask[(long long)y * d.MW + m] : 0u;
-            unsigned any = word;
+            unsigned col = y >= 0 ? d.mask[(long long)y * d.MW + m] : 0u;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) any |= __shfl_xor_sync(0xffffffffu, any, o);
-            unsigned todo = pending & any;
-            while (todo) {
-                const int c = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const unsigned bb = __ballot_sync(0xffffffffu, (word >> c) & 1u);
-                if (lane == c) h = yb - (__ffs(bb) - 1) + 1;
-                pending &= ~(1u << c);
+            for (int j = 16; j > 0; j >>= 1) {
+                const unsigned keep = j == 16 ? 0x0000FFFFu
+                                    : j == 8  ? 0x00FF00FFu
+                                    : j == 4  ? 0x0F0F0F0Fu
+                                    : j == 2  ? 0x33333333u
+                                              : 0x55555555u; // bits c with (c & j) == 0
+                const unsigned other = __shfl_xor_sync(0xffffffffu, col, j);
+                col = (lane & j) ? ((col & ~keep) | ((other & ~keep) >> j)) : ((col & keep) | ((other & keep) << j));
             }
+            // the highest occupied row of a column not found above
+            if (((pending >> lane) & 1u) && col != 0u) h = yb - (__ffs(col) - 1) + 1;
+            pending &= ~__ballot_sync(0xffffffffu, col != 0u);
         }
         if (x < d.W) {
             d.heights[x] = h;
@@ -390,6 +426,9 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
         if (ns <= 0) kc = 0;
     }
     const size_t buf = (size_t)(tn & 1u) * (size_t)d.ns_max; // event list of step tn
+    // counts of this selection start at zero (the selection below adds to
+    // them after the next grid barrier)
+    for (long long r = (long long)blk * PLAN_NT + tid; r < ns; r += (long long)G * PLAN_NT) d.ev_count[buf + r] = 0;
 
     // ---- C/D: candidates in draw order, the first n_s accepted, merged
     long long acc = 0; // accepted candidates so far (all blocks agree)
@@ -437,7 +476,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
             if (lr >= 0) {
                 const long long rank = before + lr;
                 if (rank == ns - 1) s_kstop = (unsigned long long)(blk * C + j + 1);
-                if (rank < ns) plan_select(d, s_key[j], (int)rank, buf);
+                if (rank < ns) plan_select<R>(d, s_key[j], (int)rank, buf, nyr);
             }
         }
         acc = total;
@@ -468,61 +507,56 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
             tt = plan_block_sum(tt, s_ll);
             const long long rank = acc + bf + pr;
             if (a && rank == ns - 1) s_kstop = (unsigned long long)(k + 1);
-            if (a && rank < ns) plan_select(d, key, (int)rank, buf);
+            if (a && rank < ns) plan_select<R>(d, key, (int)rank, buf, nyr);
             acc += tt;
             base += (long long)G * PLAN_NT;
             ++round;
         }
         __syncthreads();
-        if (tid == 0 && s_kstop) sc->sel_kstop = (long long)s_kstop;
+        // the block that accepted the n_s-th candidate records how many were
+        // drawn up to it, and the candidates per division for the next step
+        if (tid == 0 && s_kstop) {
+            sc->pend_cand = (long long)s_kstop;
+            sc->acc_ratio = (double)s_kstop / (double)ns;
+        }
     }
     plan_grid_sync(sc, &s_dead);
 
-    // ---- E: counts of the merged divisions, per-CTA records, table emptied
+    // ---- E: the table emptied for the next selection
     const int nsel = (int)(acc < ns ? acc : ns); // selected divisions (draw ranks)
     for (int r = blk * PLAN_NT + tid; r < nsel; r += G * PLAN_NT) {
         const int slot = __ldcg(&d.hlist[r]);
-        if (slot < 0) { // a repeat of an earlier rank's (node, pair)
-            d.ev_count[buf + r] = 0;
-            if (d.inject_in_update) d.rec_owner[r] = -1;
-            continue;
-        }
-        const uint32_t key = d.ev_key[buf + r];
-        const int cnt = (int)__ldcg(&d.hcnt[slot]);
-        d.ev_count[buf + r] = cnt;
-        if (d.inject_in_update) {
-            division_record<R>(d, r, key, cnt, nyr);
-            const int owner = d.rec_owner[r];
-            const int at = atomicAdd(&d.bucket_cnt[owner], 1);
-            if (at < kBucketCap) d.bucket[owner * kBucketCap + at] = r;
-        }
-        d.hkeys[slot] = EMPTY_KEY;
-        d.hcnt[slot] = 0u;
+        if (slot >= 0) d.htab[slot] = EMPTY_ENTRY;
     }
 
     // ---- block 0: commit the step that ran, the observables, the new selection
     if (blk == 0 && tid == 0) {
+        const long long p_req = s_cm[0], p_acc = s_cm[1], p_nev = s_cm[2], p_cand = s_cm[3];
+        const long long ns_tot = s_cm[4], div_tot = s_cm[5], starved = s_cm[6], nupd = s_cm[7];
+        const long long step = s_cm[8], qfix = s_cm[9];
+        const int p_starved = (int)s_cm[10];
+        const double p_carry = s_cm_carry;
         if (!init) {
-            sc->ns_last = sc->pend_req;
-            sc->ns_total += sc->pend_req;
-            sc->carry = sc->pend_carry;
-            sc->div_total += sc->pend_acc;
-            sc->events_last = sc->pend_acc;
-            sc->n_events = sc->pend_nev;
-            sc->cand_last = sc->pend_cand;
-            if (sc->pend_starved) {
-                sc->starved_steps += 1;
-                sc->status |= ST_STARVED;
+            sc->ns_last = p_req;
+            sc->ns_total = ns_tot + p_req;
+            sc->carry = p_carry;
+            sc->div_total = div_tot + p_acc;
+            sc->events_last = p_acc;
+            sc->n_events = p_nev;
+            sc->cand_last = p_cand;
+            if (p_starved) {
+                sc->starved_steps = starved + 1;
+                atomicOr(&sc->status, ST_STARVED);
             }
-            sc->node_updates += (long long)d.W * (long long)(y_hi_old > y_r ? y_hi_old - y_r : 0);
-            sc->step += 1;
+            sc->node_updates = nupd + (long long)d.W * (long long)(y_hi_old > y_r ? y_hi_old - y_r : 0);
+            sc->step = step + 1;
         }
         sc->S1 = S1a;
         sc->S2 = S2a;
         sc->H_top = topa;
         sc->hmin = lowa;
         sc->mass_fix = mass_fix;
-        sc->quiescent_fix += frozen;
+        sc->quiescent_fix = qfix + frozen;
         int yhi;
         if (d.y_periodic) {
             yhi = d.H;
@@ -533,20 +567,19 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
         sc->y_copy = y_r;
         sc->y_r = nyr;
         sc->y_hi = yhi;
-        if (maxmass >= d.H - 1) sc->status |= ST_FRONT_AT_TOP;
-        if (capacity) sc->status |= ST_CAPACITY;
+        if (maxmass >= d.H - 1) atomicOr(&sc->status, ST_FRONT_AT_TOP);
+        if (capacity) atomicOr(&sc->status, ST_CAPACITY);
         sc->mass_accum = 0ull;
         sc->maxmass_accum = -1;
         // the selection for step tn, applied by the next update
         const long long cap = 64 * ns + 1024;
-        const long long kstop = sc->sel_kstop;
         sc->pend_req = ns_req;
         sc->pend_carry = carry_out;
         sc->pend_acc = nsel;
         sc->pend_nev = nsel;
         sc->pend_starved = (nwin_zero || (ns > 0 && acc < ns)) ? 1 : 0;
-        sc->pend_cand = nwin_zero ? 0 : (ns > 0 && acc < ns ? cap : (ns > 0 ? kstop : 0));
-        if (ns > 0 && acc >= ns) sc->acc_ratio = (double)kstop / (double)ns;
+        // (with n_s reached, the accepting block wrote pend_cand and acc_ratio)
+        if (!(ns > 0 && acc >= ns)) sc->pend_cand = nwin_zero ? 0 : (ns > 0 ? cap : 0);
         sc->plan_req = ns_req;
         sc->plan_ns = ns;
         sc->plan_kc = kc;

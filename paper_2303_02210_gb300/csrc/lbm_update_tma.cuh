@@ -266,10 +266,16 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
 
     // App. A step 3 for this CTA: the planner wrote one record per division
     // (the tile's local index among its owner's tiles, the offsets of the two
-    // pre-stream slots in the staged box, the amount) and listed the records
-    // of each owner CTA in its bucket; read ours (all records if the bucket
-    // overflowed).
+    // pre-stream slots in the staged box; the amount follows from the event
+    // count) and listed the records of each owner CTA in its bucket; read
+    // ours (all records if the bucket overflowed).
     const int nev_all = d.inject_in_update ? d.sc->rec_n : 0;
+    // the amount of division e: count * rho_cell / 2 (the event list of step
+    // t; the address is formed at each use, so that nothing more stays live
+    // through the tile loop)
+    auto amount = [&](int e) {
+        return (float)((double)d.ev_count[(size_t)(t & 1u) * (size_t)d.ns_max + (size_t)e] * d.half_cell);
+    };
     const int mine = nev_all > 0 ? d.bucket_cnt[blockIdx.x] : 0;
     if (mine <= kBucketCap) {
         for (int j = tid; j < mine; j += NT) {
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
             ev_k[j] = k;
             ev_off[2 * j] = d.rec_off[2 * e];
             ev_off[2 * j + 1] = d.rec_off[2 * e + 1];
-            ev_add[j] = d.rec_add[e];
+            ev_add[j] = amount(e);
             if (k < 32 * TMA_KFLAG_WORDS) atomicOr(&kflag[k >> 5], 1u << (k & 31));
         }
         if (tid == 0) s_nev = mine;
@@ -301,7 +307,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
                         ev_k[at] = k;
                         ev_off[2 * at] = d.rec_off[2 * e];
                         ev_off[2 * at + 1] = d.rec_off[2 * e + 1];
-                        ev_add[at] = d.rec_add[e];
+                        ev_add[at] = amount(e);
                     }
                     if (k < 32 * TMA_KFLAG_WORDS) atomicOr(&kflag[k >> 5], 1u << (k & 31));
                 }
@@ -348,8 +354,9 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
             } else {
                 for (int e = tid; e < nev_all; e += NT)
                     if (d.rec_owner[e] == (int)blockIdx.x && d.rec_k[e] == k) {
-                        add_slot(d.rec_off[2 * e], d.rec_add[e]);
-                        add_slot(d.rec_off[2 * e + 1], d.rec_add[e]);
+                        const float a = amount(e);
+                        add_slot(d.rec_off[2 * e], a);
+                        add_slot(d.rec_off[2 * e + 1], a);
                     }
             }
             fence_proxy_async_smem(); // before a later bulk copy overwrites them
