@@ -155,8 +155,11 @@ __device__ __forceinline__ bool plan_accept(const SimDev &d, const S *f, int y_r
 }
 
 // n_s = floor(g M / rho_cell + carry) (Sec. II) from the fixed-point active
-// mass, the carried fraction after it, and the first-pass candidate count
-// before clipping, ceil(n_s ratio 1.15) + 64 (FP64, as the oracle).
+// mass, and the carried fraction after it, in FP64 as the oracle. Also the
+// number of candidates for the first pass, ceil(n_s ratio 1.15) + 64 with
+// ratio the candidates per division seen last time: only a work estimate
+// (more are drawn if it falls short; the selection does not depend on it),
+// so FP32, as FP64 operations have long latencies here.
 // (Not inlined: it runs once per launch, and two inlined copies would only
 // add to the instruction fetches of a kernel that runs cold.)
 static __device__ __noinline__ void plan_ns(double growth_rate, double rho_cell, long long mass_fix, double carry_in,
@@ -167,8 +170,8 @@ static __device__ __noinline__ void plan_ns(double growth_rate, double rho_cell,
     const double fl = floor(xns);
     *ns_req = (long long)fl;
     *carry_out = xns - fl;
-    const double ratio = ratio_in > 1.0 ? ratio_in : 1.0;
-    *kcf = ceil((double)*ns_req * ratio * 1.15) + 64.0;
+    const float ratio = fmaxf((float)ratio_in, 1.0f);
+    *kcf = (double)(ceilf((float)*ns_req * ratio * 1.15f) + 64.0f);
 }
 
 template <typename S>
@@ -517,7 +520,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
         // drawn up to it, and the candidates per division for the next step
         if (tid == 0 && s_kstop) {
             sc->pend_cand = (long long)s_kstop;
-            sc->acc_ratio = (double)s_kstop / (double)ns;
+            sc->acc_ratio = (double)((float)s_kstop / (float)ns); // a work estimate only
         }
     }
     plan_grid_sync(sc, &s_dead);
