@@ -1,0 +1,195 @@
+"""Measurements on top of the simulation: the front's Fourier modes, their
+growth rates and the dispersion fit of Eq. 8, and the proliferation bias
+around the most and least advanced parts of the front (Sec. IV, Fig. 3).
+
+The analysis functions take plain arrays (front heights h(x) over time,
+division sites) and are independent of the GPU; `measure_*` run the
+simulation through the C ABI (``lbm.Simulation``) to produce those arrays.
+
+Geometry: the front is h(x), x = 0 .. W - 1 periodic, growing in +y (the
+paper grows in x, with y along the front). A mode of wavenumber k has
+q = 2 pi k / W.
+
+Run ``python -m paper_2303_02210_gb300.experiments dispersion`` (or
+``bias``) for a JSON summary.
+"""
+from __future__ import annotations
+
+import json
+import math
+from typing import Dict, Iterable, List, Optional, Sequence
+
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# Analysis (host only)
+
+def front_modes(h: np.ndarray) -> np.ndarray:
+    """Complex Fourier amplitudes a_k, k = 0 .. W//2, of a front profile h(x)
+    (the last axis), normalised so that h(x) = A cos(2 pi k x / W + phi)
+    gives |a_k| = A (0 < k < W/2) and a_0 = mean h."""
+    h = np.asarray(h, dtype=np.float64)
+    W = h.shape[-1]
+    a = np.fft.rfft(h, axis=-1) / W
+    a[..., 1:] *= 2.0
+    if W % 2 == 0:
+        a[..., -1] /= 2.0
+    return a
+
+
+def growth_rates(times: Sequence[float], heights: np.ndarray, ks: Iterable[int],
+                 t_min: Optional[float] = None, t_max: Optional[float] = None) -> Dict[int, float]:
+    """Exponential growth rate omega_k of each mode k: the least-squares slope
+    of log |a_k(t)| against t over the samples with t_min <= t <= t_max
+    (heights: one row of h(x) per time). In the frame comoving with the mean
+    height (mode 0 is left out), as in the linear stability analysis behind
+    Eq. 8."""
+    t = np.asarray(times, dtype=np.float64)
+    a = np.abs(front_modes(heights))
+    sel = np.ones_like(t, dtype=bool)
+    if t_min is not None:
+        sel &= t >= t_min
+    if t_max is not None:
+        sel &= t <= t_max
+    out = {}
+    for k in ks:
+        y = a[sel, k]
+        ok = y > 0
+        if ok.sum() < 2:
+            out[k] = float("nan")
+            continue
+        out[k] = float(np.polyfit(t[sel][ok], np.log(y[ok]), 1)[0])
+    return out
+
+
+def fit_dispersion(q: Sequence[float], omega: Sequence[float]) -> dict:
+    """Least-squares fit of omega(q) = k - gamma q^2 (Eq. 8). Returns k,
+    gamma, the unstable band q < q_c = sqrt(k / gamma) when k, gamma > 0, the
+    paper's critical size L_c = sqrt(gamma / k), and the smallest unstable
+    lattice width 2 pi / q_c."""
+    q = np.asarray(q, dtype=np.float64)
+    w = np.asarray(omega, dtype=np.float64)
+    ok = np.isfinite(w)
+    A = np.stack([np.ones(ok.sum()), -q[ok] ** 2], axis=1)
+    (k, gamma), *_ = np.linalg.lstsq(A, w[ok], rcond=None)
+    res = w[ok] - A @ np.array([k, gamma])
+    out = {"k": float(k), "gamma": float(gamma), "rms_residual": float(np.sqrt(np.mean(res ** 2))),
+           "points": int(ok.sum())}
+    if k > 0 and gamma > 0:
+        out["q_c"] = math.sqrt(k / gamma)
+        out["L_c"] = math.sqrt(gamma / k)
+        out["width_c"] = 2 * math.pi / out["q_c"]
+    return out
+
+
+def box_counts(h: np.ndarray, nodes: np.ndarray, counts: np.ndarray, W: int,
+               half_width: int = 10, depth: int = 20) -> tuple:
+    """Divisions in the two boxes of Fig. 3(c): columns within `half_width`
+    of the most (least) advanced column, periodic in x, and the `depth` rows
+    below that column's front height. `nodes` are y W + x, `counts` how often
+    each was drawn. Returns (count near h_max, count near h_min)."""
+    h = np.asarray(h)
+    x_hi, x_lo = int(np.argmax(h)), int(np.argmin(h))
+    y = np.asarray(nodes) // W
+    x = np.asarray(nodes) % W
+    c = np.asarray(counts)
+
+    def in_box(xc):
+        dx = (x - xc + W // 2) % W - W // 2
+        hb = int(h[xc])
+        return (np.abs(dx) <= half_width) & (y < hb) & (y >= hb - depth)
+
+    return int(c[in_box(x_hi)].sum()), int(c[in_box(x_lo)].sum())
+
+
+# ---------------------------------------------------------------------------
+# Measurements (GPU, through the C ABI)
+
+def dispersion_params(width: int = 512, k: int = 4, amp: float = 4.0, seed: int = 1, **kw) -> dict:
+    """One sinusoidal mode on a flat front: the lattice workloads' density
+    scale (R22), density-dependent growth (Eq. 5), fixed rear wall, height
+    width / 2 with the front at a quarter of it."""
+    from . import workloads as wl
+    H = width // 2
+    p = wl.base_params(width=width, height=H, tau=0.8, growth_mode="density", growth_rate=1e-3,
+                       front_kind="sinusoidal", front_row=float(H // 4), front_amp=amp,
+                       front_kmin=k, front_kmax=k, wall_mode="fixed", seed=seed, sim_id=k)
+    p.update(kw)
+    return p
+
+
+def measure_dispersion(width: int = 512, ks: Sequence[int] = (2, 4, 8, 16, 32), steps: int = 3000,
+                       every: int = 50, amp: float = 4.0, precision: str = "fp32", **kw) -> dict:
+    """omega(q) from single-mode runs (one simulation per k, the mode's
+    amplitude sampled every `every` steps), then the Eq. 8 fit."""
+    from .lbm import Simulation
+    rows = []
+    for k in ks:
+        p = dispersion_params(width=width, k=k, amp=amp, **kw)
+        sim = Simulation(p, precision=precision)
+        times, hs = [], []
+        for s in range(0, steps + 1, every):
+            if s:
+                sim.step(every)
+            h, _, _ = sim.front_heights()
+            times.append(s)
+            hs.append(h.astype(np.float64))
+        status = sim.stats()["status"]
+        sim.close()
+        hs = np.array(hs)
+        om = growth_rates(times, hs, [k])[k]
+        a = np.abs(front_modes(hs)[:, k])
+        rows.append({"k": int(k), "q": 2 * math.pi * k / width, "omega": om,
+                     "amp_start": float(a[0]), "amp_end": float(a[-1]), "status": int(status)})
+    fit = fit_dispersion([r["q"] for r in rows], [r["omega"] for r in rows])
+    return {"width": width, "steps": steps, "every": every, "modes": rows, "fit": fit}
+
+
+def measure_bias(width: int = 1024, steps: int = 4000, warm: int = 1000, seed: int = 1,
+                 precision: str = "fp32", **kw) -> dict:
+    """Fig. 3(c): divisions per step near h_max and near h_min (boxes of 21
+    columns by 20 rows below the front), density-dependent growth, after
+    `warm` steps; and the share of the front's roughness in its longest
+    mode at the end (the system-spanning instability of Fig. 3(b))."""
+    from .lbm import Simulation
+    from . import workloads as wl
+    H = width // 2
+    p = wl.base_params(width=width, height=H, tau=0.8, growth_mode="density", growth_rate=1e-3,
+                       front_kind="flat", front_row=float(H // 4), front_amp=0.5, wall_mode="advance",
+                       seed=seed, sim_id=seed)
+    p.update(kw)
+    sim = Simulation(p, precision=precision)
+    sim.step(warm)
+    n_hi = n_lo = 0
+    for _ in range(steps):
+        sim.step(1)
+        h, _, _ = sim.front_heights()
+        nodes, _, cnt = sim.last_events()
+        a, b = box_counts(h, nodes, cnt, width)
+        n_hi += a
+        n_lo += b
+    h, hbar, w = sim.front_heights()
+    sim.close()
+    a = np.abs(front_modes(h.astype(np.float64)))[1:]
+    power = a ** 2
+    return {"width": width, "steps": steps, "warm": warm, "divisions_near_hmax": n_hi,
+            "divisions_near_hmin": n_lo, "ratio": (n_hi / n_lo) if n_lo else None,
+            "hbar": float(hbar), "w": float(w),
+            "longest_mode_share": float(power[0] / power.sum()) if power.sum() > 0 else None}
+
+
+def main(argv: Optional[List[str]] = None) -> None:
+    import argparse
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("what", choices=["dispersion", "bias"])
+    ap.add_argument("--width", type=int, default=None)
+    ap.add_argument("--steps", type=int, default=None)
+    args = ap.parse_args(argv)
+    kw = {k: v for k, v in (("width", args.width), ("steps", args.steps)) if v is not None}
+    out = measure_dispersion(**kw) if args.what == "dispersion" else measure_bias(**kw)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

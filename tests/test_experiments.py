@@ -1,0 +1,93 @@
+"""The front-mode analysis of `experiments` (Eq. 8's dispersion fit and the
+Fig. 3(c) box counts), pinned on synthetic fronts with known answers; and,
+on the GPU, the measurement through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2303_02210_gb300 import experiments as ex
+
+
+def test_front_modes_amplitudes_and_mean():
+    W = 256
+    x = np.arange(W)
+    h = 5.0 + 3.0 * np.cos(2 * np.pi * 4 * x / W + 0.3) + 0.5 * np.sin(2 * np.pi * 9 * x / W) \
+        + 0.25 * np.cos(np.pi * x)  # the Nyquist mode, k = W / 2
+    a = ex.front_modes(h)
+    assert a.shape == (W // 2 + 1,)
+    assert abs(a[0] - 5.0) < 1e-12
+    assert abs(abs(a[4]) - 3.0) < 1e-12 and abs(np.angle(a[4]) - 0.3) < 1e-12
+    assert abs(abs(a[9]) - 0.5) < 1e-12
+    assert abs(abs(a[W // 2]) - 0.25) < 1e-12
+    others = np.delete(np.abs(a), [0, 4, 9, W // 2])
+    assert others.max() < 1e-12
+
+
+def test_growth_rates_recover_exponentials_in_the_comoving_frame():
+    W = 128
+    x = np.arange(W)
+    rates = {2: 3e-3, 5: -1e-3, 11: -8e-3}
+    times = np.arange(0, 2001, 50, dtype=float)
+    hs = []
+    for t in times:
+        h = 40.0 + 0.01 * t  # the mean advances; mode 0 is not a perturbation
+        for k, om in rates.items():
+            h = h + 2.0 * math.exp(om * t) * np.cos(2 * np.pi * k * x / W + k)
+        hs.append(h)
+    got = ex.growth_rates(times, np.array(hs), rates.keys())
+    for k, om in rates.items():
+        assert abs(got[k] - om) < 1e-7 * abs(om), (k, got[k], om)  # FFT rounding of a mode at 2e-7
+    # a window restricts the fit
+    got = ex.growth_rates(times, np.array(hs), [2], t_min=1000)
+    assert abs(got[2] - 3e-3) < 1e-12
+
+
+def test_dispersion_fit_recovers_k_gamma_and_critical_size():
+    k, gamma = 2e-3, 0.5
+    q = 2 * np.pi * np.array([1, 2, 3, 4, 6, 8]) / 256
+    rng = np.random.default_rng(3)
+    om = k - gamma * q ** 2 + rng.normal(0, 1e-7, q.size)
+    fit = ex.fit_dispersion(q, om)
+    assert abs(fit["k"] - k) < 1e-6 and abs(fit["gamma"] - gamma) < 1e-3
+    assert abs(fit["q_c"] - math.sqrt(k / gamma)) < 1e-3
+    assert abs(fit["L_c"] - math.sqrt(gamma / k)) < 0.1
+    # a stable front (k < 0) has no critical size
+    fit = ex.fit_dispersion(q, -1e-3 - gamma * q ** 2)
+    assert fit["k"] < 0 and "q_c" not in fit
+
+
+def test_box_counts_wrap_and_depth():
+    W = 64
+    h = np.full(W, 30)
+    h[2] = 40   # most advanced: its box wraps to columns W - 8 .. 12
+    h[33] = 20  # least advanced
+    nodes, counts = [], []
+
+    def put(x, y, c=1):
+        nodes.append(y * W + x)
+        counts.append(c)
+
+    put(2, 39)            # inside the h_max box, top row
+    put(W - 8, 20)        # inside (wrapped column, deepest row)
+    put(12, 25, 3)        # inside, drawn three times
+    put(2, 40)            # above the front: outside
+    put(2, 19)            # 21 rows below: outside
+    put(13, 30)           # 11 columns away: outside
+    put(33, 19)           # inside the h_min box
+    put(44, 0)            # 11 columns from the h_min column: outside
+    hi, lo = ex.box_counts(h, np.array(nodes), np.array(counts), W)
+    assert hi == 5 and lo == 1
+
+
+@pytest.mark.gpu
+def test_measured_dispersion_short_waves_decay():
+    """Single-mode fronts on a 256-wide lattice: the mode amplitudes are
+    measured from the simulation's front heights; short waves flatten (the
+    bounce-back surface tension of Eq. 7), faster than long ones."""
+    out = ex.measure_dispersion(width=256, ks=(2, 16, 32), steps=1200, every=50)
+    om = {r["k"]: r["omega"] for r in out["modes"]}
+    print(out)
+    assert all(math.isfinite(v) for v in om.values())
+    assert om[32] < 0 and om[32] < om[2]
+    assert out["modes"][-1]["amp_end"] < out["modes"][-1]["amp_start"]
