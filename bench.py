@@ -43,8 +43,11 @@ UNIT = "MLUPS"
 WORKLOAD_NAME = "lattice_edge"
 
 
+WIDTH = 4096  # lattice width of the headline workload (--width changes it, for profiling captures)
+
+
 def workload_params(rank: int = 0) -> dict:
-    return wl.lattice_edge(seed=1 + rank, sim_id=rank)
+    return wl.lattice_edge(seed=1 + rank, sim_id=rank, width=WIDTH)
 
 
 def workload_config(precision: str) -> dict:
@@ -337,10 +340,14 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--update-kernel", default="auto", choices=["auto", "plain", "tma", "tma1", "tma_sel"])
     ap.add_argument("--cpu-steps", type=int, default=12)
+    ap.add_argument("--width", type=int, default=4096,
+                    help="lattice width (4096: the headline workload; others for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the batched-ensemble, serving and 16-bit storage measurements")
     args = ap.parse_args()
+    global WIDTH
+    WIDTH = args.width
     if args.impl == "reference":
         run_reference(args)
         return
