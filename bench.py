@@ -173,8 +173,9 @@ class ClockSampler:
 def measure_ensemble(n: int = 256, steps: int = 200, warm: int = 5) -> dict:
     """The batched form: n uneven realisations (widths 256..2048, height =
     width / 2, bulk or edge growth, FP32) advanced together by lbm_batch_step
-    (one graph replay per step or four), against the same simulations stepped
-    one after another with lbm_step. Aggregate active-window node updates per
+    (graph replays of three batched launches per step: injection, update and
+    one planner block per member), against the same simulations stepped one
+    after another with lbm_step. Aggregate active-window node updates per
     second, device time by CUDA events around each region."""
     import torch
     from paper_2303_02210_gb300.lbm import Batch, Simulation

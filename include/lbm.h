@@ -220,10 +220,13 @@ const char *lbm_version(void);
  * The ensembles the roughness statistics of Sec. III need (many realisations
  * of Eq. 6's w(t)) are many small, independent lattices; stepped one after
  * another they leave most of the GPU idle. A batch advances its simulations
- * together: one replay of a CUDA graph holding, for each simulation, a chain
- * of steps (update + planner) as an independent branch, so the kernels of
- * different simulations run side by side. Each simulation computes exactly
- * what lbm_step would (the same kernels, the same counters).
+ * together by replaying a CUDA graph. When all members store their
+ * populations in the same type, a step of the whole batch is three launches
+ * (injection, update, planner), each over a table of every member's blocks,
+ * with one planner block per member; otherwise the graph holds, for each
+ * simulation, a chain of steps (update + planner) as an independent branch.
+ * Each simulation computes exactly what lbm_step would (the same arithmetic
+ * and counters, bit for bit).
  *  sims    n distinct handles on one device, created by lbm_create and not
  *          in kernel timing; the batch keeps the pointers, the caller keeps
  *          ownership and must destroy the batch before any of them.
@@ -233,11 +236,16 @@ const char *lbm_version(void);
  * afterwards; queries on a member (lbm_stats, lbm_front_heights, ...) then see
  * the result. Between lbm_batch_step calls the members may also be stepped on
  * their own. The graphs are captured in lbm_batch_create (LBM_ERR_CUDA if
- * capture fails); lbm_batch_create allocates streams, events and graphs. */
+ * capture fails); lbm_batch_create allocates streams, events, graphs and
+ * the batched launches' tables in device memory. */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **out);
 int lbm_batch_step(lbm_batch *batch, int64_t nsteps);
 int lbm_batch_destroy(lbm_batch *batch);
+/* 1 if the batch steps with the batched launches (all members share the
+ * storage type), 0 if with one graph branch per member; LBM_ERR_INVALID_ARG
+ * for NULL. */
+int lbm_batch_fused(const lbm_batch *batch);
 
 /* ---- allocation-free variant (the paper has no counterpart) ----
  * Front heights h(x) = 1 + highest set row of column x (0 if none) of a

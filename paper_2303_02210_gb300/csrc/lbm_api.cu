@@ -823,9 +823,11 @@ const char *lbm_version(void) { return "0.1.0 sm_103a"; }
 
 // ---------------------------------------------------------------------------
 // Batched stepping: independent simulations advanced together by replaying a
-// CUDA graph that holds one chain of steps per simulation as parallel branches
-// (the kernels read the step index from each simulation's device scalars, so
-// the same graph serves every step).
+// CUDA graph (the kernels read the step index from each simulation's device
+// scalars, so the same graph serves every step). When every member stores its
+// populations in the same type, a step is three launches for the whole batch
+// (injection, update, planner; each over a table of the members' blocks);
+// otherwise the graph holds one chain of steps per member as parallel branches.
 struct lbm_batch {
     std::vector<lbm_sim *> sims;
     int device;
@@ -835,19 +837,35 @@ struct lbm_batch {
     cudaEvent_t fork;
     std::vector<cudaEvent_t> join;
     cudaGraphExec_t exec[2]; // one step, kBatchChain steps
+    // batched launches: the members' SimDev and the block tables, in one allocation
+    bool fused;
+    void *dev_mem;
+    const SimDev *ds;
+    const int4 *bm_upd, *bm_inj;
+    int nb_upd, nb_inj;
 };
 
 namespace {
 constexpr int kBatchChain = 4; // steps per branch in the longer graph
 
-// Captures `steps` steps of every simulation, one branch each, into an
-// executable graph.
+// Captures `steps` steps of every simulation into an executable graph:
+// batched launches, or one branch per simulation.
 cudaError_t batch_capture(lbm_batch *b, int steps, cudaGraphExec_t *out)
 {
     cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaError_t first = cudaEventRecord(b->fork, b->origin);
-    for (size_t i = 0; i < b->sims.size() && first == cudaSuccess; ++i) {
+    cudaError_t first = cudaSuccess;
+    if (b->fused) {
+        const KernelTable *kt = b->sims[0]->kt;
+        for (int k = 0; k < steps && first == cudaSuccess; ++k) {
+            first = kt->batch_inject(b->ds, b->bm_inj, b->nb_inj, b->origin);
+            if (first == cudaSuccess) first = kt->batch_update(b->ds, b->bm_upd, b->nb_upd, b->origin);
+            if (first == cudaSuccess) first = kt->batch_plan(b->ds, (int)b->sims.size(), b->origin);
+        }
+    } else {
+        first = cudaEventRecord(b->fork, b->origin);
+    }
+    for (size_t i = 0; i < b->sims.size() && first == cudaSuccess && !b->fused; ++i) {
         lbm_sim *s = b->sims[i];
         first = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
         for (int k = 0; k < steps && first == cudaSuccess; ++k) {
@@ -863,6 +881,49 @@ cudaError_t batch_capture(lbm_batch *b, int steps, cudaGraphExec_t *out)
     if (first == cudaSuccess) first = cudaGraphInstantiate(out, g, 0);
     if (g) cudaGraphDestroy(g);
     return first;
+}
+
+// The batched launches' tables: the members' SimDev, the update's blocks
+// (about two waves of the update kernel for the whole batch, dealt by lattice
+// area, each member a multiple of its column tiles) and the injection's
+// blocks (one per 1024 divisions the member's planner can hold).
+cudaError_t batch_tables(lbm_batch *b)
+{
+    const KernelTable *kt = b->sims[0]->kt;
+    int nsm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) return e;
+    const int bps = std::max(1, kt->update_blocks_per_sm());
+    double area = 0.0;
+    for (const lbm_sim *s : b->sims) area += (double)s->p.width * (double)s->p.height;
+    const double target = 2.0 * nsm * bps;
+    std::vector<int4> upd, inj;
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        const lbm_sim *s = b->sims[i];
+        const int ncx = (s->p.width + kt->update_tile_x - 1) / kt->update_tile_x;
+        const double share = target * (double)s->p.width * (double)s->p.height / area;
+        const int nbu = std::max(1, (int)std::lround(share / ncx)) * ncx;
+        for (int j = 0; j < nbu; ++j) upd.push_back(make_int4((int)i, j, nbu, 0));
+        const int nbi = std::max(1, (s->L.ns_max + 1023) / 1024);
+        for (int j = 0; j < nbi; ++j) inj.push_back(make_int4((int)i, j, nbi, 0));
+    }
+    const size_t n = b->sims.size();
+    const size_t off_u = align256(n * sizeof(SimDev));
+    const size_t off_i = align256(off_u + upd.size() * sizeof(int4));
+    e = cudaMalloc(&b->dev_mem, off_i + inj.size() * sizeof(int4));
+    if (e != cudaSuccess) return e;
+    std::vector<SimDev> ds(n);
+    for (size_t i = 0; i < n; ++i) ds[i] = b->sims[i]->d;
+    char *base = (char *)b->dev_mem;
+    e = cudaMemcpy(base, ds.data(), n * sizeof(SimDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + off_u, upd.data(), upd.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + off_i, inj.data(), inj.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    b->ds = (const SimDev *)base;
+    b->bm_upd = (const int4 *)(base + off_u);
+    b->bm_inj = (const int4 *)(base + off_i);
+    b->nb_upd = (int)upd.size();
+    b->nb_inj = (int)inj.size();
+    return e;
 }
 } // namespace
 
@@ -884,8 +945,19 @@ int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **
     b->origin = nullptr;
     b->exec[0] = b->exec[1] = nullptr;
     b->fork = nullptr;
+    b->dev_mem = nullptr;
+    b->ds = nullptr;
+    b->bm_upd = b->bm_inj = nullptr;
+    b->nb_upd = b->nb_inj = 0;
+    // one launch per kernel for the whole batch when the members share the
+    // storage type (the plain-load update; the results are the same as the
+    // TMA-staged one's, bit for bit)
+    b->fused = true;
+    for (int32_t i = 1; i < n; ++i)
+        if (sims[i]->kt != sims[0]->kt) b->fused = false;
     cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+    if (e == cudaSuccess && b->fused) e = batch_tables(b);
     // one-time kernel attributes are set outside the capture
     for (int32_t i = 0; i < n && e == cudaSuccess; ++i)
         if (sims[i]->use_tma) e = sims[i]->kt->tma_prepare(sims[i]->d, sims[i]->tma_variant);
@@ -931,6 +1003,12 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps)
     return LBM_OK;
 }
 
+int lbm_batch_fused(const lbm_batch *b)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    return b->fused ? 1 : 0;
+}
+
 int lbm_batch_destroy(lbm_batch *b)
 {
     if (!b) return LBM_OK;
@@ -942,6 +1020,7 @@ int lbm_batch_destroy(lbm_batch *b)
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->dev_mem) cudaFree(b->dev_mem);
     delete b;
     return LBM_OK;
 }

@@ -212,6 +212,14 @@ struct KernelTable {
     // programmatic dependent of the preceding planner kernel.
     cudaError_t (*tma_prepare)(const SimDev &, int variant);
     cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t);
+    // One step's kernels for every simulation of a batch in one launch each:
+    // ds, the simulations' SimDev in device memory; bm, nb entries (simulation,
+    // block, blocks) of the update's (a multiple of each simulation's column
+    // tiles) or the injection's block table; the planner takes one block per
+    // simulation.
+    cudaError_t (*batch_inject)(const SimDev *ds, const int4 *bm, int nb, cudaStream_t);
+    cudaError_t (*batch_update)(const SimDev *ds, const int4 *bm, int nb, cudaStream_t);
+    cudaError_t (*batch_plan)(const SimDev *ds, int n, cudaStream_t);
 };
 
 extern const KernelTable kTableF32;

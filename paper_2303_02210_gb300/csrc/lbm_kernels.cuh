@@ -529,9 +529,10 @@ __device__ __forceinline__ R fix_negative(R *fo, int mode)
 
 // ===========================================================================
 // Fused update of the active window (App. A steps 1, 2, 4-7; the injection of
-// step 3 was already added to the pre-stream slots by k_plan).
+// step 3 was already added to the pre-stream slots by k_inject), run by blocks
+// blk = 0 .. nblk - 1 of TPB threads.
 template <typename S, int TPB, int NR>
-__global__ void __launch_bounds__(TPB) k_update(SimDev d)
+__device__ __forceinline__ void update_body(const SimDev &d, int blk, int nblk)
 {
     using R = arith_t<S>;
     const Pop<S> pc(d);
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d)
     // Rows the rear wall has just frozen: bring this copy up to date.
     if (y_copy < y_r) {
         const long long n = (long long)(y_r - y_copy) * Wp;
-        for (long long k = (long long)blockIdx.x * TPB + threadIdx.x; k < n; k += (long long)gridDim.x * TPB) {
+        for (long long k = (long long)blk * TPB + threadIdx.x; k < n; k += (long long)nblk * TPB) {
             const long long o = (long long)y_copy * Wp + k - kXO; // whole stored rows, ghosts included
 #pragma unroll
             for (int i = 0; i < NQ; ++i) fout[i * P + o] = fin[i * P + o];
@@ -568,9 +569,9 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d)
         // the grid is a multiple of the column-tile count: each block keeps
         // one column tile and strides over the rows
         const int nty = (nrows + NR - 1) / NR;
-        const int tx = (int)(blockIdx.x % ncx);
-        const int ty_step = (int)(gridDim.x / ncx);
-        for (int ty = (int)(blockIdx.x / ncx); ty < nty; ty += ty_step) {
+        const int tx = blk % ncx;
+        const int ty_step = nblk / ncx;
+        for (int ty = blk / ncx; ty < nty; ty += ty_step) {
             const int x = tx * TPB + threadIdx.x;
             const bool colok = x < W;
             const int xm = x == 0 ? W - 1 : x - 1;
@@ -655,6 +656,17 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d)
                         for (int i = 0; i < NQ; ++i) o[i * P] = fo[i];
                         ro = node_mass<R>(fo, rho, added);
                     }
+                    // the ghost copies of the edge columns (stored x = W and
+                    // x = -1), which the TMA-staged update reads: a lattice
+                    // may be stepped by either kernel
+                    if (x == 0) {
+#pragma unroll
+                        for (int i = 0; i < NQ; ++i) o[i * P + W] = pc.st(fo[i], i);
+                    }
+                    if (x == W - 1) {
+#pragma unroll
+                        for (int i = 0; i < NQ; ++i) o[i * P - W] = pc.st(fo[i], i);
+                    }
                     // populations are non-negative after every step, so the
                     // node holds mass iff their sum is non-zero
                     mass += fix24<R>(ro);
@@ -671,6 +683,23 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d)
         if (maxrow >= 0) atomicMax(&d.sc->maxmass_accum, maxrow);
         if (clipd != 0.0) atomicAdd(&d.sc->clip_mass, clipd);
     }
+}
+
+// The update of one simulation: the grid is a multiple of its column tiles.
+template <typename S, int TPB, int NR>
+__global__ void __launch_bounds__(TPB) k_update(SimDev d)
+{
+    update_body<S, TPB, NR>(d, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// The updates of a batch of simulations in one launch: block b works for
+// simulation bm[b].x as its block bm[b].y of bm[b].z, a multiple of that
+// simulation's column tiles (a table built once per batch).
+template <typename S, int TPB, int NR>
+__global__ void __launch_bounds__(TPB) k_update_batch(const SimDev *__restrict__ ds, const int4 *__restrict__ bm)
+{
+    const int4 a = bm[blockIdx.x];
+    update_body<S, TPB, NR>(ds[a.x], a.y, a.z);
 }
 
 // ===========================================================================

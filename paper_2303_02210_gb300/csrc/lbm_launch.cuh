@@ -47,6 +47,21 @@ struct Launch {
         k_fields<S><<<4 * 152, 256, 0, s>>>(d, cur, rho, ux, uy);
         return cudaGetLastError();
     }
+    static cudaError_t batch_inject(const SimDev *ds, const int4 *bm, int nb, cudaStream_t s)
+    {
+        k_inject_batch<S><<<nb, 128, 0, s>>>(ds, bm);
+        return cudaGetLastError();
+    }
+    static cudaError_t batch_update(const SimDev *ds, const int4 *bm, int nb, cudaStream_t s)
+    {
+        k_update_batch<S, UPD_TPB, UPD_NR><<<nb, UPD_TPB, 0, s>>>(ds, bm);
+        return cudaGetLastError();
+    }
+    static cudaError_t batch_plan(const SimDev *ds, int n, cudaStream_t s)
+    {
+        k_plan_batch<S><<<n, PLAN_NT, 0, s>>>(ds);
+        return cudaGetLastError();
+    }
     static int update_blocks_per_sm()
     {
         int n = 0;
@@ -65,7 +80,8 @@ constexpr KernelTable make_table(cudaError_t (*tma_prepare)(const SimDev &, int)
                        &Launch<S>::scan,     &Launch<S>::plan,          &Launch<S>::inject,
                        &Launch<S>::update,
                        &Launch<S>::fields,   &plan_blocks_per_sm<S>,    &Launch<S>::update_blocks_per_sm,
-                       Launch<S>::UPD_TPB,   tma_prepare,               tma_update};
+                       Launch<S>::UPD_TPB,   tma_prepare,               tma_update,
+                       &Launch<S>::batch_inject, &Launch<S>::batch_update, &Launch<S>::batch_plan};
 }
 
 } // namespace lbm

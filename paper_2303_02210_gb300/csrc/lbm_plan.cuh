@@ -51,12 +51,15 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-__device__ __forceinline__ void plan_grid_sync(DevScalars *sc, int *s_dead)
+// (G: the blocks of the grid that plan this simulation; with one block the
+// barrier is the block's own.)
+__device__ __forceinline__ void plan_grid_sync(DevScalars *sc, int *s_dead, int G)
 {
     __syncthreads();
+    if (G == 1) return;
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned long long g = gridDim.x;
+        const unsigned long long g = (unsigned long long)G;
         const unsigned long long old = atomicAdd(&sc->bar_ctr, 1ull);
         const unsigned long long target = (old / g + 1ull) * g;
         if (!*s_dead) {
@@ -174,8 +177,10 @@ static __device__ __noinline__ void plan_ns(double growth_rate, double rho_cell,
     *kcf = (double)(ceilf((float)*ns_req * ratio * 1.15f) + 64.0f);
 }
 
+// The planner of one simulation, run by blocks blk = 0 .. G - 1 of PLAN_NT
+// threads (all resident together when G > 1).
 template <typename S>
-__global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
+__device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int blk)
 {
     using R = arith_t<S>;
     DevScalars *sc = d.sc;
@@ -185,7 +190,6 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
     const int cur = (int)(tn & 1u);
     S *f = (S *)d.f[cur];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = (int)gridDim.x, blk = (int)blockIdx.x;
     __shared__ long long s_ll[PLAN_WARPS];
     __shared__ int s_i[PLAN_WARPS], s_i2[PLAN_WARPS];
     __shared__ int s_dead;
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
             d.pl_low[blk] = lw;
         }
     }
-    plan_grid_sync(sc, &s_dead);
+    plan_grid_sync(sc, &s_dead, G);
 
     // ---- B: Eq. 6 sums, the rear wall, the active mass and the next plan
     // (every block computes the same values from the same partials)
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
         }
         fm = plan_block_sum(fm, s_ll);
         if (tid == 0) d.pl_mass[blk] = fm;
-        plan_grid_sync(sc, &s_dead);
+        plan_grid_sync(sc, &s_dead, G);
         long long a = 0;
         for (int i = tid; i < G; i += PLAN_NT) a += __ldcg(&d.pl_mass[i]);
         frozen = plan_block_sum(a, s_ll);
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
             tot_b += t_i;
         }
         if (tid == 0) d.pl_cnt[blk] = tot_b;
-        plan_grid_sync(sc, &s_dead);
+        plan_grid_sync(sc, &s_dead, G);
         long long before = 0, total = 0;
         for (int i = tid; i < G; i += PLAN_NT) {
             const long long c = __ldcg(&d.pl_cnt[i]);
@@ -499,7 +503,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
             const int pr = plan_block_exscan(a ? 1 : 0, &tot_r, s_i);
             int *cnt = d.pl_cnt + (round & 1) * kPlanMaxBlocks;
             if (tid == 0) cnt[blk] = tot_r;
-            plan_grid_sync(sc, &s_dead);
+            plan_grid_sync(sc, &s_dead, G);
             long long bf = 0, tt = 0;
             for (int i = tid; i < G; i += PLAN_NT) {
                 const long long c = __ldcg(&cnt[i]);
@@ -523,7 +527,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
             sc->acc_ratio = (double)((float)s_kstop / (float)ns); // a work estimate only
         }
     }
-    plan_grid_sync(sc, &s_dead);
+    plan_grid_sync(sc, &s_dead, G);
 
     // ---- E: the table emptied for the next selection
     const int nsel = (int)(acc < ns ? acc : ns); // selected divisions (draw ranks)
@@ -593,13 +597,29 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
     }
 }
 
+// The planner of one simulation on a cooperative grid (launch_plan).
+template <typename S>
+__global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
+{
+    plan_body<S>(d, init, (int)gridDim.x, (int)blockIdx.x);
+}
+
+// The planners of a batch of simulations, one block each (ds[blockIdx.x]):
+// a block's barriers are its own, so the blocks need not be resident
+// together and the launch is an ordinary one.
+template <typename S>
+__global__ void __launch_bounds__(PLAN_NT) k_plan_batch(const SimDev *__restrict__ ds)
+{
+    plan_body<S>(ds[blockIdx.x], 0, 1, 0);
+}
+
 // App. A step 3 for the update kernels that read the populations from global
 // memory: count * rho_cell/2 into the two pre-stream slots of each selected
 // (node, pair) of step t, right before the update of step t. Distinct
 // (node, pair) never share a slot (each slot streams into exactly one
 // direction of one node).
 template <typename S>
-__global__ void k_inject(SimDev d)
+__device__ __forceinline__ void inject_body(const SimDev &d, int blk, int nblk)
 {
     using R = arith_t<S>;
     const Pop<S> pc(d);
@@ -608,7 +628,7 @@ __global__ void k_inject(SimDev d)
     S *f = (S *)d.f[cur];
     const int n = d.sc->rec_n, y_r = d.sc->y_r;
     const size_t buf = (size_t)(t & 1u) * (size_t)d.ns_max;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    for (int e = blk * (int)blockDim.x + (int)threadIdx.x; e < n; e += nblk * (int)blockDim.x) {
         const int cnt = d.ev_count[buf + e];
         if (cnt == 0) continue; // a repeat, counted at its first rank
         const uint32_t key = d.ev_key[buf + e];
@@ -627,6 +647,21 @@ __global__ void k_inject(SimDev d)
             if (xc == d.W - 1) f[o - d.W] = v;
         }
     }
+}
+
+template <typename S>
+__global__ void k_inject(SimDev d)
+{
+    inject_body<S>(d, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Block b of a batched launch works for simulation bm[b].x as its block
+// bm[b].y of bm[b].z (a table built once per batch).
+template <typename S>
+__global__ void k_inject_batch(const SimDev *__restrict__ ds, const int4 *__restrict__ bm)
+{
+    const int4 a = bm[blockIdx.x];
+    inject_body<S>(ds[a.x], a.y, a.z);
 }
 
 template <typename S>

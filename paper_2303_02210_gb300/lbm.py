@@ -102,6 +102,7 @@ _SIGNATURES = {
     "lbm_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(_P)]),
     "lbm_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbm_batch_destroy": (ctypes.c_int, [_P]),
+    "lbm_batch_fused": (ctypes.c_int, [_P]),
 }
 
 _lib = None
@@ -360,6 +361,11 @@ class Batch:
         _check(self._lib.lbm_batch_step(self._h, int(n)), "lbm_batch_step")
 
     step = lbm_batch_step
+
+    @property
+    def fused(self) -> bool:
+        """True if a step of the batch is three batched launches."""
+        return self._lib.lbm_batch_fused(self._h) == 1
 
     def close(self):
         if getattr(self, "_h", None):

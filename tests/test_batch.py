@@ -66,3 +66,63 @@ def test_batch_and_single_steps_interleave():
     for g, s in zip(members, solos):
         same(g, s)
     batch.close()
+
+
+FUSED_FP32 = [
+    (wl.lattice_small(seed=41, growth_rate=3e-3), "fp32", "auto"),
+    (wl.lattice_small(seed=42, width=300, height=70, front_row=30.0, growth_rate=3e-3, growth_mode="edge",
+                      edge_depth=4, front_kind="sinusoidal", front_amp=2.0), "fp32", "auto"),
+    (wl.lattice_small(seed=43, width=37, height=29, front_row=9.0, growth_rate=3e-3), "fp32", "plain"),
+    (wl.lattice_small(seed=44, growth_mode="density", growth_rate=3e-3), "fp32", "auto"),
+    (wl.lattice_small(seed=45, width=64, height=96, front_kind="sinusoidal", front_row=40.0, front_amp=3.0,
+                      front_kmax=4, growth_rate=3e-3, wall_min_gap=2.0), "fp32", "auto"),
+    (wl.base_params(width=48, height=32, front_kind="full", y_periodic=1, wall_mode="fixed",
+                    growth_rate=2e-3, seed=46, sim_id=46), "fp32", "auto"),
+    (wl.lattice_small(seed=47, growth_mode="none", width=1, height=24, front_row=8.0), "fp32", "auto"),
+    (wl.lattice_small(seed=48, growth_mode="band", band_rows=10, growth_rate=3e-3, height=96,
+                      front_row=40.0, wall_min_gap=12.0, sigma=0.05, negfix_mode="rescale"), "fp32", "auto"),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_fused_batch_matches_single_stepping(precision):
+    """Members sharing a storage type step with three batched launches per
+    step (one planner block per member, a shared table of update blocks):
+    every member ends bit for bit where lbm_step takes it, whichever update
+    kernel it uses alone."""
+    from paper_2303_02210_gb300.lbm import Batch
+    ms = [(p, precision, k) for p, _, k in FUSED_FP32]
+    members = [make(m) for m in ms]
+    batch = Batch(members)
+    assert batch.fused
+    batch.step(13)
+    for m, g in zip(ms, members):
+        solo = make(m)
+        solo.step(13)
+        same(g, solo)
+    batch.close()
+
+
+def test_fused_batch_interleaves_with_single_steps():
+    from paper_2303_02210_gb300.lbm import Batch
+    members = [make(m) for m in FUSED_FP32[:4]]
+    batch = Batch(members)
+    assert batch.fused
+    batch.step(6)
+    members[0].step(3)
+    members[3].step(1)
+    batch.step(9)
+    solos = [make(m) for m in FUSED_FP32[:4]]
+    for s, n in zip(solos, (18, 15, 15, 16)):
+        s.step(n)
+    for g, s in zip(members, solos):
+        same(g, s)
+    batch.close()
+
+
+def test_mixed_precision_batch_uses_branches():
+    from paper_2303_02210_gb300.lbm import Batch
+    members = [make(m) for m in MEMBERS[2:4]]  # fp32 and fp64
+    batch = Batch(members)
+    assert not batch.fused
+    batch.close()
