@@ -125,6 +125,13 @@ int lbm_validate(const lbm_params_t *params);
 /* Device bytes one simulation needs (for a caller-provided arena); host only. */
 int lbm_footprint(const lbm_params_t *params, uint64_t *bytes);
 
+/* Divisions per step the planner of such a simulation can hold: four times
+ * the initial density's n_s over the whole lattice plus 1024, at most 2^24
+ * (more sets LBM_STATUS_CAPACITY). A batch plans each member with one block
+ * of 512 threads, which suits members with small values (a few thousand);
+ * host only. */
+int lbm_plan_capacity(const lbm_params_t *params, int64_t *ns_max);
+
 /* Creates a simulation and initialises it on `stream` (a cudaStream_t, NULL =
  * legacy default stream): tissue below the initial front with u = 0 and
  * f = f^SS(rho, 0) (App. A, first paragraph), then the occupancy mask, front

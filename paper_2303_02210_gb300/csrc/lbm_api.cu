@@ -273,6 +273,15 @@ int lbm_validate(const lbm_params_t *p)
     return LBM_OK;
 }
 
+int lbm_plan_capacity(const lbm_params_t *p, int64_t *ns_max)
+{
+    if (!ns_max) return LBM_ERR_INVALID_ARG;
+    const int v = lbm_validate(p);
+    if (v != LBM_OK) return v;
+    *ns_max = make_layout(*p).ns_max;
+    return LBM_OK;
+}
+
 int lbm_footprint(const lbm_params_t *p, uint64_t *bytes)
 {
     if (!bytes) return LBM_ERR_INVALID_ARG;
@@ -910,14 +919,20 @@ cudaError_t batch_tables(lbm_batch *b)
     const size_t n = b->sims.size();
     const size_t off_u = align256(n * sizeof(SimDev));
     const size_t off_i = align256(off_u + upd.size() * sizeof(int4));
-    e = cudaMalloc(&b->dev_mem, off_i + inj.size() * sizeof(int4));
+    // stream-ordered on the batch's stream (no device-wide synchronisation:
+    // batches are built while other work runs, as in the serving loop)
+    e = cudaMallocAsync(&b->dev_mem, off_i + inj.size() * sizeof(int4), b->origin);
     if (e != cudaSuccess) return e;
     std::vector<SimDev> ds(n);
     for (size_t i = 0; i < n; ++i) ds[i] = b->sims[i]->d;
     char *base = (char *)b->dev_mem;
-    e = cudaMemcpy(base, ds.data(), n * sizeof(SimDev), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(base + off_u, upd.data(), upd.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(base + off_i, inj.data(), inj.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(base, ds.data(), n * sizeof(SimDev), cudaMemcpyHostToDevice, b->origin);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + off_u, upd.data(), upd.size() * sizeof(int4), cudaMemcpyHostToDevice, b->origin);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + off_i, inj.data(), inj.size() * sizeof(int4), cudaMemcpyHostToDevice, b->origin);
+    // the host arrays go out of scope: wait for the copies from them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->origin);
     b->ds = (const SimDev *)base;
     b->bm_upd = (const int4 *)(base + off_u);
     b->bm_inj = (const int4 *)(base + off_i);
@@ -961,13 +976,16 @@ int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **
     // one-time kernel attributes are set outside the capture
     for (int32_t i = 0; i < n && e == cudaSuccess; ++i)
         if (sims[i]->use_tma) e = sims[i]->kt->tma_prepare(sims[i]->d, sims[i]->tma_variant);
-    for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
-        cudaStream_t st = nullptr;
+    // branch streams and join events for the branch form; the batched form
+    // needs one event (a stream wait takes the event's record at the call)
+    for (int32_t i = 0; i < (b->fused ? 1 : n) && e == cudaSuccess; ++i) {
         cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->join.push_back(ev);
+        if (b->fused || e != cudaSuccess) continue;
+        cudaStream_t st = nullptr;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         if (e == cudaSuccess) b->branch.push_back(st);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) b->join.push_back(ev);
     }
     if (e == cudaSuccess) e = batch_capture(b, 1, &b->exec[0]);
     if (e == cudaSuccess) e = batch_capture(b, kBatchChain, &b->exec[1]);
@@ -987,8 +1005,9 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps)
     CK(cudaEventRecord(b->fork, b->user));
     CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
     for (size_t i = 0; i < b->sims.size(); ++i) {
-        CK(cudaEventRecord(b->join[i], b->sims[i]->stream));
-        CK(cudaStreamWaitEvent(b->origin, b->join[i], 0));
+        cudaEvent_t ev = b->join[b->fused ? 0 : i];
+        CK(cudaEventRecord(ev, b->sims[i]->stream));
+        CK(cudaStreamWaitEvent(b->origin, ev, 0));
     }
     int64_t left = nsteps;
     for (; left >= kBatchChain; left -= kBatchChain) CK(cudaGraphLaunch(b->exec[1], b->origin));
@@ -1019,8 +1038,8 @@ int lbm_batch_destroy(lbm_batch *b)
     for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->dev_mem) cudaFreeAsync(b->dev_mem, b->origin);
     if (b->origin) cudaStreamDestroy(b->origin);
-    if (b->dev_mem) cudaFree(b->dev_mem);
     delete b;
     return LBM_OK;
 }

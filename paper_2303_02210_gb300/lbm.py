@@ -77,6 +77,7 @@ _P = ctypes.c_void_p
 _SIGNATURES = {
     "lbm_validate": (ctypes.c_int, [ctypes.POINTER(lbm_params_t)]),
     "lbm_footprint": (ctypes.c_int, [ctypes.POINTER(lbm_params_t), ctypes.POINTER(ctypes.c_uint64)]),
+    "lbm_plan_capacity": (ctypes.c_int, [ctypes.POINTER(lbm_params_t), ctypes.POINTER(ctypes.c_int64)]),
     "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_params_t), _P, _P, ctypes.c_uint64,
                                   ctypes.POINTER(_P)]),
     "lbm_step": (ctypes.c_int, [_P, ctypes.c_int64]),
@@ -165,6 +166,14 @@ def make_params(d: dict, precision: str = "fp32", update_kernel: str = "auto") -
 def lbm_validate(params: dict, precision: str = "fp32") -> int:
     p = make_params(params, precision)
     return load_library().lbm_validate(ctypes.byref(p))
+
+
+def lbm_plan_capacity(params: dict, precision: str = "fp32") -> int:
+    """Divisions per step the planner of such a simulation holds."""
+    p = make_params(params, precision)
+    out = ctypes.c_int64()
+    _check(load_library().lbm_plan_capacity(ctypes.byref(p), ctypes.byref(out)), "lbm_plan_capacity")
+    return int(out.value)
 
 
 def lbm_footprint(params: dict, precision: str = "fp32") -> int:

@@ -59,6 +59,55 @@ def test_loop_admits_by_footprint_in_arrival_order_and_finishes_all():
     assert s["p50_s"] <= s["p99_s"] and s["requests"] == 5
 
 
+class FakeBatch:
+    """Stands in for Batch: steps its members; members must outlive it."""
+    open_members = set()
+    built = 0
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        assert not FakeBatch.open_members.intersection(id(m) for m in self.sims)
+        FakeBatch.open_members.update(id(m) for m in self.sims)
+        FakeBatch.built += 1
+
+    def step(self, n):
+        for m in self.sims:
+            m.step(n)
+
+    def close(self):
+        FakeBatch.open_members.difference_update(id(m) for m in self.sims)
+
+
+class FakeSimInBatch(FakeSim):
+    def close(self):
+        assert id(self) not in FakeBatch.open_members, "released while its batch was open"
+        super().close()
+
+
+def test_loop_batches_requests_with_a_chunk_to_go():
+    """Requests with at least a chunk of steps left are stepped through one
+    batch per storage type (rebuilt when the membership changes, closed
+    before a member is released); the rest finish alone; every request still
+    runs exactly its steps."""
+    FakeSim.live = FakeSim.peak = 0
+    FakeBatch.open_members, FakeBatch.built = set(), 0
+    specs = [(0.0, 64, 250, "fp32"), (0.0, 64, 100, "fp16"), (0.0, 32, 430, "fp32"), (0.001, 32, 90, "fp32"),
+             (0.002, 64, 300, "fp16"), (0.003, 32, 200, "fp32")]
+    reqs = [serving.Request(params={"width": w, "height": w // 2}, steps=k, arrival=a, precision=pr)
+            for a, w, k, pr in specs]
+    srv = serving.Server(hbm_budget=10_000, chunk=100, clock=FakeClock(), simulation=FakeSimInBatch,
+                         footprint=lambda p, prec: p["width"], new_stream=lambda: None, synchronize=lambda: None,
+                         batch=FakeBatch, capacity=lambda p, prec: 100 * p["width"], batch_max_divisions=5000)
+    srv.run(reqs)
+    assert FakeSim.live == 0 and not FakeBatch.open_members
+    assert FakeBatch.built >= 1 and srv.batches_built == FakeBatch.built
+    # planner capacity 100 W against 5000: the 32-wide requests are batched
+    assert [r.batchable for r in reqs] == [False, False, True, True, False, True]
+    for r in reqs:
+        assert r.result["stats"]["step"] == r.steps
+    assert srv.node_updates == sum(r.steps * r.params["width"] for r in reqs)
+
+
 def test_request_larger_than_the_budget_is_refused():
     r = serving.Request(params={"width": 512, "height": 256}, steps=10)
     srv = serving.Server(hbm_budget=100, simulation=FakeSim, footprint=lambda p, prec: p["width"],
@@ -90,3 +139,25 @@ def test_served_results_equal_requests_run_alone():
         alone.close()
     s = serving.summary(reqs, srv)
     assert s["p50_s"] <= s["p99_s"] and s["aggregate_mlups"] > 0
+
+
+@pytest.mark.gpu
+def test_served_results_equal_requests_run_alone_with_batching():
+    """The same with the small requests stepped through batches (rebuilt as
+    requests come and go): bit for bit what each request gives alone."""
+    from paper_2303_02210_gb300.lbm import Batch, Simulation, lbm_footprint
+    trace = wl.serving_trace(10, rate=500.0, steps=(100, 400), seed=8)
+    trace = [(t, dict(p, width=min(p["width"], 512), height=min(p["width"], 512) // 2,
+                      front_row=float(min(p["width"], 512) // 8)), n, pr) for t, p, n, pr in trace]
+    reqs = [serving.Request(params=p, steps=n, arrival=t, precision=pr, keep_populations=True)
+            for t, p, n, pr in trace]
+    budget = 4 * max(lbm_footprint(r.params, "fp32") for r in reqs)
+    srv = serving.Server(hbm_budget=budget, chunk=32, batch=Batch)
+    srv.run(reqs)
+    assert srv.batches_built > 0 and any(r.batchable for r in reqs)
+    for r in reqs:
+        alone = Simulation(r.params, precision=r.precision)
+        alone.step(r.steps)
+        assert np.array_equal(alone.pops(), r.result["populations"])
+        assert np.array_equal(alone.heights(), r.result["heights"])
+        alone.close()
