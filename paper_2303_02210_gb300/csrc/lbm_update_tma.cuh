@@ -41,7 +41,7 @@ constexpr int TMA_TX = kTmaBoxX;   // 128 columns: two warps of 64
 constexpr int TMA_LX = TMA_TX + 8; // staged columns x0 - 4 .. x0 + 131
 // Divisions of a CTA kept in shared memory (more are read from global memory
 // per tile); tiles flagged per CTA.
-constexpr int TMA_EV_CAP = 512;
+constexpr int TMA_EV_CAP = 128;
 constexpr int TMA_KFLAG_WORDS = 32;
 static_assert(kBucketCap <= TMA_EV_CAP, "a full bucket fits in shared memory");
 // a stalled copy is given up after about two seconds at 2 GHz
@@ -66,19 +66,22 @@ constexpr size_t tma_smem_bytes()
            TMA_KFLAG_WORDS * 4;
 }
 
-// Configurations: variant 0 three CTAs per SM, variant 1 two; tiles of four
-// rows; as many staged boxes per CTA as keep about the same bytes in flight
-// for every storage type.
+// Configurations. Variant 0: tiles of two rows, 128 threads, five CTAs per
+// SM (20 warps, ten tiles in flight per SM); variant 1: tiles of four rows,
+// 256 threads, three CTAs per SM (24 warps, six tiles). Twice the staged
+// boxes per CTA for 16-bit storage (half the bytes each). Variant 0 gave
+// 81.0 against 85.1 us per step on the 4096 x 2048 FP32 workload (the two-row
+// boxes re-read more halo rows from the L2, but more, shorter tiles keep
+// more copies in flight).
 template <typename S>
 struct TmaCfg {
-    static constexpr int TY = 4;
-    static constexpr int STAGES0 = sizeof(S) == 4 ? 2 : 4;
-    static constexpr int STAGES1 = sizeof(S) == 4 ? 3 : 6;
+    static constexpr int TY0 = 2, CTAS0 = 5, STAGES0 = sizeof(S) == 4 ? 2 : 4;
+    static constexpr int TY1 = 4, CTAS1 = 3, STAGES1 = sizeof(S) == 4 ? 2 : 4;
 };
+static_assert(5 * (tma_smem_bytes<float, 2, 2>() + 1024) <= 228 * 1024, "five CTAs per SM by shared memory");
 static_assert(3 * (tma_smem_bytes<float, 4, 2>() + 1024) <= 228 * 1024, "three CTAs per SM by shared memory");
-static_assert(2 * (tma_smem_bytes<float, 4, 3>() + 1024) <= 228 * 1024, "two CTAs per SM by shared memory");
+static_assert(5 * (tma_smem_bytes<__half, 2, 4>() + 1024) <= 228 * 1024, "five CTAs per SM by shared memory");
 static_assert(3 * (tma_smem_bytes<__half, 4, 4>() + 1024) <= 228 * 1024, "three CTAs per SM by shared memory");
-static_assert(2 * (tma_smem_bytes<__half, 4, 6>() + 1024) <= 228 * 1024, "two CTAs per SM by shared memory");
 
 // Two adjacent stored elements as one access.
 template <typename S> struct Pair2;
@@ -534,10 +537,10 @@ cudaError_t prepare_update_tma(const SimDev &d, int variant)
 {
     using C = TmaCfg<S>;
     if (variant == 1)
-        return d.noise_on ? prepare_update_tma_variant<S, C::TY, C::STAGES1, 2, true>()
-                          : prepare_update_tma_variant<S, C::TY, C::STAGES1, 2, false>();
-    return d.noise_on ? prepare_update_tma_variant<S, C::TY, C::STAGES0, 3, true>()
-                      : prepare_update_tma_variant<S, C::TY, C::STAGES0, 3, false>();
+        return d.noise_on ? prepare_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, true>()
+                          : prepare_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, false>();
+    return d.noise_on ? prepare_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, true>()
+                      : prepare_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, false>();
 }
 
 template <typename S, int TY, int STAGES, int CTAS, bool NOISE>
@@ -561,20 +564,19 @@ cudaError_t launch_update_tma_variant(const SimDev &d, const CUtensorMap *maps, 
     return cudaLaunchKernelEx(&cfg, k_update_tma<S, TY, STAGES, CTAS, NOISE>, d, maps[0], maps[1]);
 }
 
-// variant 0: three CTAs per SM; variant 1: two CTAs per SM with more staged
-// boxes each. Both use tiles of 4 rows.
-constexpr int tma_rows(int /*variant*/) { return 4; }
-constexpr int tma_ctas_per_sm(int variant) { return variant == 1 ? 2 : 3; }
+// rows per tile and CTAs per SM of the variants (TmaCfg)
+constexpr int tma_rows(int variant) { return variant == 1 ? 4 : 2; }
+constexpr int tma_ctas_per_sm(int variant) { return variant == 1 ? 3 : 5; }
 
 template <typename S>
 cudaError_t launch_update_tma(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s)
 {
     using C = TmaCfg<S>;
     if (variant == 1)
-        return d.noise_on ? launch_update_tma_variant<S, C::TY, C::STAGES1, 2, true>(d, maps, pdl, s)
-                          : launch_update_tma_variant<S, C::TY, C::STAGES1, 2, false>(d, maps, pdl, s);
-    return d.noise_on ? launch_update_tma_variant<S, C::TY, C::STAGES0, 3, true>(d, maps, pdl, s)
-                      : launch_update_tma_variant<S, C::TY, C::STAGES0, 3, false>(d, maps, pdl, s);
+        return d.noise_on ? launch_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, true>(d, maps, pdl, s)
+                          : launch_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, false>(d, maps, pdl, s);
+    return d.noise_on ? launch_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, true>(d, maps, pdl, s)
+                      : launch_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, false>(d, maps, pdl, s);
 }
 
 } // namespace lbm
