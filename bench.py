@@ -410,26 +410,35 @@ def main():
     value = nodes_all / (ms_max * 1e-3) / 1e6
 
     # ---- end to end through the C ABI with host buffers ----
-    import numpy as np
-    e2e_steps = max(1, min(args.steps, 100))
+    # lbm_create from host parameters, then every step lbm_step(1) and the copy
+    # of that step's front heights and exact Eq. 6 sums into pinned host
+    # buffers (lbm_front_heights_async, no wait per step), one wait at the end,
+    # Eq. 6 worked out on the host for every step, lbm_destroy
+    from paper_2303_02210_gb300.lbm import lbm_eq6
+    e2e_steps = max(1, min(args.steps, 1000))
+    W = params["width"]
+    hbuf = torch.empty((e2e_steps, W), dtype=torch.int32, pin_memory=True)
+    sbuf = torch.empty((e2e_steps, 2), dtype=torch.int64, pin_memory=True)
     barrier()
     torch.cuda.synchronize()
-    h = np.empty(params["width"], dtype=np.int32)
     t0 = time.perf_counter()
     sim2 = Simulation(params, precision=args.precision, update_kernel=args.update_kernel)
-    for _ in range(e2e_steps):
+    for k in range(e2e_steps):
         sim2.step(1)
-        h, hbar, w = sim2.front_heights()
+        sim2.lbm_front_heights_async(hbuf[k], sbuf[k])
+    sim2.sync()
+    eq6 = [lbm_eq6(a, b, W) for a, b in sbuf.tolist()]
     st2 = sim2.stats()
     sim2.close()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    assert len(eq6) == e2e_steps and int(hbuf[-1].max()) > 0
     e2e_max, e2e_nodes = reduce_over_ranks(e2e_s, st2["node_updates"], dist, "cuda")
     e2e_value = e2e_nodes / e2e_max / 1e6
     # bytes that cross the bus: the initial front profile (W int32) once at
-    # creation; W int32 heights plus hbar and w (two doubles) every step
-    h2d = params["width"] * 4 / e2e_steps
-    d2h = params["width"] * 4 + 16
+    # creation; W int32 heights and the two int64 Eq. 6 sums every step
+    h2d = W * 4 / e2e_steps
+    d2h = W * 4 + 16
 
     if rank != 0:
         if dist is not None:
@@ -456,7 +465,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "what": (f"lbm_create from host parameters, then {e2e_steps} x (lbm_step(1) + "
-                         f"lbm_front_heights into a host buffer), lbm_destroy")},
+                         f"lbm_front_heights_async of that step's heights and Eq. 6 sums into pinned host "
+                         f"buffers), one wait, Eq. 6 on the host for every step, lbm_destroy")},
         "gpu_launches": int(launches),
         "clocks": clk,
         "status": status,

@@ -153,6 +153,18 @@ int lbm_step(lbm_sim *sim, int64_t nsteps);
  * w of Eq. 6 (either pointer may be NULL). Syncs. */
 int lbm_front_heights(lbm_sim *sim, int32_t *h_host, double *hbar, double *w);
 
+/* The same without waiting: enqueues on the simulation's stream the copies of
+ * h(x) into h_host (W int32; NULL skips it) and of the exact Eq. 6 sums
+ * S1 = sum h, S2 = sum h^2 into sums_host[0..1]. Host buffers should be
+ * pinned (cudaHostAlloc) for the copies to be asynchronous; they hold the
+ * values once the stream has reached this point (lbm_sync). Eq. 6 from the
+ * sums: lbm_eq6. Enqueues only. */
+int lbm_front_heights_async(lbm_sim *sim, int32_t *h_host, int64_t *sums_host);
+
+/* Eq. 6 from the exact sums: hbar = S1 / W, w = sqrt(W S2 - S1^2) / W (IEEE
+ * double, as the kernels' FP64 wall rule). Host only. */
+int lbm_eq6(int64_t s1, int64_t s2, int32_t width, double *hbar, double *w);
+
 /* Density rho = sum_i f_i and velocity u = sum_i f_i e_i / rho (Eq. 1; u = 0
  * where rho = 0) of the current populations into caller host arrays of W*H
  * doubles, row-major [y][x]. Syncs. */

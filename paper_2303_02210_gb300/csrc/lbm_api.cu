@@ -611,6 +611,23 @@ int lbm_front_heights(lbm_sim *s, int32_t *h_host, double *hbar, double *w)
     return LBM_OK;
 }
 
+int lbm_front_heights_async(lbm_sim *s, int32_t *h_host, int64_t *sums_host)
+{
+    if (!s || !sums_host) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    if (h_host)
+        CK(cudaMemcpyAsync(h_host, s->d.heights, sizeof(int32_t) * s->p.width, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(sums_host, &s->d.sc->S1, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
+    return LBM_OK;
+}
+
+int lbm_eq6(int64_t s1, int64_t s2, int32_t width, double *hbar, double *w)
+{
+    if (width < 1 || !hbar || !w) return LBM_ERR_INVALID_ARG;
+    eq6((long long)s1, (long long)s2, width, hbar, w);
+    return LBM_OK;
+}
+
 int lbm_fields_device(lbm_sim *s, double *rho, double *ux, double *uy)
 {
     if (!s || !rho || !ux || !uy) return LBM_ERR_INVALID_ARG;

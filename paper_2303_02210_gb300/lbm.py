@@ -78,6 +78,9 @@ _SIGNATURES = {
     "lbm_validate": (ctypes.c_int, [ctypes.POINTER(lbm_params_t)]),
     "lbm_footprint": (ctypes.c_int, [ctypes.POINTER(lbm_params_t), ctypes.POINTER(ctypes.c_uint64)]),
     "lbm_plan_capacity": (ctypes.c_int, [ctypes.POINTER(lbm_params_t), ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_front_heights_async": (ctypes.c_int, [_P, _P, _P]),
+    "lbm_eq6": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]),
     "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_params_t), _P, _P, ctypes.c_uint64,
                                   ctypes.POINTER(_P)]),
     "lbm_step": (ctypes.c_int, [_P, ctypes.c_int64]),
@@ -183,6 +186,13 @@ def lbm_footprint(params: dict, precision: str = "fp32") -> int:
     return int(out.value)
 
 
+def lbm_eq6(s1: int, s2: int, width: int):
+    """Eq. 6 (hbar, w) from the exact sums of the front heights."""
+    hbar, w = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().lbm_eq6(int(s1), int(s2), int(width), ctypes.byref(hbar), ctypes.byref(w)), "lbm_eq6")
+    return hbar.value, w.value
+
+
 def lbm_front_heights_noalloc(mask_dev, width: int, height: int, heights_dev, stats_dev, stream=None):
     """Allocation-free front heights and width of a device occupancy bitmask
     (``include/lbm.h``). ``mask_dev`` (uint32, H x ceil(W/32)), ``heights_dev``
@@ -247,6 +257,14 @@ class Simulation:
         _check(self._lib.lbm_step(self._h, int(n)), "lbm_step")
 
     step = lbm_step
+
+    def lbm_front_heights_async(self, h_pinned, sums_pinned):
+        """Enqueues the copies of h(x) and of the Eq. 6 sums (S1, S2) into
+        caller-owned pinned torch CPU tensors (int32 W, int64 2); valid after
+        ``sync()``. ``h_pinned`` may be None."""
+        _check(self._lib.lbm_front_heights_async(
+            self._h, None if h_pinned is None else ctypes.c_void_p(h_pinned.data_ptr()),
+            ctypes.c_void_p(sums_pinned.data_ptr())), "lbm_front_heights_async")
 
     def lbm_front_heights(self):
         h = np.empty(self.W, dtype=np.int32)

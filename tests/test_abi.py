@@ -3,6 +3,8 @@ and its host-only logic (parameter checks, footprint, error strings) works
 without a GPU. No compute call is made here."""
 import ctypes
 
+import numpy as np
+
 import pytest
 
 from paper_2303_02210_gb300 import lbm
@@ -87,3 +89,27 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     rc = lib.lbm_create(ctypes.byref(p), None, None, 0, ctypes.byref(h))
     assert rc in (-3, -5) and not h.value
+
+
+def test_eq6_host_helper_matches_mean_and_population_std(lib):
+    rng = np.random.default_rng(5)
+    for W in (1, 7, 4096):
+        h = rng.integers(0, 3000, W).astype(np.int64)
+        hbar, w = lbm.lbm_eq6(int(h.sum()), int((h * h).sum()), W)
+        assert hbar == h.sum() / W
+        assert abs(w - h.std()) <= 1e-12 * max(1.0, h.std())
+    assert lib.lbm_eq6(1, 1, 0, None, None) == -1
+
+
+def test_plan_capacity_grows_with_growth_rate_and_lattice():
+    a = lbm.lbm_plan_capacity(wl.lattice_small())
+    b = lbm.lbm_plan_capacity(wl.lattice_small(growth_rate=1e-3))
+    c = lbm.lbm_plan_capacity(wl.lattice_edge())
+    assert 1024 <= a < b < c
+    # no growth: the floor of 1024
+    assert lbm.lbm_plan_capacity(wl.lattice_small(growth_mode="none")) == 1024
+
+
+def test_async_calls_reject_null(lib):
+    assert lib.lbm_front_heights_async(None, None, None) == -1
+    assert lib.lbm_batch_fused(None) == -1
