@@ -235,6 +235,15 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
     }
     if (d.inject_in_update)
         for (int i = blk * PLAN_NT + tid; i < d.upd_ctas; i += G * PLAN_NT) d.bucket_cnt[i] = 0;
+    // the previous selection's table entries emptied (before this selection
+    // inserts, two grid barriers on)
+    {
+        const int nprev = sc->rec_n;
+        for (int r = blk * PLAN_NT + tid; r < nprev; r += G * PLAN_NT) {
+            const int slot = __ldcg(&d.hlist[r]);
+            if (slot >= 0) d.htab[slot] = EMPTY_ENTRY;
+        }
+    }
     // n_s if no row is frozen now (almost always): the last block, which has
     // the least front to scan, works it out in FP64 while the others scan
     if (grow && blk == G - 1 && tid == 0) {
@@ -527,14 +536,9 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             sc->acc_ratio = (double)((float)s_kstop / (float)ns); // a work estimate only
         }
     }
-    plan_grid_sync(sc, &s_dead, G);
-
-    // ---- E: the table emptied for the next selection
+    // (no barrier: the commit below reads nothing another block writes after
+    // the last one, and the table is emptied by the next launch)
     const int nsel = (int)(acc < ns ? acc : ns); // selected divisions (draw ranks)
-    for (int r = blk * PLAN_NT + tid; r < nsel; r += G * PLAN_NT) {
-        const int slot = __ldcg(&d.hlist[r]);
-        if (slot >= 0) d.htab[slot] = EMPTY_ENTRY;
-    }
 
     // ---- block 0: commit the step that ran, the observables, the new selection
     if (blk == 0 && tid == 0) {
