@@ -429,7 +429,11 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     }
     s->use_tma = false;
     s->tma_grid = nsm;
-    s->tma_variant = p->update_kernel == 3 ? 1 : 0;
+    // TMA-staged variant: "tma" 0, "tma1" 1; by the lattice width when the
+    // kernel is chosen (two-row tiles up to 4096 columns, four-row tiles
+    // beyond: measured 81 against 85 us per step at 4096 x 2048 FP32, and
+    // 126 against 132 us per update at 8192 x 2048 the other way round)
+    s->tma_variant = p->update_kernel == 3 ? 1 : (p->update_kernel == 0 && p->width > 4096 ? 1 : 0);
     const bool tma_inject = p->update_kernel != 4; // 4: the selector injects into global memory
     if (s->kt->tma_update && !p->y_periodic && p->update_kernel != 1) {
         const int ty = launch_update_tma_rows(s->tma_variant);
