@@ -107,6 +107,44 @@ def test_fp64_bit_exact_1000_steps_lattice_small():
         assert_bit_exact(g, o)
 
 
+MAX_CASES = {
+    # the widest lattice the packed division key holds (x < 2^15), edge growth
+    "max_width_32768": wl.lattice_small(seed=51, width=32768, height=40, front_row=12.0, growth_rate=3e-3,
+                                        growth_mode="edge", edge_depth=4, front_kind="sinusoidal",
+                                        front_amp=2.0, front_kmax=64, wall_mode="fixed"),
+    # the front near the top of the tallest lattice (y < 2^15), advancing wall
+    "max_height_32768": wl.lattice_small(seed=52, width=40, height=32768, front_row=32740.0,
+                                         growth_rate=3e-3, wall_min_gap=8.0, wall_w_factor=2.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MAX_CASES))
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_maximum_extents(name, precision):
+    """The largest width and height the division key packs (32768), a few
+    steps: FP64 bit-exact with the oracle; FP32 (the TMA-staged kernel)
+    bit-exact with the plain-load FP32 kernel and within tolerance."""
+    p = MAX_CASES[name]
+    o = OracleSim(p)
+    o.step(6)
+    if precision == "fp64":
+        g = gpu_sim(p, "fp64")
+        g.step(6)
+        assert_bit_exact(g, o)
+        return
+    from paper_2303_02210_gb300.lbm import Simulation
+    a = Simulation(p, precision="fp32", update_kernel="plain")
+    b = Simulation(p, precision="fp32")
+    a.step(6)
+    b.step(6)
+    assert b.stats()["update_kernel"] == 2
+    assert np.array_equal(a.pops(), b.pops())
+    e_rho, e_u = field_errors(b, o)
+    assert e_rho <= RTOL_FP32 and e_u <= RTOL_FP32
+    assert np.array_equal(b.mask(), o.mask())
+    assert b.stats()["ns_total"] == o.stats()["ns_total"]
+
+
 def test_fp64_set_populations_matches_oracle():
     """A caller-supplied state (a shear wave on a periodic lattice) evolves
     identically through lbm_set_populations."""
