@@ -77,9 +77,14 @@ enum { LBM_FP32 = 0, LBM_FP64 = 1, LBM_FP16 = 2, LBM_BF16 = 3 };
  *               and for f_i = c_i), FP32 arithmetic, 36 bytes per node
  *               update
  *  update_kernel 0: choose (the TMA-staged kernel for FP32 and 16-bit
- *               storage with walls in y, else the plain-load kernel);
- *               1: plain-load kernel; 2: TMA-staged kernel (not FP64, and
- *               y_periodic = 0 only)
+ *               storage with walls in y, else the plain-load kernel; its
+ *               two-row form up to 4096 columns, the four-row form beyond);
+ *               1: plain-load kernel; 2: TMA-staged kernel, two-row form;
+ *               3: TMA-staged kernel, four-row form (2-4: not FP64, and
+ *               y_periodic = 0 only); 4: the two-row form with the
+ *               divisions injected into global memory first; 5: choose for
+ *               a simulation that shares the GPU with others (the four-row
+ *               form where the TMA-staged kernel applies)
  */
 typedef struct {
     double tau, mu, rho_c, rho_cell, sigma, rho0, growth_rate;

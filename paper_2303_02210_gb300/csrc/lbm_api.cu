@@ -268,8 +268,9 @@ int lbm_validate(const lbm_params_t *p)
     if (p->negfix_mode != LBM_NEGFIX_LITERAL && p->negfix_mode != LBM_NEGFIX_RESCALE) return LBM_ERR_INVALID_ARG;
     if (p->precision < LBM_FP32 || p->precision > LBM_BF16) return LBM_ERR_INVALID_ARG;
     if (p->y_periodic != 0 && p->y_periodic != 1) return LBM_ERR_INVALID_ARG;
-    if (p->update_kernel < 0 || p->update_kernel > 4) return LBM_ERR_INVALID_ARG;
-    if (p->update_kernel >= 2 && (p->precision == LBM_FP64 || p->y_periodic)) return LBM_ERR_INVALID_ARG;
+    if (p->update_kernel < 0 || p->update_kernel > 5) return LBM_ERR_INVALID_ARG;
+    if (p->update_kernel >= 2 && p->update_kernel <= 4 && (p->precision == LBM_FP64 || p->y_periodic))
+        return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
 
@@ -432,8 +433,12 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     // TMA-staged variant: "tma" 0, "tma1" 1; by the lattice width when the
     // kernel is chosen (two-row tiles up to 4096 columns, four-row tiles
     // beyond: measured 81 against 85 us per step at 4096 x 2048 FP32, and
-    // 126 against 132 us per update at 8192 x 2048 the other way round)
-    s->tma_variant = p->update_kernel == 3 ? 1 : (p->update_kernel == 0 && p->width > 4096 ? 1 : 0);
+    // 126 against 132 us per update at 8192 x 2048 the other way round); the
+    // four-row form for a simulation that shares the GPU (5: 15.1 against
+    // 12.5 G node updates/s aggregate for a hundred concurrent requests)
+    s->tma_variant = (p->update_kernel == 3 || p->update_kernel == 5 || (p->update_kernel == 0 && p->width > 4096))
+                         ? 1
+                         : 0;
     const bool tma_inject = p->update_kernel != 4; // 4: the selector injects into global memory
     if (s->kt->tma_update && !p->y_periodic && p->update_kernel != 1) {
         const int ty = launch_update_tma_rows(s->tma_variant);
@@ -457,7 +462,7 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
             s->use_tma = false;
             d.inject_in_update = 0;
         }
-        if (!ok && p->update_kernel >= 2) {
+        if (!ok && p->update_kernel >= 2 && p->update_kernel <= 4) {
             if (s->own_arena) cudaFree(s->arena);
             delete s;
             return LBM_ERR_CUDA;

@@ -32,7 +32,7 @@ STATUS_FRONT_AT_TOP = 1
 STATUS_GROWTH_STARVED = 2
 STATUS_CAPACITY = 4
 STATUS_TIMEOUT = 8
-UPDATE_KERNELS = {"auto": 0, "plain": 1, "tma": 2, "tma1": 3, "tma_sel": 4}
+UPDATE_KERNELS = {"auto": 0, "plain": 1, "tma": 2, "tma1": 3, "tma_sel": 4, "shared": 5}
 
 
 class LbmError(RuntimeError):

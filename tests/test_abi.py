@@ -113,3 +113,13 @@ def test_plan_capacity_grows_with_growth_rate_and_lattice():
 def test_async_calls_reject_null(lib):
     assert lib.lbm_front_heights_async(None, None, None) == -1
     assert lib.lbm_batch_fused(None) == -1
+
+
+def test_update_kernel_choices_validate():
+    p = wl.lattice_small()
+    assert lbm.lbm_validate(p, "fp32") == 0
+    for uk, ok64 in (("auto", True), ("plain", True), ("tma", False), ("tma1", False), ("shared", True)):
+        q = lbm.make_params(p, "fp64", uk)
+        assert (lbm.load_library().lbm_validate(ctypes.byref(q)) == 0) == ok64, uk
+    q = lbm.make_params(p, "fp32", 6)
+    assert lbm.load_library().lbm_validate(ctypes.byref(q)) == -1
