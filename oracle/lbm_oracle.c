@@ -15,9 +15,15 @@
  * Everything is IEEE double; build with -ffp-contract=off so that no
  * multiply-add is fused and every operation rounds exactly where it is written.
  *
- * Lattice: D2Q9 (the paper uses D2Q7, Sec. II; the D2Q9 analogue of Eq. 3 has
- * coefficients 3, 9/2, 3/2 and weights 4/9, 1/9, 1/36). Directions:
+ * Lattice: D2Q9 by default (the D2Q9 analogue of Eq. 3 has coefficients 3,
+ * 9/2, 3/2 and weights 4/9, 1/9, 1/36). Directions:
  *   0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)
+ * or the paper's triangular D2Q7 (Sec. II): rows of nodes along x, the odd
+ * rows shifted by half a spacing, rows sqrt(3)/2 apart; directions 0 rest and
+ * q = 1..6 at angles (q - 1) pi / 3, i.e. 1:(1,0) 2:(1/2,s) 3:(-1/2,s)
+ * 4:(-1,0) 5:(-1/2,-s) 6:(1/2,-s), s = sqrt(3)/2; Eq. 3 with 4, 8, 2
+ * (c_s^2 = 1/4) and weights 1/2, 1/12. The neighbour of (x, y) along 2 is
+ * (x + (y & 1), y + 1), along 3 (x - 1 + (y & 1), y + 1).
  * x is periodic (width W), y is the growth direction (height H). Node id
  * n = y*W + x. Population layout f[q][y][x], q-major.
  *
@@ -51,19 +57,42 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define NQ 9
+#define NQ 9 /* the most directions of a lattice */
 
-/* D2Q9 lattice vectors, opposite directions and weights. */
-static const int EX[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-static const int EY[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-static const int OPP[NQ] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-static const double WQ[NQ] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
-                              1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
-                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
-/* The four opposite pairs a division may load (Sec. II: "two opposite lattice
- * vectors"). Pair p touches directions PAIR_A[p] and PAIR_B[p]. */
-static const int PAIR_A[4] = {1, 2, 5, 6};
-static const int PAIR_B[4] = {3, 4, 7, 8};
+/* A lattice: q directions with vectors (ex, ey), opposites, weights, the
+ * Eq. 3 coefficients f^SS_i = w_i rho (1 + c1 e.u + c2 (e.u)^2 - c3 u.u),
+ * the opposite pairs a division may load (Sec. II: "two opposite lattice
+ * vectors"; pair p touches pa[p] and pb[p]) and the bits of each Eq. 4
+ * uniform (q fields of a 128-bit Philox block). */
+typedef struct {
+    int q, npairs, fbits;
+    double ex[NQ], ey[NQ], w[NQ], c1, c2, c3;
+    int opp[NQ], pa[4], pb[4];
+} lattice;
+
+#define HALF_SQRT3 0.8660254037844386 /* sqrt(3)/2, rounded to double */
+
+static const lattice D2Q9 = {
+    9, 4, 14,
+    {0.0, 1.0, 0.0, -1.0, 0.0, 1.0, -1.0, -1.0, 1.0},
+    {0.0, 0.0, 1.0, 0.0, -1.0, 1.0, 1.0, -1.0, -1.0},
+    {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0},
+    3.0, 4.5, 1.5,
+    {0, 3, 4, 1, 2, 7, 8, 5, 6},
+    {1, 2, 5, 6},
+    {3, 4, 7, 8}};
+
+static const lattice D2Q7 = {
+    7, 3, 18,
+    {0.0, 1.0, 0.5, -0.5, -1.0, -0.5, 0.5},
+    {0.0, 0.0, HALF_SQRT3, HALF_SQRT3, 0.0, -HALF_SQRT3, -HALF_SQRT3},
+    {0.5, 1.0 / 12.0, 1.0 / 12.0, 1.0 / 12.0, 1.0 / 12.0, 1.0 / 12.0, 1.0 / 12.0},
+    4.0, 8.0, 2.0,
+    {0, 4, 5, 6, 1, 2, 3},
+    {1, 2, 3},
+    {4, 5, 6}};
+
+enum { LATTICE_D2Q9 = 0, LATTICE_D2Q7 = 1 };
 
 enum { GROW_NONE = 0, GROW_BULK = 1, GROW_DENSITY = 2, GROW_EDGE = 3, GROW_BAND = 4 };
 enum { FRONT_FLAT = 0, FRONT_SINUSOIDAL = 1, FRONT_FULL = 2 };
@@ -83,6 +112,7 @@ typedef struct {
     int32_t width, height, growth_mode, edge_depth, band_rows, front_kind;
     int32_t front_kmin, front_kmax, wall_mode, negfix_mode, y_periodic;
     uint32_t sim_id;
+    int32_t lattice; /* LATTICE_D2Q9 or LATTICE_D2Q7 */
 } orc_params;
 
 typedef struct {
@@ -94,6 +124,7 @@ typedef struct {
 
 typedef struct {
     orc_params p;
+    const lattice *L;
     int W, H;
     size_t N;
     double *f, *fs, *fn; /* current, streamed (f*), next */
@@ -150,11 +181,46 @@ static double u01(uint32_t v) { return ((double)v + 0.5) * 2.3283064365386963e-1
 /* Node mass in the exact fixed-point unit 2^-24 (order-independent sums). */
 static int64_t fix24(double r) { return llrint(r * 16777216.0); }
 
-static double node_sum(const double *f, size_t N, size_t n)
+static double node_sum(const orc_sim *s, const double *f, size_t n)
 {
     double r = f[n];
-    for (int i = 1; i < NQ; ++i) r = r + f[(size_t)i * N + n];
+    for (int i = 1; i < s->L->q; ++i) r = r + f[(size_t)i * s->N + n];
     return r;
+}
+
+/* The node the population of direction i at (x, y) streams from (App. A
+ * step 1: f*_i(x, y) = f_i(x - e_i, y - e_i) on D2Q9; on the triangular D2Q7,
+ * the x offset of a step between rows depends on the row's parity), before
+ * any wrap or wall. */
+static void stream_source(const orc_sim *s, int i, int x, int y, int *xs, int *ys)
+{
+    if (s->p.lattice != LATTICE_D2Q7) {
+        *xs = x - (int)s->L->ex[i];
+        *ys = y - (int)s->L->ey[i];
+        return;
+    }
+    const int par = y & 1;
+    switch (i) {
+    case 1: *xs = x - 1; *ys = y; break;
+    case 2: *xs = x - 1 + par; *ys = y - 1; break; /* from the lower-left neighbour */
+    case 3: *xs = x + par; *ys = y - 1; break;     /* from the lower-right neighbour */
+    case 4: *xs = x + 1; *ys = y; break;
+    case 5: *xs = x + par; *ys = y + 1; break;     /* from the upper-right neighbour */
+    case 6: *xs = x - 1 + par; *ys = y + 1; break; /* from the upper-left neighbour */
+    default: *xs = x; *ys = y; break;
+    }
+}
+
+/* Momentum j = sum_i f_i e_i (Eq. 1), in a fixed order of operations. */
+static void momentum(const orc_sim *s, const double *fs, double *jx, double *jy)
+{
+    if (s->p.lattice == LATTICE_D2Q7) {
+        *jx = ((((fs[1] - fs[4]) + 0.5 * fs[2]) - 0.5 * fs[3]) - 0.5 * fs[5]) + 0.5 * fs[6];
+        *jy = (((fs[2] + fs[3]) - fs[5]) - fs[6]) * HALF_SQRT3;
+    } else {
+        *jx = ((((fs[1] - fs[3]) + fs[5]) - fs[6]) - fs[7]) + fs[8];
+        *jy = ((((fs[2] - fs[4]) + fs[5]) + fs[6]) - fs[7]) - fs[8];
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -191,7 +257,7 @@ static int64_t rows_mass_fix(const orc_sim *s, int y0, int y1)
 {
     int64_t m = 0;
     for (int y = y0; y < y1; ++y)
-        for (int x = 0; x < s->W; ++x) m += fix24(node_sum(s->f, s->N, (size_t)y * s->W + x));
+        for (int x = 0; x < s->W; ++x) m += fix24(node_sum(s, s->f, (size_t)y * s->W + x));
     return m;
 }
 
@@ -217,7 +283,7 @@ static void after_update(orc_sim *s)
     s->st.quiescent_mass = (double)s->st.quiescent_fix * 5.9604644775390625e-08;
     /* any mass in the top row: the front has reached the top wall */
     for (int x = 0; x < W; ++x)
-        if (node_sum(s->f, s->N, (size_t)(H - 1) * W + x) != 0.0) {
+        if (node_sum(s, s->f, (size_t)(H - 1) * W + x) != 0.0) {
             s->st.status |= ORC_STATUS_FRONT_AT_TOP;
             break;
         }
@@ -228,7 +294,7 @@ static void mask_from_state(orc_sim *s, int y0)
     for (int y = y0; y < s->H; ++y)
         for (int x = 0; x < s->W; ++x) {
             size_t n = (size_t)y * s->W + x;
-            s->mask[n] = node_sum(s->f, s->N, n) >= s->p.rho_c;
+            s->mask[n] = node_sum(s, s->f, n) >= s->p.rho_c;
         }
 }
 
@@ -289,7 +355,7 @@ static void init_state(orc_sim *s)
                     rho = s->p.rho_init * (1.0 + s->p.rho_jitter * (2.0 * u01(r[0]) - 1.0));
                 }
             }
-            for (int i = 0; i < NQ; ++i) s->f[(size_t)i * N + n] = WQ[i] * rho;
+            for (int i = 0; i < s->L->q; ++i) s->f[(size_t)i * N + n] = s->L->w[i] * rho;
         }
     free(rows);
     mask_from_state(s, 0);
@@ -314,18 +380,21 @@ static void one_step(orc_sim *s)
     const double rho_c = s->p.rho_c;
 
     /* ---- step 1: streaming into f* (rows of the active portion) ---- */
+    const lattice *L = s->L;
+    const int Q = L->q;
     for (int y = yr; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             size_t n = (size_t)y * W + x;
-            for (int i = 0; i < NQ; ++i) {
-                int xs = (x - EX[i] + W) % W;
-                int ys = y - EY[i];
+            for (int i = 0; i < Q; ++i) {
+                int xs, ys;
+                stream_source(s, i, x, y, &xs, &ys);
+                xs = (xs + W) % W;
                 double v;
                 if (s->p.y_periodic) {
                     ys = (ys + H) % H;
                     v = s->f[(size_t)i * N + (size_t)ys * W + xs];
                 } else if (ys < yr || ys >= H) {
-                    v = s->f[(size_t)OPP[i] * N + n]; /* half-way bounce-back */
+                    v = s->f[(size_t)L->opp[i] * N + n]; /* half-way bounce-back */
                 } else {
                     v = s->f[(size_t)i * N + (size_t)ys * W + xs];
                 }
@@ -365,8 +434,9 @@ static void one_step(orc_sim *s)
                 int64_t idx = (int64_t)(((uint64_t)r[0] * (uint64_t)nwin) >> 32);
                 int64_t node = (int64_t)y_lo * W + idx;
                 int y = (int)(node / W), x = (int)(node % W);
-                int pair = (int)(r[1] >> 30);
-                double rs = node_sum(s->fs, N, (size_t)node); /* rho* */
+                /* a pair uniform over the lattice's opposite pairs */
+                int pair = L->npairs == 4 ? (int)(r[1] >> 30) : (int)(((uint64_t)r[1] * (uint64_t)L->npairs) >> 32);
+                double rs = node_sum(s, s->fs, (size_t)node); /* rho* */
                 int ok = 0;
                 switch (s->p.growth_mode) {
                 case GROW_BULK: ok = rs >= rho_c; break;
@@ -406,8 +476,8 @@ static void one_step(orc_sim *s)
             int pair = (int)(key[a] % 4);
             int32_t cnt = (int32_t)(b - a);
             double add = (double)cnt * half;
-            s->fs[(size_t)PAIR_A[pair] * N + (size_t)node] += add;
-            s->fs[(size_t)PAIR_B[pair] * N + (size_t)node] += add;
+            s->fs[(size_t)L->pa[pair] * N + (size_t)node] += add;
+            s->fs[(size_t)L->pb[pair] * N + (size_t)node] += add;
             s->ev_node[s->ev_n] = node;
             s->ev_pair[s->ev_n] = pair;
             s->ev_count[s->ev_n] = cnt;
@@ -432,88 +502,89 @@ static void one_step(orc_sim *s)
         for (int x = 0; x < W; ++x) {
             size_t n = (size_t)y * W + x;
             double fs[NQ], fo[NQ];
-            for (int i = 0; i < NQ; ++i) fs[i] = s->fs[(size_t)i * N + n];
+            for (int i = 0; i < Q; ++i) fs[i] = s->fs[(size_t)i * N + n];
             /* step 4: moments of f* after proliferation (Eq. 1) */
             double rho = fs[0];
-            for (int i = 1; i < NQ; ++i) rho = rho + fs[i];
+            for (int i = 1; i < Q; ++i) rho = rho + fs[i];
             int occ = rho >= rho_c;
             s->mask[n] = (uint8_t)occ;
             if (!occ) {
                 /* step 5, rho < rho_c: reverse directions (two-step bounce-back) */
-                for (int i = 0; i < NQ; ++i) fo[i] = fs[OPP[i]];
+                for (int i = 0; i < Q; ++i) fo[i] = fs[L->opp[i]];
             } else {
-                double jx = ((((fs[1] - fs[3]) + fs[5]) - fs[6]) - fs[7]) + fs[8];
-                double jy = ((((fs[2] - fs[4]) + fs[5]) + fs[6]) - fs[7]) - fs[8];
+                double jx, jy;
+                momentum(s, fs, &jx, &jy);
                 double ux = jx / rho, uy = jy / rho;
                 double usx = cmu * ux, usy = cmu * uy; /* u* = (1 - mu) u */
                 double uu = usx * usx + usy * usy;
                 /* step 5, rho >= rho_c: BGK relaxation towards f^SS (Eqs. 2-3) */
-                for (int i = 0; i < NQ; ++i) {
-                    double eu = (double)EX[i] * usx + (double)EY[i] * usy;
-                    double t1 = 1.0 + 3.0 * eu;
-                    t1 = t1 + 4.5 * (eu * eu);
-                    t1 = t1 - 1.5 * uu;
-                    double fss = (WQ[i] * rho) * t1;
+                for (int i = 0; i < Q; ++i) {
+                    double eu = L->ex[i] * usx + L->ey[i] * usy;
+                    double t1 = 1.0 + L->c1 * eu;
+                    t1 = t1 + L->c2 * (eu * eu);
+                    t1 = t1 - L->c3 * uu;
+                    double fss = (L->w[i] * rho) * t1;
                     fo[i] = fs[i] - omega * (fs[i] - fss);
                 }
-                /* step 6: mass-conserving noise (Eq. 4). Nine uniforms u_i on (0,1)
-                 * with 14 random bits each, from one Philox block: its four words
-                 * read as the 128-bit integer w0 + 2^32 w1 + 2^64 w2 + 2^96 w3,
-                 * whose bits 14 i .. 14 i + 13 are m_i (bits 126, 127 unused);
-                 * u_i = (m_i + 1/2) 2^-14. eta~_i = sigma (2 u_i - 1), so
-                 * eta_i = eta~_i - mean(eta~) = 2 sigma (u_i - mean(u)). */
+                /* step 6: mass-conserving noise (Eq. 4). Q uniforms u_i on (0,1)
+                 * with b random bits each (D2Q9: 9 of 14 bits, D2Q7: 7 of 18),
+                 * from one Philox block: its four words read as the 128-bit
+                 * integer w0 + 2^32 w1 + 2^64 w2 + 2^96 w3, whose bits b i ..
+                 * b i + b - 1 are m_i; u_i = (m_i + 1/2) 2^-b.
+                 * eta~_i = sigma (2 u_i - 1), so eta_i = eta~_i - mean(eta~)
+                 * = 2 sigma (u_i - mean(u)). */
                 if (s->p.sigma != 0.0) {
                     uint32_t w[4];
                     draw(s, (uint32_t)n, t, STREAM_NOISE, w);
                     uint32_t m[NQ];
-                    for (int i = 0; i < NQ; ++i) {
-                        const int bit = 14 * i, j = bit / 32, o = bit % 32;
+                    for (int i = 0; i < Q; ++i) {
+                        const int bit = L->fbits * i, j = bit / 32, o = bit % 32;
                         uint64_t two = (uint64_t)w[j];
                         if (j + 1 < 4) two |= (uint64_t)w[j + 1] << 32;
-                        m[i] = (uint32_t)(two >> o) & 0x3FFFu;
+                        m[i] = (uint32_t)(two >> o) & ((1u << L->fbits) - 1u);
                     }
                     double u[NQ];
-                    for (int i = 0; i < NQ; ++i) u[i] = ((double)m[i] + 0.5) * 6.103515625e-05;
+                    for (int i = 0; i < Q; ++i) u[i] = ((double)m[i] + 0.5) * ldexp(1.0, -L->fbits);
                     double S = u[0];
-                    for (int i = 1; i < NQ; ++i) S = S + u[i];
-                    const double ubar = S / 9.0;
-                    for (int i = 0; i < NQ; ++i) fo[i] = fo[i] + two_sigma * (u[i] - ubar);
+                    for (int i = 1; i < Q; ++i) S = S + u[i];
+                    const double ubar = S / (double)Q;
+                    for (int i = 0; i < Q; ++i) fo[i] = fo[i] + two_sigma * (u[i] - ubar);
                 }
                 /* step 7: correct negative populations */
                 if (s->p.negfix_mode == NEGFIX_LITERAL) {
                     if (fo[0] < 0.0) {
                         double r0 = fo[0];
-                        for (int i = 1; i < NQ; ++i) r0 = r0 + fo[i];
+                        for (int i = 1; i < Q; ++i) r0 = r0 + fo[i];
                         fo[0] = 0.0;
                         double sm = fo[0];
-                        for (int i = 1; i < NQ; ++i) sm = sm + fo[i];
-                        for (int i = 0; i < NQ; ++i) fo[i] = (r0 * fo[i]) / sm;
+                        for (int i = 1; i < Q; ++i) sm = sm + fo[i];
+                        for (int i = 0; i < Q; ++i) fo[i] = (r0 * fo[i]) / sm;
                     }
-                    for (int i = 1; i < NQ; ++i)
+                    for (int i = 1; i < Q; ++i)
                         if (fo[i] < 0.0) {
                             double a = -fo[i];
-                            fo[OPP[i]] = fo[OPP[i]] + a;
+                            fo[L->opp[i]] = fo[L->opp[i]] + a;
                             fo[i] = 0.0;
                             s->st.clip_mass += 2.0 * a;
                         }
                 } else {
                     int neg = 0;
-                    for (int i = 0; i < NQ; ++i) neg |= fo[i] < 0.0;
+                    for (int i = 0; i < Q; ++i) neg |= fo[i] < 0.0;
                     if (neg) {
                         double r0 = fo[0];
-                        for (int i = 1; i < NQ; ++i) r0 = r0 + fo[i];
-                        for (int i = 0; i < NQ; ++i)
+                        for (int i = 1; i < Q; ++i) r0 = r0 + fo[i];
+                        for (int i = 0; i < Q; ++i)
                             if (fo[i] < 0.0) fo[i] = 0.0;
                         double sm = fo[0];
-                        for (int i = 1; i < NQ; ++i) sm = sm + fo[i];
-                        for (int i = 0; i < NQ; ++i) fo[i] = (r0 * fo[i]) / sm;
+                        for (int i = 1; i < Q; ++i) sm = sm + fo[i];
+                        for (int i = 0; i < Q; ++i) fo[i] = (r0 * fo[i]) / sm;
                     }
                 }
             }
-            for (int i = 0; i < NQ; ++i) s->fn[(size_t)i * N + n] = fo[i];
+            for (int i = 0; i < Q; ++i) s->fn[(size_t)i * N + n] = fo[i];
         }
     /* rows behind the rear wall are quiescent: unchanged */
-    for (int i = 0; i < NQ; ++i)
+    for (int i = 0; i < Q; ++i)
         if (yr > 0) memcpy(s->fn + (size_t)i * N, s->f + (size_t)i * N, sizeof(double) * (size_t)yr * W);
     double *tmp = s->f;
     s->f = s->fn;
@@ -530,14 +601,18 @@ void *orc_create(const orc_params *p)
     if (p->width < 1 || p->height < 3 || (int64_t)p->width * p->height > (1 << 30)) return NULL;
     if (p->width > 32768 || p->height > 32768) return NULL;
     if (!(p->tau > 0.5) || !(p->rho_cell > 0.0) || !(p->rho_c >= 0.0)) return NULL;
+    if (p->lattice != LATTICE_D2Q9 && p->lattice != LATTICE_D2Q7) return NULL;
+    /* a y-periodic triangular lattice needs an even number of rows */
+    if (p->lattice == LATTICE_D2Q7 && p->y_periodic && (p->height & 1)) return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->p = *p;
+    s->L = p->lattice == LATTICE_D2Q7 ? &D2Q7 : &D2Q9;
     s->W = p->width;
     s->H = p->height;
     s->N = (size_t)s->W * s->H;
-    s->f = (double *)calloc(NQ * s->N, sizeof(double));
-    s->fs = (double *)calloc(NQ * s->N, sizeof(double));
-    s->fn = (double *)calloc(NQ * s->N, sizeof(double));
+    s->f = (double *)calloc((size_t)s->L->q * s->N, sizeof(double));
+    s->fs = (double *)calloc((size_t)s->L->q * s->N, sizeof(double));
+    s->fn = (double *)calloc((size_t)s->L->q * s->N, sizeof(double));
     s->mask = (uint8_t *)calloc(s->N, 1);
     s->h = (int32_t *)calloc(s->W, sizeof(int32_t));
     if (!s->f || !s->fs || !s->fn || !s->mask || !s->h) {
@@ -567,7 +642,7 @@ void orc_step(void *h, int64_t n)
 void orc_get_pops(void *h, double *out)
 {
     orc_sim *s = (orc_sim *)h;
-    memcpy(out, s->f, sizeof(double) * NQ * s->N);
+    memcpy(out, s->f, sizeof(double) * (size_t)s->L->q * s->N);
 }
 
 /* Replace the populations (e.g. a test's own initial state); the occupancy
@@ -575,7 +650,7 @@ void orc_get_pops(void *h, double *out)
 void orc_set_pops(void *h, const double *in)
 {
     orc_sim *s = (orc_sim *)h;
-    memcpy(s->f, in, sizeof(double) * NQ * s->N);
+    memcpy(s->f, in, sizeof(double) * (size_t)s->L->q * s->N);
     mask_from_state(s, s->st.y_r);
     s->st.status = 0;
     after_update(s);
@@ -601,11 +676,11 @@ void orc_fields(void *h, double *rho, double *ux, double *uy)
     orc_sim *s = (orc_sim *)h;
     for (size_t n = 0; n < s->N; ++n) {
         double fs[NQ];
-        for (int i = 0; i < NQ; ++i) fs[i] = s->f[(size_t)i * s->N + n];
+        for (int i = 0; i < s->L->q; ++i) fs[i] = s->f[(size_t)i * s->N + n];
         double r = fs[0];
-        for (int i = 1; i < NQ; ++i) r = r + fs[i];
-        double jx = ((((fs[1] - fs[3]) + fs[5]) - fs[6]) - fs[7]) + fs[8];
-        double jy = ((((fs[2] - fs[4]) + fs[5]) + fs[6]) - fs[7]) - fs[8];
+        for (int i = 1; i < s->L->q; ++i) r = r + fs[i];
+        double jx, jy;
+        momentum(s, fs, &jx, &jy);
         rho[n] = r;
         ux[n] = r != 0.0 ? jx / r : 0.0;
         uy[n] = r != 0.0 ? jy / r : 0.0;
@@ -626,4 +701,5 @@ int64_t orc_last_events(void *h, int64_t *node, int32_t *pair, int32_t *count, i
 }
 
 int32_t orc_sizeof_params(void) { return (int32_t)sizeof(orc_params); }
+int32_t orc_directions(void *h) { return (int32_t)((orc_sim *)h)->L->q; }
 int32_t orc_sizeof_stats(void) { return (int32_t)sizeof(orc_stats); }

@@ -26,6 +26,7 @@ GROWTH_MODES = {"none": 0, "bulk": 1, "density": 2, "edge": 3, "band": 4}
 FRONT_KINDS = {"flat": 0, "sinusoidal": 1, "full": 2}
 WALL_MODES = {"fixed": 0, "advance": 1}
 NEGFIX_MODES = {"literal": 0, "rescale": 1}
+LATTICES = {"d2q9": 0, "d2q7": 1}
 
 
 class _Params(ctypes.Structure):
@@ -43,6 +44,7 @@ class _Params(ctypes.Structure):
         ("front_kmax", ctypes.c_int32), ("wall_mode", ctypes.c_int32),
         ("negfix_mode", ctypes.c_int32), ("y_periodic", ctypes.c_int32),
         ("sim_id", ctypes.c_uint32),
+        ("lattice", ctypes.c_int32),
     ]
 
 
@@ -95,6 +97,8 @@ def _load():
         lib.orc_philox4x32_10.argtypes = [ctypes.c_void_p] * 3
         lib.orc_sizeof_params.restype = ctypes.c_int32
         lib.orc_sizeof_stats.restype = ctypes.c_int32
+        lib.orc_directions.restype = ctypes.c_int32
+        lib.orc_directions.argtypes = [ctypes.c_void_p]
         assert lib.orc_sizeof_params() == ctypes.sizeof(_Params)
         assert lib.orc_sizeof_stats() == ctypes.sizeof(_Stats)
         _lib = lib
@@ -104,7 +108,7 @@ def _load():
 def _params(d: dict) -> _Params:
     p = _Params()
     for name, ctype in _Params._fields_:
-        v = d[name]
+        v = d.get(name, "d2q9") if name == "lattice" else d[name]
         if name == "growth_mode":
             v = GROWTH_MODES[v] if isinstance(v, str) else v
         elif name == "front_kind":
@@ -113,6 +117,8 @@ def _params(d: dict) -> _Params:
             v = WALL_MODES[v] if isinstance(v, str) else v
         elif name == "negfix_mode":
             v = NEGFIX_MODES[v] if isinstance(v, str) else v
+        elif name == "lattice":
+            v = LATTICES[v] if isinstance(v, str) else v
         setattr(p, name, v)
     return p
 
@@ -139,6 +145,7 @@ class OracleSim:
         self._h = self._lib.orc_create(ctypes.byref(self._p))
         if not self._h:
             raise ValueError("oracle rejected the parameters")
+        self.Q = int(self._lib.orc_directions(self._h))
 
     def close(self):
         if self._h:
@@ -155,13 +162,13 @@ class OracleSim:
         self._lib.orc_step(self._h, int(n))
 
     def pops(self) -> np.ndarray:
-        out = np.empty((9, self.H, self.W), dtype=np.float64)
+        out = np.empty((self.Q, self.H, self.W), dtype=np.float64)
         self._lib.orc_get_pops(self._h, out.ctypes.data)
         return out
 
     def set_pops(self, f: np.ndarray):
         f = np.ascontiguousarray(f, dtype=np.float64)
-        assert f.shape == (9, self.H, self.W)
+        assert f.shape == (self.Q, self.H, self.W)
         self._lib.orc_set_pops(self._h, f.ctypes.data)
 
     def mask(self) -> np.ndarray:

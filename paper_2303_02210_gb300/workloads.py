@@ -30,7 +30,7 @@ def base_params(**overrides) -> dict:
         front_kind="flat", front_row=16.0, front_amp=0.5, front_kmin=1, front_kmax=64,
         wall_mode="advance", wall_min_gap=50.0, wall_w_factor=10.0,
         negfix_mode="literal", y_periodic=0,
-        seed=1, sim_id=0,
+        seed=1, sim_id=0, lattice="d2q9",
     )
     for k, v in overrides.items():
         if k not in p:
