@@ -53,6 +53,7 @@ enum { LBM_FRONT_FLAT = 0, LBM_FRONT_SINUSOIDAL = 1, LBM_FRONT_FULL = 2 };
 enum { LBM_WALL_FIXED = 0, LBM_WALL_ADVANCE = 1 };
 enum { LBM_NEGFIX_LITERAL = 0, LBM_NEGFIX_RESCALE = 1 };
 enum { LBM_FP32 = 0, LBM_FP64 = 1, LBM_FP16 = 2, LBM_BF16 = 3 };
+enum { LBM_D2Q9 = 0, LBM_D2Q7 = 1 };
 
 /*
  * Model parameters (App. A parameter list; Sec. II for the model).
@@ -85,6 +86,13 @@ enum { LBM_FP32 = 0, LBM_FP64 = 1, LBM_FP16 = 2, LBM_BF16 = 3 };
  *               divisions injected into global memory first; 5: choose for
  *               a simulation that shares the GPU with others (the four-row
  *               form where the TMA-staged kernel applies)
+ *  lattice      LBM_D2Q9, or LBM_D2Q7: the paper's triangular lattice (Sec.
+ *               II; Eq. 3 with 4, 8, 2, weights 1/2 and 1/12), rows of nodes
+ *               along x with the odd rows shifted by half a spacing, rows
+ *               sqrt(3)/2 apart, directions 1:(1,0) 2:(1/2,s) 3:(-1/2,s)
+ *               4:(-1,0) 5:(-1/2,-s) 6:(1/2,-s), s = sqrt(3)/2; FP32 or FP64,
+ *               update_kernel 0, 1 or 5 (the plain-load kernel), an even H
+ *               if y_periodic. Populations have 7 planes instead of 9
  */
 typedef struct {
     double tau, mu, rho_c, rho_cell, sigma, rho0, growth_rate;
@@ -95,6 +103,7 @@ typedef struct {
     uint32_t sim_id;
     int32_t precision;
     int32_t update_kernel;
+    int32_t lattice;
 } lbm_params_t;
 
 /* Counters and observables after the latest completed step. */
@@ -178,9 +187,10 @@ int lbm_fields(lbm_sim *sim, double *rho, double *ux, double *uy);
 /* Same as lbm_fields into caller device arrays of W*H doubles. Enqueues only. */
 int lbm_fields_device(lbm_sim *sim, double *rho, double *ux, double *uy);
 
-/* Current populations into a caller host array of 9*H*W doubles, [q][y][x]
+/* Current populations into a caller host array of Q*H*W doubles, [q][y][x]
  * with the D2Q9 order 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1)
- * 6:(-1,1) 7:(-1,-1) 8:(1,-1). Syncs. */
+ * 6:(-1,1) 7:(-1,-1) 8:(1,-1) (Q = 9), or the D2Q7 order of lbm_params_t
+ * (Q = 7). Syncs. */
 int lbm_populations(lbm_sim *sim, double *f_host);
 
 /* Replaces the populations with the caller's host array (layout as above,

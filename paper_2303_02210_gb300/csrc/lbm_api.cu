@@ -87,6 +87,7 @@ uint16_t encode16(int precision, double f, float c)
 
 struct Layout {
     int Wp, MW, hcap, ns_max;
+    int Q; // lattice directions (population planes)
     long long P;
     int elem;
     uint64_t off_f0, off_f1, off_mask, off_heights, off_rows0, off_sc, off_htab, off_hlist, off_evk,
@@ -97,6 +98,7 @@ Layout make_layout(const lbm_params_t &p)
 {
     Layout L{};
     L.elem = p.precision == LBM_FP64 ? 8 : (p.precision == LBM_FP32 ? 4 : 2);
+    L.Q = p.lattice == LBM_D2Q7 ? 7 : 9;
     // stored row: kXO columns left of x = 0 (x = -1 the ghost of W - 1), the
     // W columns, the ghost of column 0 at x = W, padding to 128 bytes of FP32
     L.Wp = (p.width + 2 * kXO + 31) / 32 * 32;
@@ -115,7 +117,7 @@ Layout make_layout(const lbm_params_t &p)
     L.hcap = 1;
     while (L.hcap < 2 * L.ns_max) L.hcap <<= 1;
     uint64_t o = 0;
-    const uint64_t fbytes = (uint64_t)9 * (uint64_t)L.P * (uint64_t)L.elem;
+    const uint64_t fbytes = (uint64_t)L.Q * (uint64_t)L.P * (uint64_t)L.elem;
     L.off_f0 = o; o = align256(o + fbytes);
     L.off_f1 = o; o = align256(o + fbytes);
     L.off_mask = o; o = align256(o + (uint64_t)p.height * L.MW * 4u);
@@ -271,6 +273,12 @@ int lbm_validate(const lbm_params_t *p)
     if (p->update_kernel < 0 || p->update_kernel > 5) return LBM_ERR_INVALID_ARG;
     if (p->update_kernel >= 2 && p->update_kernel <= 4 && (p->precision == LBM_FP64 || p->y_periodic))
         return LBM_ERR_INVALID_ARG;
+    if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D2Q7) return LBM_ERR_INVALID_ARG;
+    // D2Q7: FP32 or FP64 storage, the plain-load update, an even H when periodic in y
+    if (p->lattice == LBM_D2Q7 &&
+        ((p->precision != LBM_FP32 && p->precision != LBM_FP64) ||
+         (p->update_kernel != 0 && p->update_kernel != 1 && p->update_kernel != 5) || (p->y_periodic && (p->height & 1))))
+        return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
 
@@ -317,10 +325,13 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     s->p = *p;
     s->device = dev;
     s->L = make_layout(*p);
-    s->kt = p->precision == LBM_FP64   ? &kTableF64
-            : p->precision == LBM_FP16 ? &kTableF16
-            : p->precision == LBM_BF16 ? &kTableBF16
-                                       : &kTableF32;
+    if (p->lattice == LBM_D2Q7)
+        s->kt = p->precision == LBM_FP64 ? &kTableF64Q7 : &kTableF32Q7;
+    else
+        s->kt = p->precision == LBM_FP64   ? &kTableF64
+                : p->precision == LBM_FP16 ? &kTableF16
+                : p->precision == LBM_BF16 ? &kTableBF16
+                                           : &kTableF32;
     s->stream = (cudaStream_t)stream;
     s->cur = 0;
     s->step = 0;
@@ -669,14 +680,15 @@ int lbm_populations(lbm_sim *s, double *f_host)
     if (!s || !f_host) return LBM_ERR_INVALID_ARG;
     USE_DEVICE(s);
     const int W = s->p.width, H = s->p.height, el = s->L.elem;
-    std::vector<char> tmp((size_t)9 * W * H * el);
-    for (int i = 0; i < 9; ++i) {
+    const int Q = s->L.Q;
+    std::vector<char> tmp((size_t)Q * W * H * el);
+    for (int i = 0; i < Q; ++i) {
         const char *src = (const char *)s->d.f[s->cur] + (size_t)i * s->L.P * el;
         CK(cudaMemcpy2DAsync(tmp.data() + (size_t)i * W * H * el, (size_t)W * el, src, (size_t)s->L.Wp * el,
                              (size_t)W * el, H, cudaMemcpyDeviceToHost, s->stream));
     }
     CK(cudaStreamSynchronize(s->stream));
-    const size_t n = (size_t)9 * W * H;
+    const size_t n = (size_t)s->L.Q * W * H;
     if (el == 8) {
         std::memcpy(f_host, tmp.data(), n * 8);
     } else if (el == 4) {
@@ -696,7 +708,7 @@ int lbm_set_populations(lbm_sim *s, const double *f_host)
     if (!s || !f_host) return LBM_ERR_INVALID_ARG;
     USE_DEVICE(s);
     const int W = s->p.width, H = s->p.height, el = s->L.elem;
-    const size_t n = (size_t)9 * W * H;
+    const size_t n = (size_t)s->L.Q * W * H;
     // every step leaves the populations non-negative; so must the caller
     for (size_t k = 0; k < n; ++k)
         if (!(f_host[k] >= 0.0) || !std::isfinite(f_host[k])) return LBM_ERR_INVALID_ARG;
@@ -713,7 +725,7 @@ int lbm_set_populations(lbm_sim *s, const double *f_host)
             t[k] = encode16(s->p.precision, f_host[k], s->d.pop_shift[plane_class((int)(k / plane))]);
     }
     for (int b = 0; b < 2; ++b)
-        for (int i = 0; i < 9; ++i) {
+        for (int i = 0; i < s->L.Q; ++i) {
             char *dst = (char *)s->d.f[b] + (size_t)i * s->L.P * el;
             CK(cudaMemcpy2DAsync(dst, (size_t)s->L.Wp * el, tmp.data() + (size_t)i * W * H * el, (size_t)W * el,
                                  (size_t)W * el, H, cudaMemcpyHostToDevice, s->stream));
@@ -833,7 +845,7 @@ int lbm_timing_read(lbm_sim *s, int64_t *launches, double *total_ms, int64_t *no
 int lbm_bytes_per_node(lbm_sim *s, int64_t *bytes)
 {
     if (!s || !bytes) return LBM_ERR_INVALID_ARG;
-    *bytes = 18 * (int64_t)s->L.elem;
+    *bytes = 2 * (int64_t)s->L.Q * (int64_t)s->L.elem;
     return LBM_OK;
 }
 

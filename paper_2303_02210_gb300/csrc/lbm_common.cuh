@@ -226,6 +226,8 @@ extern const KernelTable kTableF32;
 extern const KernelTable kTableF64;
 extern const KernelTable kTableF16;
 extern const KernelTable kTableBF16;
+extern const KernelTable kTableF32Q7; // the triangular D2Q7 lattice
+extern const KernelTable kTableF64Q7;
 
 // CTAs the TMA-staged update kernel runs on this many SMs.
 int launch_update_tma_ctas(int nsm, int variant);

@@ -5,4 +5,5 @@
 
 namespace lbm {
 const KernelTable kTableF64 = make_table<double>();
+const KernelTable kTableF64Q7 = make_table7<double>();
 } // namespace lbm

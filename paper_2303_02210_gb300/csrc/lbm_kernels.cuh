@@ -144,6 +144,53 @@ __device__ __forceinline__ long long pull_slot(const SimDev &d, int y_r, int x, 
     return (long long)q * d.P + (long long)ys * d.Wp + xs;
 }
 
+// ---------------------------------------------------------------------------
+// What the planner needs to know about a lattice: its directions, the
+// pre-stream slot of a direction, and the opposite pairs a division loads.
+// Lat9: D2Q9. Lat7: the triangular D2Q7 (Sec. II) with rows of nodes along
+// x, odd rows shifted by half a spacing: 1:(1,0) 2:(1/2,s) 3:(-1/2,s)
+// 4:(-1,0) 5:(-1/2,-s) 6:(1/2,-s), s = sqrt(3)/2; opp(q) = q + 3 (mod 6);
+// the neighbour of (x, y) along 2 is (x + (y & 1), y + 1).
+struct Lat9 {
+    static constexpr int Q = 9;
+    __device__ static long long slot(const SimDev &d, int y_r, int x, int y, int q)
+    {
+        return pull_slot(d, y_r, x, y, q);
+    }
+    __device__ static int pair_of(uint32_t r) { return (int)(r >> 30); }
+    __device__ static int pa(int p) { return pair_a(p); }
+    __device__ static int pb(int p) { return pair_b(p); }
+};
+
+__host__ __device__ constexpr int opp7(int q) { return q == 0 ? 0 : (q <= 3 ? q + 3 : q - 3); }
+// source of direction q at (x, y) before any wrap or wall: x offset by row
+// parity for the directions between rows
+__host__ __device__ constexpr int src7_dx(int q, int par)
+{
+    return q == 1 ? -1 : (q == 4 ? 1 : (q == 2 || q == 6 ? par - 1 : (q == 3 || q == 5 ? par : 0)));
+}
+__host__ __device__ constexpr int src7_dy(int q) { return q == 2 || q == 3 ? -1 : (q == 5 || q == 6 ? 1 : 0); }
+
+struct Lat7 {
+    static constexpr int Q = 7;
+    __device__ static long long slot(const SimDev &d, int y_r, int x, int y, int q)
+    {
+        int ys = y + src7_dy(q);
+        if (d.y_periodic) {
+            ys = ys < 0 ? ys + d.H : (ys >= d.H ? ys - d.H : ys);
+        } else if (ys < y_r || ys >= d.H) {
+            return (long long)opp7(q) * d.P + (long long)y * d.Wp + x;
+        }
+        int xs = x + src7_dx(q, y & 1);
+        xs = xs < 0 ? xs + d.W : (xs >= d.W ? xs - d.W : xs);
+        return (long long)q * d.P + (long long)ys * d.Wp + xs;
+    }
+    // a pair uniform over the three
+    __device__ static int pair_of(uint32_t r) { return (int)(((unsigned long long)r * 3ull) >> 32); }
+    __device__ static int pa(int p) { return p + 1; }
+    __device__ static int pb(int p) { return p + 4; }
+};
+
 // ===========================================================================
 // Initial state (App. A, first paragraph): rho = rho_init (optionally
 // jittered by U[1 - j, 1 + j]) below the front, zero above, u = 0,
@@ -709,20 +756,20 @@ __global__ void __launch_bounds__(TPB) k_update_batch(const SimDev *__restrict__
 // open-addressing table that merges repeated (node, pair) draws, and the
 // per-division records of the TMA-staged update.
 
-template <typename S>
+template <typename S, typename LT = Lat9>
 __device__ __forceinline__ arith_t<S> rho_star(const SimDev &d, const S *f, int y_r, int x, int y)
 {
     using R = arith_t<S>;
     const Pop<S> pc(d);
-    long long o[NQ];
+    long long o[LT::Q];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) o[q] = pull_slot(d, y_r, x, y, q);
-    R v[NQ];
+    for (int q = 0; q < LT::Q; ++q) o[q] = LT::slot(d, y_r, x, y, q);
+    R v[LT::Q];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] = pc.ld(f[o[q]], q);
+    for (int q = 0; q < LT::Q; ++q) v[q] = pc.ld(f[o[q]], q);
     R r = v[0];
 #pragma unroll
-    for (int q = 1; q < NQ; ++q) r = r + v[q];
+    for (int q = 1; q < LT::Q; ++q) r = r + v[q];
     return r;
 }
 
@@ -731,6 +778,7 @@ struct Candidate {
     uint32_t u; // acceptance uniform word (density-dependent growth)
 };
 
+template <typename LT = Lat9>
 __device__ __forceinline__ Candidate draw_candidate(const SimDev &d, long long k, uint32_t t, int ylo,
                                                     unsigned long long nwin)
 {
@@ -741,7 +789,7 @@ __device__ __forceinline__ Candidate draw_candidate(const SimDev &d, long long k
     Candidate c;
     c.y = ylo + (int)(idx / (uint32_t)d.W);
     c.x = (int)(idx % (uint32_t)d.W);
-    c.pair = (int)(r.y >> 30);
+    c.pair = LT::pair_of(r.y);
     c.u = r.z;
     return c;
 }

@@ -3,6 +3,7 @@
 // through.
 #pragma once
 
+#include "lbm_d2q7.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_plan.cuh"
 
@@ -82,6 +83,82 @@ constexpr KernelTable make_table(cudaError_t (*tma_prepare)(const SimDev &, int)
                        &Launch<S>::fields,   &plan_blocks_per_sm<S>,    &Launch<S>::update_blocks_per_sm,
                        Launch<S>::UPD_TPB,   tma_prepare,               tma_update,
                        &Launch<S>::batch_inject, &Launch<S>::batch_update, &Launch<S>::batch_plan};
+}
+
+// The triangular D2Q7 lattice (FP32 or FP64 storage; plain-load update only).
+template <typename S>
+struct Launch7 {
+    static constexpr int UPD_TPB = 128;
+    static constexpr int UPD_NR = sizeof(S) == 8 ? 1 : 2;
+
+    static cudaError_t fill(const SimDev &d, cudaStream_t s)
+    {
+        k_fill7<S><<<4 * 152, 256, 0, s>>>(d);
+        return cudaGetLastError();
+    }
+    static cudaError_t ghosts(const SimDev &d, cudaStream_t s)
+    {
+        k_ghosts7<S><<<152, 256, 0, s>>>(d);
+        return cudaGetLastError();
+    }
+    static cudaError_t scan(const SimDev &d, int cur, cudaStream_t s)
+    {
+        k_scan7<S><<<4 * 152, 256, 0, s>>>(d, cur);
+        return cudaGetLastError();
+    }
+    static cudaError_t plan(const SimDev &d, int init, cudaStream_t s)
+    {
+        return launch_plan<S, Lat7>(d, init, s);
+    }
+    static cudaError_t inject(const SimDev &d, cudaStream_t s)
+    {
+        k_inject<S, Lat7><<<152, 128, 0, s>>>(d);
+        return cudaGetLastError();
+    }
+    static cudaError_t update(const SimDev &d, cudaStream_t s)
+    {
+        k_update7<S, UPD_TPB, UPD_NR><<<d.update_grid, UPD_TPB, 0, s>>>(d);
+        return cudaGetLastError();
+    }
+    static cudaError_t fields(const SimDev &d, int cur, double *rho, double *ux, double *uy, cudaStream_t s)
+    {
+        k_fields7<S><<<4 * 152, 256, 0, s>>>(d, cur, rho, ux, uy);
+        return cudaGetLastError();
+    }
+    static cudaError_t batch_inject(const SimDev *ds, const int4 *bm, int nb, cudaStream_t s)
+    {
+        k_inject_batch<S, Lat7><<<nb, 128, 0, s>>>(ds, bm);
+        return cudaGetLastError();
+    }
+    static cudaError_t batch_update(const SimDev *ds, const int4 *bm, int nb, cudaStream_t s)
+    {
+        k_update7_batch<S, UPD_TPB, UPD_NR><<<nb, UPD_TPB, 0, s>>>(ds, bm);
+        return cudaGetLastError();
+    }
+    static cudaError_t batch_plan(const SimDev *ds, int n, cudaStream_t s)
+    {
+        k_plan_batch<S, Lat7><<<n, PLAN_NT, 0, s>>>(ds);
+        return cudaGetLastError();
+    }
+    static int update_blocks_per_sm()
+    {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_update7<S, UPD_TPB, UPD_NR>, UPD_TPB, 0) !=
+            cudaSuccess)
+            return 0;
+        return n;
+    }
+};
+
+template <typename S>
+constexpr KernelTable make_table7()
+{
+    return KernelTable{(int)sizeof(S),         &Launch7<S>::fill,          &Launch7<S>::ghosts,
+                       &Launch7<S>::scan,      &Launch7<S>::plan,          &Launch7<S>::inject,
+                       &Launch7<S>::update,    &Launch7<S>::fields,        &plan_blocks_per_sm<S, Lat7>,
+                       &Launch7<S>::update_blocks_per_sm,
+                       Launch7<S>::UPD_TPB,    nullptr,                    nullptr,
+                       &Launch7<S>::batch_inject, &Launch7<S>::batch_update, &Launch7<S>::batch_plan};
 }
 
 } // namespace lbm

@@ -119,7 +119,7 @@ __device__ __forceinline__ int plan_block_exscan(int v, int *total, int *s_i)
 // entry is the table slot if this draw was the first of its (node, pair),
 // else -1. For the TMA-staged update, a first draw also gets its record and
 // a place in its owner CTA's bucket (y_r: the rear wall of the coming step).
-template <typename R>
+template <typename R, typename LT = Lat9>
 __device__ __forceinline__ void plan_select(const SimDev &d, uint32_t key, int rank, size_t buf, int y_r)
 {
     EventTable tb;
@@ -130,7 +130,7 @@ __device__ __forceinline__ void plan_select(const SimDev &d, uint32_t key, int r
     d.hlist[rank] = slot;
     d.ev_key[buf + rank] = key;
     if (first >= 0) atomicAdd(&d.ev_count[buf + first], 1);
-    if (d.inject_in_update) {
+    if (LT::Q == 9 && d.inject_in_update) { // records for the TMA-staged (D2Q9) update
         if (slot >= 0) {
             const int owner = division_record<R>(d, rank, key, y_r);
             const int at = atomicAdd(&d.bucket_cnt[owner], 1);
@@ -143,11 +143,11 @@ __device__ __forceinline__ void plan_select(const SimDev &d, uint32_t key, int r
 
 // Acceptance of a candidate (as `accept`, with the heights of this launch
 // read from L2: other blocks wrote them before the last grid barrier).
-template <typename S>
+template <typename S, typename LT = Lat9>
 __device__ __forceinline__ bool plan_accept(const SimDev &d, const S *f, int y_r, const Candidate &c)
 {
     using R = arith_t<S>;
-    const R rs = rho_star<S>(d, f, y_r, c.x, c.y);
+    const R rs = rho_star<S, LT>(d, f, y_r, c.x, c.y);
     switch (d.growth_mode) {
     case GROW_BULK:
     case GROW_BAND: return rs >= rho_c_of<R>(d);
@@ -179,7 +179,7 @@ static __device__ __noinline__ void plan_ns(double growth_rate, double rho_cell,
 
 // The planner of one simulation, run by blocks blk = 0 .. G - 1 of PLAN_NT
 // threads (all resident together when G > 1).
-template <typename S>
+template <typename S, typename LT = Lat9>
 __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int blk)
 {
     using R = arith_t<S>;
@@ -385,7 +385,7 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             const Pop<S> pc(d);
             R r = pc.ld(f[o], 0);
 #pragma unroll
-            for (int i = 1; i < NQ; ++i) r = r + pc.ld(f[i * d.P + o], i);
+            for (int i = 1; i < LT::Q; ++i) r = r + pc.ld(f[i * d.P + o], i);
             fm += fix24<R>(r);
         }
         fm = plan_block_sum(fm, s_ll);
@@ -465,8 +465,8 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             bool a = false;
             uint32_t key = 0u;
             if (j < C && k < kc) {
-                const Candidate c = draw_candidate(d, k, tn, ylo, nwin);
-                a = plan_accept<S>(d, f, nyr, c);
+                const Candidate c = draw_candidate<LT>(d, k, tn, ylo, nwin);
+                a = plan_accept<S, LT>(d, f, nyr, c);
                 key = pack_key(c.x, c.y, c.pair);
             }
             int t_i;
@@ -492,7 +492,7 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             if (lr >= 0) {
                 const long long rank = before + lr;
                 if (rank == ns - 1) s_kstop = (unsigned long long)(blk * C + j + 1);
-                if (rank < ns) plan_select<R>(d, s_key[j], (int)rank, buf, nyr);
+                if (rank < ns) plan_select<R, LT>(d, s_key[j], (int)rank, buf, nyr);
             }
         }
         acc = total;
@@ -504,8 +504,8 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             bool a = false;
             uint32_t key = 0u;
             if (k < cap) {
-                const Candidate c = draw_candidate(d, k, tn, ylo, nwin);
-                a = plan_accept<S>(d, f, nyr, c);
+                const Candidate c = draw_candidate<LT>(d, k, tn, ylo, nwin);
+                a = plan_accept<S, LT>(d, f, nyr, c);
                 key = pack_key(c.x, c.y, c.pair);
             }
             int tot_r;
@@ -523,7 +523,7 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             tt = plan_block_sum(tt, s_ll);
             const long long rank = acc + bf + pr;
             if (a && rank == ns - 1) s_kstop = (unsigned long long)(k + 1);
-            if (a && rank < ns) plan_select<R>(d, key, (int)rank, buf, nyr);
+            if (a && rank < ns) plan_select<R, LT>(d, key, (int)rank, buf, nyr);
             acc += tt;
             base += (long long)G * PLAN_NT;
             ++round;
@@ -602,19 +602,19 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
 }
 
 // The planner of one simulation on a cooperative grid (launch_plan).
-template <typename S>
+template <typename S, typename LT = Lat9>
 __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
 {
-    plan_body<S>(d, init, (int)gridDim.x, (int)blockIdx.x);
+    plan_body<S, LT>(d, init, (int)gridDim.x, (int)blockIdx.x);
 }
 
 // The planners of a batch of simulations, one block each (ds[blockIdx.x]):
 // a block's barriers are its own, so the blocks need not be resident
 // together and the launch is an ordinary one.
-template <typename S>
+template <typename S, typename LT = Lat9>
 __global__ void __launch_bounds__(PLAN_NT) k_plan_batch(const SimDev *__restrict__ ds)
 {
-    plan_body<S>(ds[blockIdx.x], 0, 1, 0);
+    plan_body<S, LT>(ds[blockIdx.x], 0, 1, 0);
 }
 
 // App. A step 3 for the update kernels that read the populations from global
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan_batch(const SimDev *__restrict
 // (node, pair) of step t, right before the update of step t. Distinct
 // (node, pair) never share a slot (each slot streams into exactly one
 // direction of one node).
-template <typename S>
+template <typename S, typename LT = Lat9>
 __device__ __forceinline__ void inject_body(const SimDev &d, int blk, int nblk)
 {
     using R = arith_t<S>;
@@ -640,8 +640,8 @@ __device__ __forceinline__ void inject_body(const SimDev &d, int blk, int nblk)
         const R add = (R)((double)cnt * d.half_cell);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int q = h == 0 ? pair_a(p) : pair_b(p);
-            const long long o = pull_slot(d, y_r, x, y, q);
+            const int q = h == 0 ? LT::pa(p) : LT::pb(p);
+            const long long o = LT::slot(d, y_r, x, y, q);
             // (the slot is in plane q or opp(q): one weight class)
             const S v = pc.st(pc.ld(f[o], q) + add, q);
             f[o] = v;
@@ -653,22 +653,22 @@ __device__ __forceinline__ void inject_body(const SimDev &d, int blk, int nblk)
     }
 }
 
-template <typename S>
+template <typename S, typename LT = Lat9>
 __global__ void k_inject(SimDev d)
 {
-    inject_body<S>(d, (int)blockIdx.x, (int)gridDim.x);
+    inject_body<S, LT>(d, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // Block b of a batched launch works for simulation bm[b].x as its block
 // bm[b].y of bm[b].z (a table built once per batch).
-template <typename S>
+template <typename S, typename LT = Lat9>
 __global__ void k_inject_batch(const SimDev *__restrict__ ds, const int4 *__restrict__ bm)
 {
     const int4 a = bm[blockIdx.x];
-    inject_body<S>(ds[a.x], a.y, a.z);
+    inject_body<S, LT>(ds[a.x], a.y, a.z);
 }
 
-template <typename S>
+template <typename S, typename LT = Lat9>
 cudaError_t launch_plan(const SimDev &d, int init, cudaStream_t s)
 {
     // a cooperative launch: every block resident at once (the grid barriers
@@ -682,14 +682,14 @@ cudaError_t launch_plan(const SimDev &d, int init, cudaStream_t s)
     la[0].val.cooperative = 1;
     cfg.attrs = la;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_plan<S>, d, init);
+    return cudaLaunchKernelEx(&cfg, k_plan<S, LT>, d, init);
 }
 
-template <typename S>
+template <typename S, typename LT = Lat9>
 int plan_blocks_per_sm()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plan<S>, PLAN_NT, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plan<S, LT>, PLAN_NT, 0) != cudaSuccess) return 0;
     return n;
 }
 

@@ -32,6 +32,7 @@ STATUS_FRONT_AT_TOP = 1
 STATUS_GROWTH_STARVED = 2
 STATUS_CAPACITY = 4
 STATUS_TIMEOUT = 8
+LATTICES = {"d2q9": 0, "d2q7": 1}
 UPDATE_KERNELS = {"auto": 0, "plain": 1, "tma": 2, "tma1": 3, "tma_sel": 4, "shared": 5}
 
 
@@ -54,6 +55,7 @@ class lbm_params_t(ctypes.Structure):
         ("front_kmax", ctypes.c_int32), ("wall_mode", ctypes.c_int32),
         ("negfix_mode", ctypes.c_int32), ("y_periodic", ctypes.c_int32),
         ("sim_id", ctypes.c_uint32), ("precision", ctypes.c_int32), ("update_kernel", ctypes.c_int32),
+        ("lattice", ctypes.c_int32),
     ]
 
 
@@ -152,6 +154,9 @@ def make_params(d: dict, precision: str = "fp32", update_kernel: str = "auto") -
             v = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         elif name == "update_kernel":
             v = UPDATE_KERNELS[update_kernel] if isinstance(update_kernel, str) else int(update_kernel)
+        elif name == "lattice":
+            v = d.get("lattice", "d2q9")
+            v = LATTICES[v] if isinstance(v, str) else int(v)
         else:
             v = d[name]
             if name == "growth_mode" and isinstance(v, str):
@@ -219,6 +224,7 @@ class Simulation:
         self.precision = precision
         self.W = int(params["width"])
         self.H = int(params["height"])
+        self.Q = 7 if params.get("lattice", "d2q9") in ("d2q7", 1) else 9  # population planes
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self._p = make_params(params, precision, update_kernel)
         nbytes = lbm_footprint(params, precision)
@@ -292,7 +298,7 @@ class Simulation:
                "lbm_fields_device")
 
     def lbm_populations(self):
-        f = np.empty((9, self.H, self.W))
+        f = np.empty((self.Q, self.H, self.W))
         _check(self._lib.lbm_populations(self._h, f.ctypes.data), "lbm_populations")
         return f
 
@@ -300,7 +306,7 @@ class Simulation:
 
     def lbm_set_populations(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64)
-        assert f.shape == (9, self.H, self.W)
+        assert f.shape == (self.Q, self.H, self.W)
         _check(self._lib.lbm_set_populations(self._h, f.ctypes.data), "lbm_set_populations")
 
     set_pops = lbm_set_populations
