@@ -267,6 +267,17 @@ def measure_storage_16bit() -> dict:
     return out
 
 
+def measure_d2q7() -> dict:
+    """The headline workload on the paper's triangular D2Q7 lattice (FP32,
+    plain-load update: 7 loads and 7 stores of 4 bytes per node update)."""
+    p = wl.lattice_edge(seed=1, lattice="d2q7")
+    out = measure_storage(p, "fp32")
+    out["kernel"] = "k_update7 (plain loads)"
+    out["workload"] = (f"D2Q7 {p['width']}x{p['height']}, otherwise as the headline workload "
+                       f"(one window copy ~{7 * p['width'] * 1026 * 4 / 1e6:.0f} MB, just under the 129 MB L2)")
+    return out
+
+
 def measure_serving(n: int = 100, rate: float = 200.0, steps=(500, 5000), budget_gb: float = 100.0) -> dict:
     """The served form: a fixed trace of n requests (Poisson arrivals at
     `rate` per second, widths log-uniform 128..4096, height = width / 2, bulk,
@@ -475,6 +486,7 @@ def main():
         line["ensemble"] = measure_ensemble()
         line["serving"] = measure_serving()
         line["storage_16bit"] = measure_storage_16bit()
+        line["d2q7"] = measure_d2q7()
     if world == 1 and not args.no_cpu_baseline:
         rate, dt, window = oracle_rate(workload_params(), args.cpu_steps)
         line["cpu_baseline"] = {
