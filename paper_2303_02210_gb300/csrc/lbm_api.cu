@@ -427,12 +427,14 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     d.update_grid = g0 >= ncx ? (g0 / ncx) * ncx : ncx;
     // the planner's blocks must all be resident at once (cooperative launch)
     const int pbs = s->kt->plan_blocks_per_sm();
-    // as few blocks as the work needs (every grid barrier costs an arrival per
-    // block, and small lattices in a batch share the GPU): one 32-column mask
-    // word per warp, about four candidates per thread at the largest n_s;
-    // at least two, at most one per SM
-    const long long want = std::max<long long>((L.MW + 15) / 16, (L.ns_max + 2047) / 2048);
-    const int pg = (int)std::min<long long>(nsm, std::max<long long>(2, want));
+    // one 32-column mask word per warp, about one candidate per thread at
+    // the largest n_s; at least two blocks, at most a quarter of the SMs
+    // (every grid barrier costs an arrival per block; measured on the edge-
+    // growth workload with 17, 34, 38 and 48 blocks, the FP32 step took 77.9,
+    // 76.6, 76.3 and 77.4 us at 4096 x 2048 and 147.6, 143.1, 142.8 and
+    // 142.4 us at 8192 x 2048)
+    const long long want = std::max<long long>((L.MW + 15) / 16, (L.ns_max + 511) / 512);
+    const int pg = (int)std::min<long long>(std::max(2, nsm / 4), std::max<long long>(2, want));
     d.plan_grid = pbs > 0 ? std::min(pg, kPlanMaxBlocks) : 0;
     if (d.plan_grid < 1) {
         if (s->own_arena) cudaFree(s->arena);
