@@ -91,8 +91,10 @@ enum { LBM_D2Q9 = 0, LBM_D2Q7 = 1 };
  *               along x with the odd rows shifted by half a spacing, rows
  *               sqrt(3)/2 apart, directions 1:(1,0) 2:(1/2,s) 3:(-1/2,s)
  *               4:(-1,0) 5:(-1/2,-s) 6:(1/2,-s), s = sqrt(3)/2; FP32 or FP64,
- *               update_kernel 0, 1 or 5 (the plain-load kernel), an even H
- *               if y_periodic. Populations have 7 planes instead of 9
+ *               update_kernel 0, 1, 2 or 5 (0, 2 and 5: the one TMA-staged
+ *               D2Q7 kernel, two-row tiles, for FP32 with walls in y, else
+ *               the plain-load kernel; 3 and 4 are refused), an even H if
+ *               y_periodic. Populations have 7 planes instead of 9
  */
 typedef struct {
     double tau, mu, rho_c, rho_cell, sigma, rho0, growth_rate;

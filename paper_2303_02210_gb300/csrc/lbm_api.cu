@@ -199,11 +199,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// Population copy as a 3-D FP32 tensor {Wp, H, 9} of whole stored rows
+// Population copy as a 3-D tensor {Wp, H, Q} of whole stored rows
 // (coordinate x_stored = x + kXO, so the ghost columns are inside) with row
-// pitch Wp and plane pitch P elements; `bx` x `by` x 9 boxes. Out-of-range
+// pitch Wp and plane pitch P elements; `bx` x `by` x Q boxes. Out-of-range
 // loads read zeros.
-bool encode_population_map(CUtensorMap *m, void *base, int Wp, int H, long long P, int bx, int by, int precision)
+bool encode_population_map(CUtensorMap *m, void *base, int Wp, int H, long long P, int Q, int bx, int by,
+                           int precision)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
@@ -211,9 +212,9 @@ bool encode_population_map(CUtensorMap *m, void *base, int Wp, int H, long long 
     const CUtensorMapDataType dt = precision == LBM_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : precision == LBM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const cuuint64_t dims[3] = {(cuuint64_t)Wp, (cuuint64_t)H, 9};
+    const cuuint64_t dims[3] = {(cuuint64_t)Wp, (cuuint64_t)H, (cuuint64_t)Q};
     const cuuint64_t strides[2] = {(cuuint64_t)Wp * el, (cuuint64_t)P * el};
-    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 9};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)Q};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -274,10 +275,11 @@ int lbm_validate(const lbm_params_t *p)
     if (p->update_kernel >= 2 && p->update_kernel <= 4 && (p->precision == LBM_FP64 || p->y_periodic))
         return LBM_ERR_INVALID_ARG;
     if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D2Q7) return LBM_ERR_INVALID_ARG;
-    // D2Q7: FP32 or FP64 storage, the plain-load update, an even H when periodic in y
+    // D2Q7: FP32 or FP64 storage, the plain-load or the (one) TMA-staged
+    // update, an even H when periodic in y
     if (p->lattice == LBM_D2Q7 &&
-        ((p->precision != LBM_FP32 && p->precision != LBM_FP64) ||
-         (p->update_kernel != 0 && p->update_kernel != 1 && p->update_kernel != 5) || (p->y_periodic && (p->height & 1))))
+        ((p->precision != LBM_FP32 && p->precision != LBM_FP64) || p->update_kernel == 3 || p->update_kernel == 4 ||
+         (p->y_periodic && (p->height & 1))))
         return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
@@ -449,7 +451,9 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     // 126 against 132 us per update at 8192 x 2048 the other way round); the
     // four-row form for a simulation that shares the GPU (5: 15.1 against
     // 12.5 G node updates/s aggregate for a hundred concurrent requests)
-    s->tma_variant = (p->update_kernel == 3 || p->update_kernel == 5 || (p->update_kernel == 0 && p->width > 4096))
+    // (D2Q7: one form, two-row tiles)
+    s->tma_variant = p->lattice == LBM_D2Q9 && (p->update_kernel == 3 || p->update_kernel == 5 ||
+                                                (p->update_kernel == 0 && p->width > 4096))
                          ? 1
                          : 0;
     const bool tma_inject = p->update_kernel != 4; // 4: the selector injects into global memory
@@ -459,7 +463,7 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
         while ((1 << d.upd_tyl2) < ty) ++d.upd_tyl2;
         bool ok = true;
         for (int b = 0; b < 2 && ok; ++b)
-            ok = encode_population_map(&s->maps[b], (char *)d.f[b] - (size_t)kXO * L.elem, d.Wp, d.H, d.P,
+            ok = encode_population_map(&s->maps[b], (char *)d.f[b] - (size_t)kXO * L.elem, d.Wp, d.H, d.P, L.Q,
                                        kTmaBoxX + 8, ty + 2, p->precision);
         s->use_tma = ok;
         d.inject_in_update = ok && tma_inject ? 1 : 0;

@@ -302,6 +302,38 @@ __device__ __forceinline__ R fix_negative7(R *fo, int mode)
     return added;
 }
 
+// For the TMA-staged D2Q7 update (as division_record for D2Q9): where
+// division e goes. Its node's tile (of kTmaBoxX x 2^upd_tyl2 nodes of the
+// active window, dealt round-robin over upd_ctas CTAs), that tile's index
+// among the owner's tiles, and the offsets of its two pre-stream slots in the
+// tile's staged box ((kTmaBoxX + 8) x (2^upd_tyl2 + 2) x 7 with the tile at
+// column 4, row 1): the source (x + src7_dx(q, y & 1), y + src7_dy(q)),
+// unwrapped in x (the box holds the ghost columns -1 and W), or across a wall
+// the node's own population opp7(q). Returns the owner CTA.
+__device__ __forceinline__ int division_record7(const SimDev &d, int e, uint32_t key, int y_r)
+{
+    constexpr int LX = kTmaBoxX + 8;
+    const int TY = 1 << d.upd_tyl2, PL = (TY + 2) * LX;
+    const int x = key_x(key), y = key_y(key), p = key_pair(key);
+    const int ncx = (d.W + kTmaBoxX - 1) / kTmaBoxX;
+    const int ty = (y - y_r) >> d.upd_tyl2, tx = x / kTmaBoxX;
+    const uint32_t tile = (uint32_t)(ty * ncx + tx);
+    const uint32_t q = __umulhi(tile, d.upd_magic);
+    const int x0 = tx * kTmaBoxX, y0 = y_r + ty * TY;
+    const int owner = (int)(tile - q * (uint32_t)d.upd_ctas);
+    d.rec_owner[e] = owner;
+    d.rec_k[e] = (int)q;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int qd = h == 0 ? Lat7::pa(p) : Lat7::pb(p);
+        const int ys = y + src7_dy(qd);
+        d.rec_off[2 * e + h] = (ys < y_r || ys >= d.H)
+                                   ? opp7(qd) * PL + (y - y0 + 1) * LX + (x - x0 + 4)
+                                   : qd * PL + (ys - y0 + 1) * LX + (x + src7_dx(qd, y & 1) - x0 + 4);
+    }
+    return owner;
+}
+
 // ===========================================================================
 // The fused update on D2Q7 (App. A steps 1, 2, 4-7; step 3's divisions were
 // added to the pre-stream slots by k_inject): as update_body, with the

@@ -85,7 +85,8 @@ constexpr KernelTable make_table(cudaError_t (*tma_prepare)(const SimDev &, int)
                        &Launch<S>::batch_inject, &Launch<S>::batch_update, &Launch<S>::batch_plan};
 }
 
-// The triangular D2Q7 lattice (FP32 or FP64 storage; plain-load update only).
+// The triangular D2Q7 lattice (FP32 or FP64 storage; the TMA-staged update
+// for FP32 comes with the table).
 template <typename S>
 struct Launch7 {
     static constexpr int UPD_TPB = 128;
@@ -150,14 +151,18 @@ struct Launch7 {
     }
 };
 
+// (tma_prepare, tma_update: the TMA-staged update of lbm_update7_tma.cuh for
+// FP32 storage, null otherwise)
 template <typename S>
-constexpr KernelTable make_table7()
+constexpr KernelTable make_table7(cudaError_t (*tma_prepare)(const SimDev &, int) = nullptr,
+                                  cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *, int, bool,
+                                                            cudaStream_t) = nullptr)
 {
     return KernelTable{(int)sizeof(S),         &Launch7<S>::fill,          &Launch7<S>::ghosts,
                        &Launch7<S>::scan,      &Launch7<S>::plan,          &Launch7<S>::inject,
                        &Launch7<S>::update,    &Launch7<S>::fields,        &plan_blocks_per_sm<S, Lat7>,
                        &Launch7<S>::update_blocks_per_sm,
-                       Launch7<S>::UPD_TPB,    nullptr,                    nullptr,
+                       Launch7<S>::UPD_TPB,    tma_prepare,                tma_update,
                        &Launch7<S>::batch_inject, &Launch7<S>::batch_update, &Launch7<S>::batch_plan};
 }
 

@@ -29,6 +29,7 @@
 // keeps the new selection's statistics pending.
 #pragma once
 
+#include "lbm_d2q7.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_tma.cuh"
 
@@ -130,9 +131,13 @@ __device__ __forceinline__ void plan_select(const SimDev &d, uint32_t key, int r
     d.hlist[rank] = slot;
     d.ev_key[buf + rank] = key;
     if (first >= 0) atomicAdd(&d.ev_count[buf + first], 1);
-    if (LT::Q == 9 && d.inject_in_update) { // records for the TMA-staged (D2Q9) update
+    if (d.inject_in_update) { // records for the TMA-staged update
         if (slot >= 0) {
-            const int owner = division_record<R>(d, rank, key, y_r);
+            int owner;
+            if constexpr (LT::Q == 9)
+                owner = division_record<R>(d, rank, key, y_r);
+            else
+                owner = division_record7(d, rank, key, y_r);
             const int at = atomicAdd(&d.bucket_cnt[owner], 1);
             if (at < kBucketCap) d.bucket[owner * kBucketCap + at] = rank;
         } else {

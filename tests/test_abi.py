@@ -124,3 +124,24 @@ def test_update_kernel_choices_validate():
         assert (lbm.load_library().lbm_validate(ctypes.byref(q)) == 0) == ok64, uk
     q = lbm.make_params(p, "fp32", 6)
     assert lbm.load_library().lbm_validate(ctypes.byref(q)) == -1
+
+
+def test_d2q7_update_kinds_validate():
+    """D2Q7 takes the plain-load kernel and its one TMA-staged form (FP32,
+    walls in y): kinds auto, plain, tma and shared; not the four-row form or
+    the global-injection selector, not 16-bit storage, not tma when periodic
+    in y, and no odd H when periodic."""
+    p = dict(wl.lattice_small(), lattice="d2q7")
+    lib = lbm.load_library()
+    for uk, ok in (("auto", True), ("plain", True), ("tma", True), ("shared", True), ("tma1", False),
+                   ("tma_sel", False)):
+        q = lbm.make_params(p, "fp32", uk)
+        assert (lib.lbm_validate(ctypes.byref(q)) == 0) == ok, uk
+    for uk, ok in (("auto", True), ("plain", True), ("tma", False), ("shared", True)):
+        q = lbm.make_params(p, "fp64", uk)
+        assert (lib.lbm_validate(ctypes.byref(q)) == 0) == ok, uk
+    assert lbm.lbm_validate(p, "fp16") == -1 and lbm.lbm_validate(p, "bf16") == -1
+    per = dict(p, y_periodic=1, front_kind="full", height=64)
+    assert lib.lbm_validate(ctypes.byref(lbm.make_params(per, "fp32", "tma"))) == -1
+    assert lib.lbm_validate(ctypes.byref(lbm.make_params(per, "fp32", "auto"))) == 0
+    assert lbm.lbm_validate(dict(per, height=63)) == -1

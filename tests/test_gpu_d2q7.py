@@ -1,14 +1,15 @@
 """The triangular D2Q7 lattice (the paper's, Sec. II) on the GPU against the
 FP64 oracle, through the C ABI: FP64 bit-exact (populations, mask, heights,
 every counter, the division schedule), FP32 within 1e-5 with no flips, at
-128 x 64 over 1000 steps and at the full 4096 x 2048 edge workload; and the
-batched form bit-exact with single stepping."""
+128 x 64 over 1000 steps and at the full 4096 x 2048 edge workload; the
+TMA-staged FP32 update bit-exact with the plain-load one; and the batched
+form bit-exact with single stepping."""
 import numpy as np
 import pytest
 
 from oracle.oracle import OracleSim
 from paper_2303_02210_gb300 import workloads as wl
-from tests.test_gpu_parity import RTOL_FP32, assert_bit_exact, field_errors
+from tests.test_gpu_parity import EXACT_STATS, RTOL_FP32, assert_bit_exact, field_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -88,14 +89,77 @@ def test_full_size_edge_workload():
     assert g32.stats()["ns_total"] == o.stats()["ns_total"]
 
 
-def test_tma_kinds_are_refused_for_d2q7():
+def test_update_kinds_for_d2q7():
+    """One TMA-staged D2Q7 form (two-row tiles, FP32, walls in y): "tma" and
+    the automatic choice take it, "tma1" and "tma_sel" are refused, as are
+    16-bit storage and "tma" on a lattice periodic in y."""
     from paper_2303_02210_gb300.lbm import lbm_validate
     p = q7(wl.lattice_small())
-    with pytest.raises(Exception):
-        gpu_sim(p, "fp32", "tma")
+    for kind in ("tma1", "tma_sel"):
+        with pytest.raises(Exception):
+            gpu_sim(p, "fp32", kind)
     with pytest.raises(Exception):
         gpu_sim(p, "fp16")
+    with pytest.raises(Exception):
+        gpu_sim(CASES["periodic_full"], "fp32", "tma")
     assert lbm_validate(p, "fp32") == 0
+    assert gpu_sim(p, "fp32").stats()["update_kernel"] == 2
+    assert gpu_sim(p, "fp32", "tma").stats()["update_kernel"] == 2
+    assert gpu_sim(p, "fp32", "plain").stats()["update_kernel"] == 1
+    assert gpu_sim(CASES["periodic_full"], "fp32").stats()["update_kernel"] == 1
+    assert gpu_sim(p, "fp64").stats()["update_kernel"] == 1
+
+
+TMA_CASES = {k: v for k, v in CASES.items() if not v.get("y_periodic")}
+TMA_CASES["ragged_300"] = q7(wl.lattice_small(seed=74, width=300, height=70, front_row=30.0,
+                                              growth_rate=3e-3, sigma=0.05))
+TMA_CASES["wide_edge"] = q7(wl.lattice_small(seed=75, width=384, height=96, front_row=40.0,
+                                             growth_mode="edge", growth_rate=3e-3,
+                                             front_kind="sinusoidal", front_amp=2.0))
+TMA_CASES["odd_width_129"] = q7(wl.lattice_small(seed=76, width=129, height=41, front_row=15.0,
+                                                 growth_rate=3e-3))
+
+
+@pytest.mark.parametrize("name", sorted(TMA_CASES))
+def test_tma_bit_exact_with_plain_kernel(name):
+    """The TMA-staged D2Q7 update pulls from staged boxes (parity-dependent
+    column offsets, ghost columns, zero-filled rows past the lattice) but runs
+    update7_body's per-node arithmetic: every population, mask bit, height and
+    counter must agree bit for bit with the plain-load kernel."""
+    p = TMA_CASES[name]
+    a = gpu_sim(p, "fp32", "plain")
+    b = gpu_sim(p, "fp32", "tma")
+    assert a.stats()["update_kernel"] == 1 and b.stats()["update_kernel"] == 2
+    for chunk in (1, 9, 90, 200):
+        a.step(chunk)
+        b.step(chunk)
+        sa, sb = a.stats(), b.stats()
+        for k in EXACT_STATS + ["node_updates", "y_hi"]:
+            assert sa[k] == sb[k], (k, sa[k], sb[k])
+        assert np.array_equal(a.pops(), b.pops())
+        assert np.array_equal(a.mask(), b.mask())
+        assert np.array_equal(a.heights(), b.heights())
+
+
+def test_tma_full_size_repeatable_on_reused_memory():
+    """Four fresh full-size TMA-staged D2Q7 runs, three steps each on reused
+    device memory, agree bit for bit with the plain-load kernel (a stage
+    refill overtaking a pending shared-memory read would show here)."""
+    import torch
+    p = q7(wl.lattice_edge(seed=1))
+    a = gpu_sim(p, "fp32", "plain")
+    a.step(3)
+    ref = a.pops()
+    del a
+    for trial in range(4):
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        b = gpu_sim(p, "fp32", "tma")
+        assert b.stats()["update_kernel"] == 2
+        b.step(3)
+        fb = b.pops()
+        del b
+        assert np.array_equal(fb, ref), f"trial {trial}: {int((fb != ref).sum())} populations differ"
 
 
 def test_batched_d2q7_matches_single_stepping():
