@@ -44,16 +44,20 @@ WORKLOAD_NAME = "lattice_edge"
 
 
 WIDTH = 4096  # lattice width of the headline workload (--width changes it, for profiling captures)
+LATTICE = "d2q9"  # the headline lattice (--lattice d2q7, for profiling captures)
 
 
 def workload_params(rank: int = 0) -> dict:
-    return wl.lattice_edge(seed=1 + rank, sim_id=rank, width=WIDTH)
+    return wl.lattice_edge(seed=1 + rank, sim_id=rank, width=WIDTH, lattice=LATTICE)
 
 
 def workload_config(precision: str) -> dict:
     p = workload_params()
+    nq = 7 if LATTICE == "d2q7" else 9  # population planes
+    # one population copy of the ~1026-row active window, in MB
+    mb = nq * p["width"] * 1026 * {"fp64": 8, "fp32": 4}.get(precision, 2) / 1e6
     return {
-        "workload": (f"D2Q9 {p['width']}x{p['height']}, edge-restricted growth depth {p['edge_depth']}, "
+        "workload": (f"{LATTICE.upper()} {p['width']}x{p['height']}, edge-restricted growth depth {p['edge_depth']}, "
                      f"tau {p['tau']}, g {p['growth_rate']}, sinusoidal front k {p['front_kmin']}-"
                      f"{p['front_kmax']} amplitude {p['front_amp']} at row {int(p['front_row'])}, "
                      f"sigma {p['sigma']}, fixed rear wall, {precision} storage"),
@@ -61,11 +65,11 @@ def workload_config(precision: str) -> dict:
         "growth_mode": p["growth_mode"],
         "precision": precision,
         "l2": (f"no flush: each step reads one {precision} population copy of the active window "
-               f"(~{9 * p['width'] * 1026 * {'fp64': 8, 'fp32': 4}.get(precision, 2) / 1e6:.0f} MB) and "
-               f"writes the other; the 129 MB L2 holds less than that"
-               if precision != "fp16" and precision != "bf16" else
-               f"no flush; NOTE each step reads only ~{9 * p['width'] * 1026 * 2 / 1e6:.0f} MB of 16-bit "
-               f"populations, less than the 129 MB L2 (storage_16bit measures on a lattice twice as wide)"),
+               f"(~{mb:.0f} MB) and writes the other; the 129 MB L2 holds less than that"
+               if mb > 129 else
+               f"no flush; NOTE each step reads only ~{mb:.0f} MB of {precision} populations, less than "
+               f"the 129 MB L2" + (" (storage_16bit measures on a lattice twice as wide)"
+                                   if precision in ("fp16", "bf16") else "")),
         "parallelism": "replicas",
     }
 
@@ -362,12 +366,15 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--width", type=int, default=4096,
                     help="lattice width (4096: the headline workload; others for profiling captures)")
+    ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d2q7"],
+                    help="lattice of the main run (d2q9: the headline workload; d2q7 for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the batched-ensemble, serving and 16-bit storage measurements")
     args = ap.parse_args()
-    global WIDTH
+    global WIDTH, LATTICE
     WIDTH = args.width
+    LATTICE = args.lattice
     if args.impl == "reference":
         run_reference(args)
         return
@@ -389,6 +396,8 @@ def main():
     sim = Simulation(params, precision=args.precision, update_kernel=args.update_kernel)
     stream = sim.stream
     kernel_used = {1: "k_update (plain loads)", 2: "k_update_tma (bulk tensor copies)"}[sim.stats()["update_kernel"]]
+    if LATTICE == "d2q7":
+        kernel_used = kernel_used.replace("k_update", "k_update7")
 
     def barrier():
         if dist is not None:
@@ -469,7 +478,8 @@ def main():
     nodes_per_launch = k_nodes / max(args.steps, 1)
     launch_ms = k_ms / max(k_launches, 1)
     achieved = bpn * nodes_per_launch / (launch_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
-    traffic = profiled_traffic(bpn, nodes_per_launch)
+    # (the committed traffic figure is the D2Q9 update's)
+    traffic = profiled_traffic(bpn, nodes_per_launch) if LATTICE == "d2q9" else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
