@@ -340,51 +340,96 @@ __global__ void __launch_bounds__(Tma7Geom<TY>::NT, CTAS)
                 rhob = rhob + gb[i];
             }
             const bool occa = oka && rhoa >= rho_c, occb = okb && rhob >= rho_c;
-            u32x4 wa{0u, 0u, 0u, 0u}, wb{0u, 0u, 0u, 0u};
-            if (NOISE && (occa || occb)) {
-                const uint32_t n = (uint32_t)(y * W + x);
-                wa = philox4x32_10(u32x4{n, t, STREAM_NOISE, d.sim}, d.pk);
-                wb = philox4x32_10(u32x4{n + 1u, t, STREAM_NOISE, d.sim}, d.pk);
-            }
-            float fa[NQ7], fb[NQ7];
-            const float adda = update_node7<NOISE>(ga, rhoa, occa, fa, wa, cf, negfix);
-            const float addb = update_node7<NOISE>(gb, rhob, occb, fb, wb, cf, negfix);
-            // occupancy bits: lanes 0-15 hold one 32-column word, lanes 16-31 the next
-            unsigned v = ((unsigned)occa | ((unsigned)occb << 1)) << (2 * (lane & 15));
-            v |= __shfl_xor_sync(0xffffffffu, v, 1);
-            v |= __shfl_xor_sync(0xffffffffu, v, 2);
-            v |= __shfl_xor_sync(0xffffffffu, v, 4);
-            v |= __shfl_xor_sync(0xffffffffu, v, 8);
-            const int word = (x0 >> 5) + 2 * half + (lane >> 4);
-            if ((lane & 15) == 0 && word < d.MW) d.mask[(long long)y * d.MW + word] = v;
             float *o = fout + (long long)y * Wp + x;
-            // (odd W: the last column alone, x = W is the ghost)
-            if (oka) store_nodes7(o, P, fa, fb, okb);
-            // ghost copies of the edge columns for the next step's boxes
-            if (x == 0) {
+            if (__all_sync(0xffffffffu, occa && occb)) {
+                // the bulk: all 64 nodes of the warp's segment are occupied
+                // (and inside the lattice): no per-node branches, one full
+                // mask word per 16 lanes, the fix only where a value went
+                // negative (it leaves non-negative nodes as they are)
+                const uint32_t n = (uint32_t)(y * W + x);
+                float fa[NQ7], fb[NQ7];
+                if (NOISE) {
+                    float eta[NQ7];
+                    noise_eta7<float>(eta, philox4x32_10(u32x4{n, t, STREAM_NOISE, d.sim}, d.pk), cf);
+                    collide7<float>(ga, rhoa, fa, cf, eta);
+                    noise_eta7<float>(eta, philox4x32_10(u32x4{n + 1u, t, STREAM_NOISE, d.sim}, d.pk), cf);
+                    collide7<float>(gb, rhob, fb, cf, eta);
+                } else {
+                    collide7<float>(ga, rhoa, fa, cf, nullptr);
+                    collide7<float>(gb, rhob, fb, cf, nullptr);
+                }
+                float mn = fminf(fa[0], fb[0]);
 #pragma unroll
-                for (int i = 0; i < NQ7; ++i) o[i * P + W] = fa[i];
-            }
-            if (x == W - 1) {
+                for (int i = 1; i < NQ7; ++i) mn = fminf(mn, fminf(fa[i], fb[i]));
+                float adda = 0.0f, addb = 0.0f;
+                if (__any_sync(0xffffffffu, mn < 0.0f)) {
+                    adda = fix_negative7<float>(fa, negfix);
+                    addb = fix_negative7<float>(fb, negfix);
+                    clip += adda;
+                    clip += addb;
+                }
+                if ((lane & 15) == 0) d.mask[(long long)y * d.MW + (x0 >> 5) + 2 * half + (lane >> 4)] = 0xffffffffu;
+                store_nodes7(o, P, fa, fb, true);
+                const int xw = x0 + 64 * half; // first column of the warp
+                if (xw == 0 || xw + 63 == W - 1) { // a warp at the lattice edge: ghost copies
+                    if (x == 0) {
 #pragma unroll
-                for (int i = 0; i < NQ7; ++i) o[i * P - W] = fa[i];
-            }
-            if (x + 1 == W - 1) {
+                        for (int i = 0; i < NQ7; ++i) o[i * P + W] = fa[i];
+                    }
+                    if (x + 1 == W - 1) {
 #pragma unroll
-                for (int i = 0; i < NQ7; ++i) o[i * P + 1 - W] = fb[i];
-            }
-            // the node's mass: rho plus what the fix added (as update7_body)
-            if (oka) {
-                clip += adda;
-                const float ro = rhoa + adda;
-                mass += fix24<float>(ro);
-                if (ro != 0.0f) maxrow = y;
-            }
-            if (okb) {
-                clip += addb;
-                const float ro = rhob + addb;
-                mass += fix24<float>(ro);
-                if (ro != 0.0f) maxrow = y;
+                        for (int i = 0; i < NQ7; ++i) o[i * P + 1 - W] = fb[i];
+                    }
+                }
+                const float roa = rhoa + adda, rob = rhob + addb;
+                mass += fix24<float>(roa) + fix24<float>(rob);
+                if (roa != 0.0f || rob != 0.0f) maxrow = y;
+            } else {
+                u32x4 wa{0u, 0u, 0u, 0u}, wb{0u, 0u, 0u, 0u};
+                if (NOISE && (occa || occb)) {
+                    const uint32_t n = (uint32_t)(y * W + x);
+                    wa = philox4x32_10(u32x4{n, t, STREAM_NOISE, d.sim}, d.pk);
+                    wb = philox4x32_10(u32x4{n + 1u, t, STREAM_NOISE, d.sim}, d.pk);
+                }
+                float fa[NQ7], fb[NQ7];
+                const float adda = update_node7<NOISE>(ga, rhoa, occa, fa, wa, cf, negfix);
+                const float addb = update_node7<NOISE>(gb, rhob, occb, fb, wb, cf, negfix);
+                // occupancy bits: lanes 0-15 hold one 32-column word, lanes 16-31 the next
+                unsigned v = ((unsigned)occa | ((unsigned)occb << 1)) << (2 * (lane & 15));
+                v |= __shfl_xor_sync(0xffffffffu, v, 1);
+                v |= __shfl_xor_sync(0xffffffffu, v, 2);
+                v |= __shfl_xor_sync(0xffffffffu, v, 4);
+                v |= __shfl_xor_sync(0xffffffffu, v, 8);
+                const int word = (x0 >> 5) + 2 * half + (lane >> 4);
+                if ((lane & 15) == 0 && word < d.MW) d.mask[(long long)y * d.MW + word] = v;
+                // (odd W: the last column alone, x = W is the ghost)
+                if (oka) store_nodes7(o, P, fa, fb, okb);
+                // ghost copies of the edge columns for the next step's boxes
+                if (x == 0) {
+#pragma unroll
+                    for (int i = 0; i < NQ7; ++i) o[i * P + W] = fa[i];
+                }
+                if (x == W - 1) {
+#pragma unroll
+                    for (int i = 0; i < NQ7; ++i) o[i * P - W] = fa[i];
+                }
+                if (x + 1 == W - 1) {
+#pragma unroll
+                    for (int i = 0; i < NQ7; ++i) o[i * P + 1 - W] = fb[i];
+                }
+                // the node's mass: rho plus what the fix added (as update7_body)
+                if (oka) {
+                    clip += adda;
+                    const float ro = rhoa + adda;
+                    mass += fix24<float>(ro);
+                    if (ro != 0.0f) maxrow = y;
+                }
+                if (okb) {
+                    clip += addb;
+                    const float ro = rhob + addb;
+                    mass += fix24<float>(ro);
+                    if (ro != 0.0f) maxrow = y;
+                }
             }
         }
         tx += dtx;
