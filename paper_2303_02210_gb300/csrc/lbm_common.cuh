@@ -205,11 +205,11 @@ struct KernelTable {
     int (*plan_blocks_per_sm)();
     int (*update_blocks_per_sm)();
     int update_tile_x; // columns per block of the update kernel
-    // TMA-staged update (lbm_update_tma.cuh; null for FP64 storage). maps[b]
-    // loads from copy b (box (kTmaBoxX + 8) x (rows per tile + 2) x 9, in
-    // stored-row coordinates). tma_prepare sets the kernel attributes a
-    // launch needs (the first launch does it too); pdl: launch as a
-    // programmatic dependent of the preceding planner kernel.
+    // TMA-staged update (lbm_update_tma.cuh, for D2Q7 lbm_update7_tma.cuh;
+    // null for FP64 storage). maps[b] loads from copy b (box (kTmaBoxX + 8) x
+    // (rows per tile + 2) x Q, in stored-row coordinates). tma_prepare sets
+    // the kernel attributes a launch needs (the first launch does it too);
+    // pdl: launch as a programmatic dependent of the preceding kernel.
     cudaError_t (*tma_prepare)(const SimDev &, int variant);
     cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t);
     // One step's kernels for every simulation of a batch in one launch each:
