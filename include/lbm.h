@@ -257,9 +257,10 @@ const char *lbm_version(void);
  * of Eq. 6's w(t)) are many small, independent lattices; stepped one after
  * another they leave most of the GPU idle. A batch advances its simulations
  * together by replaying a CUDA graph. When all members store their
- * populations in the same type, a step of the whole batch is three launches
- * (injection, update, planner), each over a table of every member's blocks,
- * with one planner block per member; otherwise the graph holds, for each
+ * populations in the same type on the same lattice, a step of the whole
+ * batch is three launches (injection, update, planner), each over a table
+ * of every member's blocks, with one planner block per member; otherwise
+ * the graph holds, for each
  * simulation, a chain of steps (update + planner) as an independent branch.
  * Each simulation computes exactly what lbm_step would (the same arithmetic
  * and counters, bit for bit).
@@ -279,8 +280,8 @@ int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **
 int lbm_batch_step(lbm_batch *batch, int64_t nsteps);
 int lbm_batch_destroy(lbm_batch *batch);
 /* 1 if the batch steps with the batched launches (all members share the
- * storage type), 0 if with one graph branch per member; LBM_ERR_INVALID_ARG
- * for NULL. */
+ * storage type and the lattice), 0 if with one graph branch per member;
+ * LBM_ERR_INVALID_ARG for NULL. */
 int lbm_batch_fused(const lbm_batch *batch);
 
 /* ---- allocation-free variant (the paper has no counterpart) ----
