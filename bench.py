@@ -4,11 +4,13 @@ Default workload: the 4096 x 2048 D2Q9 lattice with edge-restricted growth
 (divisions within 8 rows of the front), tau = 0.8, sinusoidal initial front
 (wavenumbers 1..64, amplitude 1), FP32 storage, fixed rear wall: about 4.2M
 active nodes per step, so each FP32 population copy of the active window is
-about 300 MB, well above the 129 MB L2 (no L2 flush is needed between steps).
+about 151 MB (a step reads one and writes the other), above the 129 MB L2 (no
+L2 flush is needed between steps).
 
-A step is one full time step of the method: the proliferation planner, the
-fused update kernel and the observables kernel (App. A steps 1-7 plus the
-front heights, Eq. 6 and the rear wall).
+A step is one full time step of the method: the fused update kernel (App. A
+steps 1-7) and the planner kernel, which computes the observables (front
+heights, Eq. 6, the rear wall, the active mass) and selects the next step's
+divisions.
 
 Reports MLUPS = active-window node updates per second (whole job, all ranks),
 the fused kernel's achieved HBM bandwidth against the measured copy peak,

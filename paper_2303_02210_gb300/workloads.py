@@ -73,8 +73,8 @@ def lattice_edge(seed: int = 1, **kw) -> dict:
     tau = 0.8, front at row 1024 perturbed by the sum of sinusoids with
     wavenumbers 1..64 and random phases, total amplitude 1.0. The rear wall is
     held fixed so that the whole tissue (about 4.2M nodes) is updated every
-    step: the working set (about 300 MB per FP32 population copy) is far larger
-    than the 129 MB L2."""
+    step: one FP32 population copy of it is about 151 MB, and a step reads one
+    copy and writes the other (about 303 MB), against the 129 MB L2."""
     p = base_params(width=4096, height=2048, tau=0.8, growth_rate=1e-4, growth_mode="edge",
                     edge_depth=8, front_kind="sinusoidal", front_row=1024.0, front_amp=1.0,
                     front_kmin=1, front_kmax=64, wall_mode="fixed", seed=seed)
