@@ -1,7 +1,8 @@
 // The paper's triangular D2Q7 lattice (Sec. II; Eq. 3 with coefficients 4, 8,
 // 2 and weights 1/2, 1/12, c_s^2 = 1/4): the kernels whose arithmetic or
 // streaming differ from D2Q9, in FP32 or FP64 storage (the planner and the
-// injection are the D2Q9 ones on the Lat7 traits). Rows of nodes along x, odd
+// injection are the D2Q9 ones on the Lat7 traits), and the division records
+// of the TMA-staged D2Q7 update (lbm_update7_tma.cuh). Rows of nodes along x, odd
 // rows shifted by half a spacing, rows sqrt(3)/2 apart; directions 0 rest and
 // 1:(1,0) 2:(1/2,s) 3:(-1/2,s) 4:(-1,0) 5:(-1/2,-s) 6:(1/2,-s), s = sqrt(3)/2,
 // opposites q <-> q + 3. Population layout f[q][y][x] with seven planes.
