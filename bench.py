@@ -292,6 +292,23 @@ def measure_d2q7() -> dict:
     return out
 
 
+def dense_params() -> dict:
+    """The headline workload with the tissue filling all but the top four of
+    the 2048 rows (front at row 2044): about 8.4M active nodes, so a FP32
+    step reads and writes about 604 MB of populations, twice the headline's."""
+    return wl.lattice_edge(seed=1, front_row=2044.0)
+
+
+def measure_dense(steps: int = 300) -> dict:
+    """The dense variant (dense_params) by measure_storage. The front meets
+    the top wall within the run (status bit 1); growth goes on below it."""
+    p = dense_params()
+    out = measure_storage(p, "fp32", steps=steps)
+    out["workload"] = (f"D2Q9 {p['width']}x{p['height']}, front at row {int(p['front_row'])}, otherwise as the "
+                       f"headline workload (one window copy ~{9 * p['width'] * p['height'] * 4 / 1e6:.0f} MB)")
+    return out
+
+
 def measure_serving(n: int = 100, rate: float = 200.0, steps=(500, 5000), budget_gb: float = 100.0) -> dict:
     """The served form: a fixed trace of n requests (Poisson arrivals at
     `rate` per second, widths log-uniform 128..4096, height = width / 2, bulk,
@@ -507,6 +524,10 @@ def main():
         line["serving"] = measure_serving()
         line["storage_16bit"] = measure_storage_16bit()
         line["d2q7"] = measure_d2q7()
+        try:
+            line["dense"] = measure_dense()
+        except Exception as e:  # reported, not fatal: the headline line stands
+            line["dense"] = {"error": f"{type(e).__name__}: {e}"}
     if world == 1 and not args.no_cpu_baseline:
         rate, dt, window = oracle_rate(workload_params(), args.cpu_steps)
         line["cpu_baseline"] = {

@@ -45,3 +45,15 @@ def test_profiled_traffic_scales_with_nodes():
         assert 0.5 * 72 < d["dram_bytes_per_node"] <= 1.5 * 72
     else:
         assert t is None
+
+
+def test_dense_variant_doubles_the_window():
+    """The dense C3 variant: the same lattice and growth as the headline with
+    the front at row 2044, so the active window (all rows below the top mass
+    row + 2) is about twice the headline's 1026 rows."""
+    p = bench.dense_params()
+    h = bench.workload_params()
+    assert (p["width"], p["height"]) == (h["width"], h["height"]) == (4096, 2048)
+    assert p["front_row"] == 2044.0 and h["front_row"] == 1024.0
+    assert {k: v for k, v in p.items() if k != "front_row"} == {k: v for k, v in h.items() if k != "front_row"}
+    assert p["wall_mode"] == "fixed"  # the whole tissue is updated every step
