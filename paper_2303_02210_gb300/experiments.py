@@ -1,6 +1,8 @@
 """Measurements on top of the simulation: the front's Fourier modes, their
-growth rates and the dispersion fit of Eq. 8, and the proliferation bias
-around the most and least advanced parts of the front (Sec. IV, Fig. 3).
+growth rates and the dispersion fit of Eq. 8, the proliferation bias
+around the most and least advanced parts of the front (Sec. IV, Fig. 3), and
+the roughening of the front over an ensemble of realisations (Eq. 6 width
+w(t) ~ t^beta, Sec. III).
 
 The analysis functions take plain arrays (front heights h(x) over time,
 division sites) and are independent of the GPU; `measure_*` run the
@@ -11,7 +13,7 @@ paper grows in x, with y along the front). A mode of wavenumber k has
 q = 2 pi k / W.
 
 Run ``python -m paper_2303_02210_gb300.experiments dispersion`` (or
-``bias``) for a JSON summary.
+``bias``, or ``roughness``) for a JSON summary.
 """
 from __future__ import annotations
 
@@ -103,6 +105,25 @@ def box_counts(h: np.ndarray, nodes: np.ndarray, counts: np.ndarray, W: int,
     return int(c[in_box(x_hi)].sum()), int(c[in_box(x_lo)].sum())
 
 
+def ensemble_width(ws: np.ndarray) -> np.ndarray:
+    """The ensemble's interface width at each sample time: the root mean
+    square over realisations of their Eq. 6 widths, ws[time, realisation]."""
+    ws = np.asarray(ws, dtype=np.float64)
+    return np.sqrt(np.mean(ws * ws, axis=1))
+
+
+def growth_exponent(times: Sequence[float], w: Sequence[float], lo: float, hi: float) -> Optional[float]:
+    """beta of w ~ t^beta: the least-squares slope of log w against log t over
+    the samples with lo <= t <= hi; None if fewer than three samples there
+    or a width that is not positive."""
+    t = np.asarray(times, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    m = (t >= lo) & (t <= hi)
+    if m.sum() < 3 or np.any(w[m] <= 0) or np.any(t[m] <= 0):
+        return None
+    return float(np.polyfit(np.log(t[m]), np.log(w[m]), 1)[0])
+
+
 # ---------------------------------------------------------------------------
 # Measurements (GPU, through the C ABI)
 
@@ -179,15 +200,67 @@ def measure_bias(width: int = 1024, steps: int = 4000, warm: int = 1000, seed: i
             "longest_mode_share": float(power[0] / power.sum()) if power.sum() > 0 else None}
 
 
+def roughness_params(width: int = 1024, height: int = 8192, seed: int = 1, **kw) -> dict:
+    """One realisation of the roughening ensemble: the 1024-wide bulk-growth
+    workload (flat front at row 32 with seeded noise, tau = 0.8, advancing
+    rear wall) on a lattice tall enough that the front does not reach the top
+    within the run, with faster growth (g = 1e-3) by default."""
+    from . import workloads as wl
+    p = wl.lattice_kpz(seed=seed, width=width, height=height, growth_rate=1e-3, sim_id=seed)
+    p.update(kw)
+    return p
+
+
+def measure_roughness(width: int = 1024, seeds: int = 16, steps: int = 20000, every: int = 100,
+                      height: int = 8192, windows: Sequence = ((300, 3000), (1000, 10000), (2000, 20000)),
+                      precision: str = "fp32", simulation=None, batch=None, **kw) -> dict:
+    """w(t) of `seeds` realisations stepped together as one batch, Eq. 6's w
+    of each sampled every `every` steps; the ensemble width (ensemble_width)
+    and beta over each window of `windows` (growth_exponent). `simulation`
+    and `batch` default to lbm.Simulation and lbm.Batch."""
+    if simulation is None or batch is None:
+        from .lbm import Batch, Simulation
+        simulation = simulation or Simulation
+        batch = batch or Batch
+    sims = [simulation(roughness_params(width=width, height=height, seed=1 + s, **kw), precision=precision)
+            for s in range(seeds)]
+    b = batch(sims)
+    times, ws, hbar = [], [], []
+    try:
+        for k in range(steps // every):
+            b.step(every)
+            fh = [sm.front_heights() for sm in sims]
+            times.append((k + 1) * every)
+            ws.append([f[2] for f in fh])
+            hbar.append(float(np.mean([f[1] for f in fh])))
+        status = sorted({int(sm.stats()["status"]) for sm in sims})
+    finally:
+        b.close()
+        for sm in sims:
+            sm.close()
+    w = ensemble_width(np.array(ws)) if ws else np.zeros(0)
+    return {"width": width, "height": height, "seeds": seeds, "steps": steps, "every": every,
+            "t": times, "w": [float(v) for v in w], "hbar": hbar, "status": status,
+            "beta": {f"{lo}-{hi}": growth_exponent(times, w, lo, hi) for lo, hi in windows}}
+
+
 def main(argv: Optional[List[str]] = None) -> None:
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("what", choices=["dispersion", "bias"])
+    ap.add_argument("what", choices=["dispersion", "bias", "roughness"])
     ap.add_argument("--width", type=int, default=None)
     ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--seeds", type=int, default=None, help="realisations (roughness)")
     args = ap.parse_args(argv)
     kw = {k: v for k, v in (("width", args.width), ("steps", args.steps)) if v is not None}
-    out = measure_dispersion(**kw) if args.what == "dispersion" else measure_bias(**kw)
+    if args.what == "dispersion":
+        out = measure_dispersion(**kw)
+    elif args.what == "bias":
+        out = measure_bias(**kw)
+    else:
+        if args.seeds is not None:
+            kw["seeds"] = args.seeds
+        out = measure_roughness(**kw)
     print(json.dumps(out))
 
 

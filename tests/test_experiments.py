@@ -91,3 +91,73 @@ def test_measured_dispersion_short_waves_decay():
     assert all(math.isfinite(v) for v in om.values())
     assert om[32] < 0 and om[32] < om[2]
     assert out["modes"][-1]["amp_end"] < out["modes"][-1]["amp_start"]
+
+
+def test_growth_exponent_recovers_power_laws():
+    t = np.arange(100, 20001, 100, dtype=np.float64)
+    for beta in (1 / 3, 0.5, 0.25):
+        w = 0.3 * t ** beta
+        assert abs(ex.growth_exponent(t, w, 300, 3000) - beta) < 1e-12
+        assert abs(ex.growth_exponent(t, w, 1000, 20000) - beta) < 1e-12
+    # a crossover: slope 1 before t = 2000, 1/3 after; each window sees its own
+    w = np.where(t < 2000, t / 2000.0, (t / 2000.0) ** (1 / 3))
+    assert abs(ex.growth_exponent(t, w, 100, 1900) - 1.0) < 1e-12
+    assert abs(ex.growth_exponent(t, w, 2000, 20000) - 1 / 3) < 1e-12
+    # multiplicative noise of 2% moves the fit by little
+    rng = np.random.default_rng(3)
+    wn = 0.3 * t ** (1 / 3) * np.exp(0.02 * rng.standard_normal(t.size))
+    assert abs(ex.growth_exponent(t, wn, 300, 20000) - 1 / 3) < 0.01
+    # too few samples, or a flat front (w = 0), give no exponent
+    assert ex.growth_exponent(t, 0.3 * t ** 0.5, 100, 200) is None
+    assert ex.growth_exponent(t, np.zeros_like(t), 300, 3000) is None
+
+
+def test_ensemble_width_is_the_rms_over_realisations():
+    ws = np.array([[1.0, 3.0], [2.0, 2.0], [0.0, 0.0]])
+    assert np.allclose(ex.ensemble_width(ws), [math.sqrt(5.0), 2.0, 0.0])
+
+
+def test_measure_roughness_drives_a_batch_and_fits_beta():
+    """The roughness driver with stand-ins for the simulation and the batch:
+    realisation i roughens as a_i t^beta, so the ensemble width is
+    sqrt(mean a_i^2) t^beta and every window must give beta back; the batch
+    steps `every` at a time and everything is closed at the end."""
+    beta = 0.3
+    closed = []
+
+    class FakeSim:
+        def __init__(self, params, precision="fp32"):
+            self.p, self.t = params, 0
+            self.a = 0.1 * params["seed"]
+
+        def front_heights(self):
+            return np.zeros(self.p["width"], np.int32), 32.0 + 0.01 * self.t, self.a * self.t ** beta
+
+        def stats(self):
+            return {"status": 0}
+
+        def close(self):
+            closed.append(self)
+
+    class FakeBatch:
+        def __init__(self, sims):
+            self.sims, self.calls = sims, []
+
+        def step(self, n):
+            self.calls.append(n)
+            for s in self.sims:
+                s.t += n
+
+        def close(self):
+            closed.append(self)
+
+    out = ex.measure_roughness(width=64, seeds=4, steps=5000, every=50, height=256,
+                               windows=((100, 1000), (1000, 5000)), simulation=FakeSim, batch=FakeBatch)
+    assert out["t"] == list(range(50, 5001, 50))
+    a_rms = math.sqrt(np.mean([(0.1 * s) ** 2 for s in range(1, 5)]))
+    assert np.allclose(out["w"], a_rms * np.array(out["t"], dtype=np.float64) ** beta)
+    for v in out["beta"].values():
+        assert abs(v - beta) < 1e-12
+    assert out["status"] == [0] and len(closed) == 5
+    p = ex.roughness_params(width=64, height=256, seed=3)
+    assert p["growth_mode"] == "bulk" and p["wall_mode"] == "advance" and p["sim_id"] == 3
