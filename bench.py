@@ -57,7 +57,7 @@ def workload_config(precision: str) -> dict:
     p = workload_params()
     nq = 7 if LATTICE == "d2q7" else 9  # population planes
     # one population copy of the ~1026-row active window, in MB
-    mb = nq * p["width"] * 1026 * {"fp64": 8, "fp32": 4}.get(precision, 2) / 1e6
+    mb = nq * p["width"] * 1026 * {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision] / 1e6
     return {
         "workload": (f"{LATTICE.upper()} {p['width']}x{p['height']}, edge-restricted growth depth {p['edge_depth']}, "
                      f"tau {p['tau']}, g {p['growth_rate']}, sinusoidal front k {p['front_kmin']}-"
@@ -367,7 +367,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config("fp64 (oracle)"),
+        # our arm's workload description; the oracle computes in FP64 (dtype)
+        "config": workload_config(args.precision),
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -57,3 +57,14 @@ def test_dense_variant_doubles_the_window():
     assert p["front_row"] == 2044.0 and h["front_row"] == 1024.0
     assert {k: v for k, v in p.items() if k != "front_row"} == {k: v for k, v in h.items() if k != "front_row"}
     assert p["wall_mode"] == "fixed"  # the whole tissue is updated every step
+
+
+def test_workload_config_knows_every_storage_type():
+    """The L2 note's byte count comes from a strict table: an unknown
+    precision string is an error, not silently 2 bytes."""
+    import pytest
+    for pr, mb in (("fp64", 303), ("fp32", 151), ("fp16", 76), ("bf16", 76)):
+        cfg, _ = _config("d2q9", 4096, pr)
+        assert f"{mb} MB" in cfg["l2"]
+    with pytest.raises(KeyError):
+        _config("d2q9", 4096, "fp64 (oracle)")
