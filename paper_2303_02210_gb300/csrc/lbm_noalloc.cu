@@ -5,7 +5,9 @@
 // the allocator. Its cross-block scratch (one
 // partial result per block and a completion counter) is a file-scope device
 // array that every GPU loading this library holds until the process exits.
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 
 #include "../../include/lbm.h"
 #include "lbm_common.cuh"
@@ -100,8 +102,27 @@ __global__ void __launch_bounds__(NOALLOC_TPB)
 }
 
 // Device address of the scratch array, looked up once per device (with that
-// device current) on the first call made there.
-static void *g_scratch_addr[64];
+// device current) by the first call made there. Host threads may make their
+// first calls concurrently: the lookup runs under a mutex and the address is
+// published through an atomic pointer, so every later call only loads it.
+static std::atomic<void *> g_scratch_addr[64];
+static std::mutex g_scratch_lock;
+
+static cudaError_t scratch_address(int dev, NoallocScratch **out)
+{
+    void *p = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> guard(g_scratch_lock);
+        p = g_scratch_addr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return e;
+            g_scratch_addr[dev].store(p, std::memory_order_release);
+        }
+    }
+    *out = (NoallocScratch *)p;
+    return cudaSuccess;
+}
 
 } // namespace lbm
 
@@ -119,13 +140,9 @@ extern "C" int lbm_front_heights_noalloc(const uint32_t *mask_dev, int32_t width
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return lbm_record_cuda_error(e);
     if (dev < 0 || dev >= 64) return LBM_ERR_INVALID_ARG;
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return lbm_record_cuda_error(e);
-        g_scratch_addr[dev] = p;
-    }
-    NoallocScratch *scr = (NoallocScratch *)g_scratch_addr[dev];
+    NoallocScratch *scr = nullptr;
+    e = scratch_address(dev, &scr);
+    if (e != cudaSuccess) return lbm_record_cuda_error(e);
     cudaStream_t s = (cudaStream_t)stream;
     // the completion counter must start at zero; the partials are overwritten
     e = cudaMemsetAsync(&scr->done, 0, sizeof(unsigned int), s);
