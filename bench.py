@@ -122,9 +122,13 @@ def profiled_traffic(bytes_per_node_alg: int, nodes_per_launch: float):
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region.
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Samples carry nvidia-smi's timestamp; `stop(since)` keeps those taken
+    after the host time `since` (the start of the loaded window), so samples
+    of an idle GPU before the run are not counted."""
+
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -134,6 +138,8 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        """Starts sampling every 25 ms; returns once the first sample is in
+        (or after 3 s)."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -142,10 +148,13 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
                  "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, since: float = 0.0):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -159,14 +168,17 @@ class ClockSampler:
         with open(self.path) as fh:
             for line in fh:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 9:
+                if len(parts) < 10:
                     continue
                 try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    if ts + 1.0 < since:
+                        continue
+                    sm.append(float(parts[2]))
+                    smax.append(float(parts[3]))
                 except ValueError:
                     continue
-                for n, v in zip(names, parts[5:9]):
+                for n, v in zip(names, parts[6:10]):
                     if v.lower().startswith("active"):
                         reasons.add(n)
         os.unlink(self.path)
@@ -227,8 +239,9 @@ def measure_ensemble(n: int = 256, steps: int = 200, warm: int = 5) -> dict:
 def measure_storage(params: dict, precision: str, steps: int = 1000, warm: int = 10,
                     update_kernel: str = "auto") -> dict:
     """One storage precision on `params`: whole-step rate by CUDA events
-    over `steps` steps, and the update kernel's average launch time (one
-    launch in 16 timed) against the measured copy peak."""
+    over `steps` steps (no other events in that region), then the update
+    kernel's average launch time over a separate pass of 200 steps with every
+    update launch bracketed by events, against the measured copy peak."""
     import torch
     from paper_2303_02210_gb300.lbm import Simulation
     sim = Simulation(params, precision=precision, update_kernel=update_kernel)
@@ -236,8 +249,6 @@ def measure_storage(params: dict, precision: str, steps: int = 1000, warm: int =
     sim.step(warm)
     sim.sync()
     n0 = sim.stats()["node_updates"]
-    sim.lbm_timing_stride(16)
-    sim.lbm_timing_enable((steps + 15) // 16)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -246,6 +257,10 @@ def measure_storage(params: dict, precision: str, steps: int = 1000, warm: int =
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     nodes = sim.stats()["node_updates"] - n0
+    kern_steps = 200
+    sim.lbm_timing_stride(1)
+    sim.lbm_timing_enable(kern_steps)
+    sim.step(kern_steps)
     k_launches, k_ms, k_nodes = sim.lbm_timing_read()
     bpn = sim.lbm_bytes_per_node()
     q7 = params.get("lattice", "d2q9") == "d2q7"
@@ -257,7 +272,7 @@ def measure_storage(params: dict, precision: str, steps: int = 1000, warm: int =
     torch.cuda.empty_cache()
     peak, _ = measured_peak()
     launch_ms = k_ms / max(k_launches, 1)
-    achieved = bpn * (k_nodes / steps) / (launch_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
+    achieved = bpn * (k_nodes / max(k_launches, 1)) / (launch_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
     return {"precision": precision, "value": nodes / (ms * 1e-3) / 1e6, "unit": UNIT,
             "ms_per_step": ms / steps, "steps": steps, "bytes_per_node": bpn, "kernel": kernel,
             "avg_launch_ms": launch_ms, "achieved_gbs": achieved, "frac": achieved / peak}
@@ -348,28 +363,92 @@ def oracle_rate(params: dict, steps: int):
     return window * steps / dt / 1e6, dt, window
 
 
+def _oracle_child(steps: int, start_at: float):
+    """One independent oracle process of the all-core baseline: creates the
+    workload, waits for the common start time, steps, prints JSON."""
+    from oracle.oracle import OracleSim
+    params = workload_params()
+    o = OracleSim(params)
+    wait = start_at - time.time()
+    if wait > 0:
+        time.sleep(wait)
+    t0 = time.time()
+    o.step(steps)
+    t1 = time.time()
+    o.close()
+    print(json.dumps({"start": t0, "end": t1}), flush=True)
+
+
+def oracle_rate_cores(steps: int, want: int = 0):
+    """The FP64 oracle, as it stands (single-threaded), run as independent
+    processes on the host cores at once, each on `steps` steps of the same
+    workload. Returns (aggregate MLUPS over the active window, processes,
+    seconds of the common stepping region). The process count is nproc,
+    capped so that their lattices take at most 60% of the available memory."""
+    params = workload_params()
+    nq = 7 if params.get("lattice") == "d2q7" else 9
+    per = 3 * nq * params["width"] * params["height"] * 8 + (64 << 20)
+    n = want or (os.cpu_count() or 1)
+    try:
+        with open("/proc/meminfo") as fh:
+            avail = next(int(l.split()[1]) * 1024 for l in fh if l.startswith("MemAvailable"))
+        n = max(1, min(n, int(0.6 * avail // per)))
+    except Exception:
+        pass
+    start_at = time.time() + 12.0
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+    procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-child", str(steps),
+                               "--oracle-start", repr(start_at), "--width", str(WIDTH), "--lattice", LATTICE],
+                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, env=env, cwd=ROOT)
+             for _ in range(n)]
+    spans = []
+    for pr in procs:
+        out, _ = pr.communicate()
+        if pr.returncode == 0:
+            spans.append(json.loads(out.decode().strip().splitlines()[-1]))
+    if not spans:
+        return None
+    # the window the GPU updates (as oracle_rate counts it)
+    from oracle.oracle import OracleSim
+    import numpy as np
+    o = OracleSim(params)
+    rho = o.pops().sum(0)
+    rows = np.nonzero(rho.any(1))[0]
+    y_hi = min(params["height"], int(rows.max()) + 2) if len(rows) else 1
+    window = params["width"] * (y_hi - o.stats()["y_r"])
+    o.close()
+    t0 = min(sp["start"] for sp in spans)
+    t1 = max(sp["end"] for sp in spans)
+    return len(spans) * window * steps / (t1 - t0) / 1e6, len(spans), t1 - t0
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle (no reference code exists for this
-    paper) on the host cores, same workload, metric and unit."""
+    paper) on the host cores, same workload, metric and unit: one process per
+    host core (as many as memory allows), each an independent single-threaded
+    oracle run of the bounded sample, stepping at the same time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     params = workload_params()
     warm = min(args.warmup, 1)
     steps = max(1, min(args.steps, 12))
-    if warm:
-        oracle_rate(params, warm)
-    rate, dt, window = oracle_rate(params, steps)
-    sample = (f"{steps} oracle steps (after {warm} warm-up) of the full {params['width']}x"
-              f"{params['height']} workload, single thread; rate counted over the "
-              f"{window} active-window nodes per step the GPU updates")
+    res = oracle_rate_cores(steps)
+    if res is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle processes failed"}), flush=True)
+        return
+    rate, cores, dt = res
+    sample = (f"{cores} independent single-threaded oracle processes at once, each {steps} steps of the full "
+              f"{params['width']}x{params['height']} workload (created before the common start, so the "
+              f"{warm} warm-up step is the creation); aggregate rate over the active-window nodes per step "
+              f"the GPU updates")
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         # our arm's workload description; the oracle computes in FP64 (dtype)
         "config": workload_config(args.precision),
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -382,19 +461,27 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
-    ap.add_argument("--update-kernel", default="auto", choices=["auto", "plain", "tma", "tma1", "tma_sel"])
+    ap.add_argument("--update-kernel", default="auto",
+                    help="auto, plain, tma, tma1, tma_sel, shared, or the numeric lbm_params_t code")
     ap.add_argument("--cpu-steps", type=int, default=12)
     ap.add_argument("--width", type=int, default=4096,
                     help="lattice width (4096: the headline workload; others for profiling captures)")
     ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d2q7"],
                     help="lattice of the main run (d2q9: the headline workload; d2q7 for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-child", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-start", type=float, default=0.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the batched-ensemble, serving and 16-bit storage measurements")
     args = ap.parse_args()
+    if args.update_kernel.isdigit():
+        args.update_kernel = int(args.update_kernel)
     global WIDTH, LATTICE
     WIDTH = args.width
     LATTICE = args.lattice
+    if args.oracle_child:
+        _oracle_child(args.oracle_child, args.oracle_start)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -424,16 +511,18 @@ def main():
             dist.barrier()
 
     # ---- device-resident throughput (inputs resident in HBM) ----
+    # the timed region holds the K steps and nothing else: no per-launch
+    # events (an event pair keeps the update from overlapping the planner
+    # before it), only the outer pair
+    # clocks: sampled from the warm-up to the end of a loaded window of at
+    # least 0.3 s that contains the timed region (untimed steps follow it
+    # when the timed region alone is shorter than the sampling interval)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t_load = time.time()
     sim.step(args.warmup)
     sim.sync()
     st0 = sim.stats()
-    # the update kernel is timed with CUDA events on one launch in 16: an event
-    # pair stops a launch from overlapping the planner before it
-    stride = 16 if args.steps >= 64 else 1
-    sim.lbm_timing_stride(stride)
-    sim.lbm_timing_enable((args.steps + stride - 1) // stride)
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -444,13 +533,25 @@ def main():
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
     st1 = sim.stats()
-    k_launches, k_ms, k_nodes = sim.lbm_timing_read()
     nodes = st1["node_updates"] - st0["node_updates"]
     launches = st1["launches"] - st0["launches"]
-    bpn = sim.lbm_bytes_per_node()
     status = st1["status"]
+    # ---- the update kernel's launch duration: a separate pass right after,
+    # every update launch bracketed by CUDA events on the simulation's stream
+    kern_steps = max(64, min(args.steps, 500))
+    sim.lbm_timing_stride(1)
+    sim.lbm_timing_enable(kern_steps)
+    sim.step(kern_steps)
+    k_launches, k_ms, k_nodes = sim.lbm_timing_read()
+    bpn = sim.lbm_bytes_per_node()
+    while time.time() - t_load < 0.3:
+        sim.step(200)
+        sim.sync()
+    clk = clocks.stop(since=t_load)
+    if clk is not None:
+        clk["window"] = (f"{clk['samples']} nvidia-smi samples (25 ms apart) from the warm-up through the timed "
+                         f"region, the kernel-timing pass and untimed steps to 0.3 s of load")
     sim.close()
     del sim
 
@@ -463,7 +564,8 @@ def main():
     # buffers (lbm_front_heights_async, no wait per step), one wait at the end,
     # Eq. 6 worked out on the host for every step, lbm_destroy
     from paper_2303_02210_gb300.lbm import lbm_eq6
-    e2e_steps = max(1, min(args.steps, 1000))
+    # (a fixed job of 1000 steps, whatever --steps is)
+    e2e_steps = 1000
     W = params["width"]
     hbuf = torch.empty((e2e_steps, W), dtype=torch.int32, pin_memory=True)
     sbuf = torch.empty((e2e_steps, 2), dtype=torch.int64, pin_memory=True)
@@ -494,8 +596,8 @@ def main():
         return
 
     peak, peak_kind = measured_peak()
-    # nodes per launch over all steps of the timed region; time per launch over the sampled ones
-    nodes_per_launch = k_nodes / max(args.steps, 1)
+    # nodes and time per launch over the kernel-timing pass
+    nodes_per_launch = k_nodes / max(k_launches, 1)
     launch_ms = k_ms / max(k_launches, 1)
     achieved = bpn * nodes_per_launch / (launch_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
     # (the committed traffic figure is the D2Q9 update's)
@@ -510,6 +612,8 @@ def main():
                      "kernel": kernel_used + ": fused stream/collide/front/noise",
                      "algorithmic_bytes_per_launch": bpn * nodes_per_launch,
                      "avg_launch_ms": launch_ms, "timed_launches": int(k_launches),
+                     "kernel_timing": (f"{int(k_launches)} consecutive update launches right after the timed "
+                                       f"region, each bracketed by CUDA events on the simulation's stream"),
                      "peak_source": peak_kind},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
@@ -531,12 +635,23 @@ def main():
             line["dense"] = {"error": f"{type(e).__name__}: {e}"}
     if world == 1 and not args.no_cpu_baseline:
         rate, dt, window = oracle_rate(workload_params(), args.cpu_steps)
-        line["cpu_baseline"] = {
-            "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{args.cpu_steps} steps of the FP64 CPU oracle on the full "
-                       f"{params['width']}x{params['height']} workload ({dt:.1f} s, one thread); "
-                       f"rate over the {window} active-window nodes per step"),
-        }
+        one = {"value": rate, "cores": 1,
+               "sample": (f"{args.cpu_steps} steps of the FP64 CPU oracle on the full "
+                          f"{params['width']}x{params['height']} workload ({dt:.1f} s, one thread); "
+                          f"rate over the {window} active-window nodes per step")}
+        allc = oracle_rate_cores(args.cpu_steps)
+        if allc is not None:
+            rate_n, cores, dt_n = allc
+            line["cpu_baseline"] = {
+                "value": rate_n, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": (f"{cores} independent single-threaded oracle processes stepping at once "
+                           f"({os.cpu_count()} host cores), each {args.cpu_steps} steps of the full "
+                           f"{params['width']}x{params['height']} workload ({dt_n:.1f} s); aggregate rate "
+                           f"over the {window} active-window nodes per step"),
+                "single_core": one,
+            }
+        else:
+            line["cpu_baseline"] = dict(one, unit=UNIT, kind="oracle")
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
