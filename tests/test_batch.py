@@ -126,3 +126,102 @@ def test_mixed_precision_batch_uses_branches():
     batch = Batch(members)
     assert not batch.fused
     batch.close()
+
+
+# ---- against the FP64 oracle directly (not only against lbm_step) ----
+ORACLE_MEMBERS = [
+    wl.lattice_small(seed=51, width=64, height=48, front_row=12.0, growth_rate=3e-3),
+    wl.lattice_small(seed=52, growth_mode="edge", edge_depth=4, front_kind="sinusoidal", front_amp=2.0,
+                     front_kmax=6, growth_rate=3e-3),
+    wl.lattice_small(seed=53, width=256, height=64, growth_rate=2e-3, wall_min_gap=8.0),
+    wl.lattice_small(seed=54, width=96, height=40, growth_mode="density", growth_rate=3e-3),
+    wl.lattice_small(seed=55, width=37, height=33, front_row=10.0, growth_mode="band", band_rows=5,
+                     growth_rate=3e-3, wall_min_gap=4.0),
+]
+
+
+def _oracle_after(p, steps):
+    from oracle.oracle import OracleSim
+    o = OracleSim(p)
+    o.step(steps)
+    return o
+
+
+def _bit_exact_with_oracle(g, o):
+    assert np.array_equal(g.pops(), o.pops())
+    assert np.array_equal(g.mask(), o.mask())
+    assert np.array_equal(g.heights(), o.heights())
+    sg, so = g.stats(), o.stats()
+    for k in ("step", "ns_last", "ns_total", "div_total", "starved_steps", "cand_last", "events_last",
+              "mass_fix", "quiescent_fix", "S1", "S2", "y_r", "H_top", "hmin", "carry", "w"):
+        assert sg[k] == so[k], (k, sg[k], so[k])
+    # (the negative fix's added mass is summed by atomic FP64 adds in any
+    # order on the GPU: equal up to the last bits)
+    assert abs(sg["clip_mass"] - so["clip_mass"]) <= 1e-12 * max(abs(so["clip_mass"]), 1e-300)
+    for x, y in zip(g.last_events(), o.last_events()):
+        assert np.array_equal(x, y)
+
+
+def _fp32_close_to_oracle(g, o, tol=1e-5):
+    rg, uxg, uyg = g.fields()
+    ro, uxo, uyo = o.fields()
+    assert np.abs(rg - ro).max() / np.abs(ro).max() <= tol
+    occ = o.mask()
+    du = np.hypot(uxg - uxo, uyg - uyo)[occ]
+    uo = np.hypot(uxo, uyo)[occ]
+    assert np.sqrt((du ** 2).sum()) / np.sqrt((uo ** 2).sum()) <= tol
+    assert np.array_equal(g.mask(), o.mask())
+    assert np.array_equal(g.heights(), o.heights())
+    sg, so = g.stats(), o.stats()
+    assert sg["ns_total"] == so["ns_total"] and sg["div_total"] == so["div_total"]
+
+
+def test_fused_fp64_batch_bit_exact_with_the_oracle():
+    """The batched launches in FP64 (their own kernels over the member
+    tables) against the FP64 oracle, member by member, bit for bit: mixed
+    widths 37..256, every growth mode, a moving rear wall."""
+    from paper_2303_02210_gb300.lbm import Batch, Simulation
+    members = [Simulation(p, precision="fp64") for p in ORACLE_MEMBERS]
+    batch = Batch(members)
+    assert batch.fused
+    batch.step(200)
+    for p, g in zip(ORACLE_MEMBERS, members):
+        _bit_exact_with_oracle(g, _oracle_after(p, 200))
+    assert any(m.stats()["y_r"] > 0 for m in members)  # the wall moved somewhere
+    batch.close()
+
+
+def test_fused_fp32_batch_within_tolerance_of_the_oracle():
+    """The batched FP32 launches over 1000 steps at the workloads' growth rate
+    g = 1e-4: every member within 1e-5 of the oracle in density and velocity,
+    no mask or height flips, the same number of divisions. (At g = 3e-3 the
+    carried fraction of n_s integrates the FP32 mass rounding and, after some
+    hundreds of steps, floors to a different n_s: from then on the two runs
+    are different realisations.)"""
+    from paper_2303_02210_gb300.lbm import Batch, Simulation
+    ps = [dict(p, growth_rate=1e-4) for p in ORACLE_MEMBERS]
+    members = [Simulation(p, precision="fp32") for p in ps]
+    batch = Batch(members)
+    assert batch.fused
+    batch.step(1000)
+    for p, g in zip(ps, members):
+        _fp32_close_to_oracle(g, _oracle_after(p, 1000))
+    batch.close()
+
+
+def test_branch_batch_fp64_members_bit_exact_with_the_oracle():
+    """A batch of mixed storage types (one graph branch per member): its FP64
+    members bit for bit with the oracle, its FP32 members within 1e-5."""
+    from paper_2303_02210_gb300.lbm import Batch, Simulation
+    precs = ["fp64", "fp32", "fp64", "fp32", "fp64"]
+    members = [Simulation(p, precision=pr) for p, pr in zip(ORACLE_MEMBERS, precs)]
+    batch = Batch(members)
+    assert not batch.fused
+    batch.step(150)
+    for p, pr, g in zip(ORACLE_MEMBERS, precs, members):
+        o = _oracle_after(p, 150)
+        if pr == "fp64":
+            _bit_exact_with_oracle(g, o)
+        else:
+            _fp32_close_to_oracle(g, o)
+    batch.close()

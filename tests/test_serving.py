@@ -161,3 +161,38 @@ def test_served_results_equal_requests_run_alone_with_batching():
         assert np.array_equal(alone.pops(), r.result["populations"])
         assert np.array_equal(alone.heights(), r.result["heights"])
         alone.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("batching", [False, True])
+def test_served_results_against_the_oracle(batching):
+    """Small requests served together (queueing under a budget, optionally
+    batched) against the FP64 oracle run of each request alone: FP64 requests
+    bit for bit (populations, heights, counters), FP32 requests within 1e-5
+    in density with no mask or height flips and the same divisions."""
+    from oracle.oracle import OracleSim
+    from paper_2303_02210_gb300.lbm import Batch, lbm_footprint
+    trace = wl.serving_trace(8, rate=500.0, steps=(60, 240), seed=11)
+    reqs = []
+    for i, (t, p, n, _) in enumerate(trace):
+        W = 32 * (2 + i % 5)  # 64 .. 192 columns
+        p = dict(p, width=W, height=W // 2, front_row=float(W // 8))
+        reqs.append(serving.Request(params=p, steps=n, arrival=t, precision="fp64" if i % 2 else "fp32",
+                                    keep_populations=True))
+    budget = 3 * max(lbm_footprint(r.params, "fp64") for r in reqs)
+    srv = serving.Server(hbm_budget=budget, chunk=32, batch=Batch if batching else None)
+    srv.run(reqs)
+    for r in reqs:
+        o = OracleSim(r.params)
+        o.step(r.steps)
+        st, so = r.result["stats"], o.stats()
+        assert np.array_equal(r.result["heights"], o.heights())
+        assert st["ns_total"] == so["ns_total"] and st["div_total"] == so["div_total"]
+        if r.precision == "fp64":
+            assert np.array_equal(r.result["populations"], o.pops())
+            assert st["mass_fix"] == so["mass_fix"] and st["carry"] == so["carry"]
+        else:
+            rho_g = r.result["populations"].sum(0)
+            rho_o = o.pops().sum(0)
+            assert np.abs(rho_g - rho_o).max() / np.abs(rho_o).max() <= 1e-5
+        o.close()
