@@ -216,8 +216,30 @@ int lbm_last_events(lbm_sim *sim, int64_t *node, int32_t *pair, int32_t *count, 
 /* Counters and observables after the latest step. Syncs. */
 int lbm_stats(lbm_sim *sim, lbm_stats_t *out);
 
-/* Clears the sticky device status bits. Enqueues only. */
+/* Clears the sticky device status bits, and restarts the planner's grid-
+ * barrier counter and division merge table (which hold nothing between steps;
+ * after a step abandoned on LBM_STATUS_TIMEOUT they may be inconsistent).
+ * Enqueues only. */
 int lbm_clear_status(lbm_sim *sim);
+
+/* Failure-detection test hook (no counterpart in the paper). Every wait in
+ * the kernels is bounded: the TMA-staged update's waits for its bulk copies
+ * and for its warps, and the cooperative planner's grid barriers give up after
+ * a budget of clock cycles (default about two seconds at 2 GHz), raise
+ * LBM_STATUS_TIMEOUT, stop waiting, let the copies already issued land and
+ * return, so that the context stays usable. This call sets, for the steps
+ * that follow on this handle, the budget (budget_cycles > 0; 0 restores the
+ * default) and what is withheld so that a wait must run out:
+ *  withhold bit 0  the TMA-staged update issues no bulk copies (each thread's
+ *                  first wait for a staged tile runs out);
+ *  withhold bit 1  the planner's grid barriers wait for one arrival more than
+ *                  the grid makes (each block's first barrier runs out).
+ * A step run with a bit set is abandoned: its populations, observables and
+ * selection are meaningless. Recover with lbm_debug_waits(sim, 0, 0),
+ * lbm_clear_status and lbm_set_populations. For tests only; not for a
+ * simulation in a batch. Syncs. LBM_ERR_INVALID_ARG for a negative budget or
+ * withhold outside 0..3. */
+int lbm_debug_waits(lbm_sim *sim, int64_t budget_cycles, int32_t withhold);
 
 /* Kernel timing for throughput measurement: while enabled, every launch of
  * the fused update kernel is bracketed by CUDA events on the simulation's
@@ -302,8 +324,13 @@ int lbm_batch_fused(const lbm_batch *batch);
  * LBM_ERR_INVALID_ARG. Every GPU that loads the library keeps that array until
  * the process exits. The first call on each device looks up the array's device
  * address with that device current, so make it before capturing any stream on
- * that device. All calls share the array: calls whose kernels overlap on a GPU
- * race and must be serialised (one stream, or events). Enqueues only. */
+ * that device. Host threads may make first calls concurrently (the lookup is
+ * guarded). The address is kept for the life of the process: after a
+ * cudaDeviceReset of that device it is stale, so do not use this function on
+ * a device that was reset. All calls share the array: calls whose kernels
+ * overlap on a GPU race and must be serialised (one stream, or events); each
+ * call zeroes the array's completion counter on its stream before its kernel.
+ * Enqueues only. */
 #define LBM_NOALLOC_MAX_WIDTH 32768
 int lbm_front_heights_noalloc(const uint32_t *mask_dev, int32_t width, int32_t height, int32_t *heights_dev,
                               double *stats_dev, void *stream);

@@ -445,37 +445,38 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     }
     s->use_tma = false;
     s->tma_grid = nsm;
-    // TMA-staged variant: "tma" 0, "tma1" 1; by the lattice width when the
-    // kernel is chosen (two-row tiles up to 4096 columns, four-row tiles
-    // beyond: measured 81 against 85 us per step at 4096 x 2048 FP32, and
-    // 126 against 132 us per update at 8192 x 2048 the other way round); the
-    // four-row form for a simulation that shares the GPU (5: 15.1 against
-    // 12.5 G node updates/s aggregate for a hundred concurrent requests)
-    // (D2Q7: one form, two-row tiles)
-    s->tma_variant = p->lattice == LBM_D2Q9 && (p->update_kernel == 3 || p->update_kernel == 5 ||
-                                                (p->update_kernel == 0 && p->width > 4096))
-                         ? 1
-                         : 0;
+    // staged update variant (KernelTable::tma_info): "tma" 0 (two-row tiles)
+    // and "tma1" 1 (four-row tiles). Chosen by the lattice width when
+    // automatic (two-row tiles up to 4096 columns, four-row tiles beyond:
+    // measured 81 against 85 us per step at 4096 x 2048 FP32, and 126 against
+    // 132 us per update at 8192 x 2048 the other way round); the four-row form
+    // for a simulation that shares the GPU (5: 15.1 against 12.5 G node
+    // updates/s aggregate for a hundred concurrent requests). D2Q7: one form.
+    const int variant = p->lattice == LBM_D2Q9 && (p->update_kernel == 3 || p->update_kernel == 5 ||
+                                                   (p->update_kernel == 0 && p->width > 4096))
+                            ? 1
+                            : 0;
+    s->tma_variant = variant;
     const bool tma_inject = p->update_kernel != 4; // 4: the selector injects into global memory
-    if (s->kt->tma_update && !p->y_periodic && p->update_kernel != 1) {
-        const int ty = launch_update_tma_rows(s->tma_variant);
-        d.upd_tyl2 = 0;
-        while ((1 << d.upd_tyl2) < ty) ++d.upd_tyl2;
+    int box_rows = 0, iter_rows = 0, ctas_per_sm = 0;
+    const int kind = s->kt->tma_info ? s->kt->tma_info(variant, &box_rows, &iter_rows, &ctas_per_sm) : -1;
+    if (kind >= 0 && s->kt->tma_update && !p->y_periodic && p->update_kernel != 1) {
         bool ok = true;
         for (int b = 0; b < 2 && ok; ++b)
             ok = encode_population_map(&s->maps[b], (char *)d.f[b] - (size_t)kXO * L.elem, d.Wp, d.H, d.P, L.Q,
-                                       kTmaBoxX + 8, ty + 2, p->precision);
+                                       kTmaBoxX + 8, box_rows, p->precision);
         s->use_tma = ok;
         d.inject_in_update = ok && tma_inject ? 1 : 0;
+        const int ty = iter_rows;
+        d.upd_tyl2 = 0;
+        while ((1 << d.upd_tyl2) < ty) ++d.upd_tyl2;
         // persistent CTAs, but no more than one per eight tiles of the whole
         // lattice (small lattices then leave SMs to others in a batch); at
         // least two, since the reciprocal below needs upd_ctas >= 2
         const long long tiles = (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) * ((p->height + ty - 1) / ty);
-        d.upd_ctas = (int)std::max<long long>(
-            2, std::min<long long>(launch_update_tma_ctas(nsm, s->tma_variant), (tiles + 7) / 8));
+        d.upd_ctas = (int)std::max<long long>(2, std::min<long long>((long long)ctas_per_sm * nsm, (tiles + 7) / 8));
         d.upd_magic = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d.upd_ctas - 1) / (uint64_t)d.upd_ctas);
-        if (d.upd_ctas > kTmaMaxCtas ||
-            (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) * ((p->height + ty - 1) / ty) >= (1LL << 22)) {
+        if (d.upd_ctas > kTmaMaxCtas || tiles >= (1LL << 22)) {
             s->use_tma = false;
             d.inject_in_update = 0;
         }
@@ -617,6 +618,26 @@ int lbm_clear_status(lbm_sim *s)
     if (!s) return LBM_ERR_INVALID_ARG;
     USE_DEVICE(s);
     CK(cudaMemsetAsync(&s->d.sc->status, 0, sizeof(int), s->stream));
+    // after a step abandoned on a timeout the planner's grid-barrier counter
+    // may be off a multiple of its grid and its merge table may hold entries
+    // no list points at: both restart (between steps they hold nothing the
+    // next planner needs)
+    CK(cudaMemsetAsync(&s->d.sc->bar_ctr, 0, sizeof(unsigned long long), s->stream));
+    CK(cudaMemsetAsync(s->d.htab, 0xFF, (size_t)s->L.hcap * 8u, s->stream));
+    return LBM_OK;
+}
+
+int lbm_debug_waits(lbm_sim *s, int64_t budget_cycles, int32_t withhold)
+{
+    if (!s || budget_cycles < 0 || withhold < 0 || withhold > 3) return LBM_ERR_INVALID_ARG;
+    USE_DEVICE(s);
+    // stream-ordered, so the kernels of later steps see it (pageable host
+    // values are staged by the copy call itself)
+    const long long b = budget_cycles;
+    const int w = withhold;
+    CK(cudaMemcpyAsync(&s->d.sc->wait_budget, &b, sizeof(b), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&s->d.sc->wait_test, &w, sizeof(w), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
     return LBM_OK;
 }
 

@@ -136,7 +136,16 @@ struct DevScalars {
     // block while the others scan the front
     long long spec_req;
     double spec_carry, spec_kcf;
+    // failure-detection test hooks (lbm_debug_waits): the clock-cycle budget
+    // of every bounded wait (0: the default of about two seconds), and what a
+    // test withholds so that waits run out (WAIT_TEST_* bits)
+    long long wait_budget;
+    int wait_test;
+    int pad2;
 };
+enum { WAIT_TEST_COPIES = 1, WAIT_TEST_BARRIER = 2 };
+// Default budget of the bounded waits: about two seconds at 2 GHz.
+constexpr long long kWaitBudget = 4000000000ll;
 
 // Everything a kernel needs to know about one simulation.
 struct SimDev {
@@ -212,6 +221,9 @@ struct KernelTable {
     // pdl: launch as a programmatic dependent of the preceding kernel.
     cudaError_t (*tma_prepare)(const SimDev &, int variant);
     cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t);
+    // a staged variant's geometry: rows of one bulk copy's box, rows per
+    // tile, CTAs per SM; 0 for a variant the table has, -1 for none
+    int (*tma_info)(int variant, int *box_rows, int *iter_rows, int *ctas_per_sm);
     // One step's kernels for every simulation of a batch in one launch each:
     // ds, the simulations' SimDev in device memory; bm, nb entries (simulation,
     // block, blocks) of the update's (a multiple of each simulation's column
@@ -229,20 +241,15 @@ extern const KernelTable kTableBF16;
 extern const KernelTable kTableF32Q7; // the triangular D2Q7 lattice
 extern const KernelTable kTableF64Q7;
 
-// CTAs the TMA-staged update kernel runs on this many SMs.
-int launch_update_tma_ctas(int nsm, int variant);
-
 // Records a CUDA error for lbm_last_cuda_error and maps it to an LBM_ERR_* code.
 int lbm_record_cuda_error(cudaError_t e);
-// Rows per tile of a TMA-staged update variant.
-int launch_update_tma_rows(int variant);
 // Stored columns left of x = 0 (so that tile boxes start at stored column
 // 128 k, 16-byte aligned for every storage type): x = -1 is the ghost of
 // column W - 1.
 constexpr int kXO = 4;
 constexpr int kTmaBoxX = 128;
 constexpr int kTmaMaxCtas = 1024; // the reciprocal above is exact for tile < 2^22
-constexpr int kBucketCap = 64;     // division records listed per update CTA (more: full scan)
+constexpr int kBucketCap = 256;    // division records listed per update CTA (more: full scan)
 constexpr int kPlanMaxBlocks = 1024;
 
 } // namespace lbm

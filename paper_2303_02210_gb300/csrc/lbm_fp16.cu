@@ -5,7 +5,9 @@
 #include "lbm_update_tma.cuh"
 
 namespace lbm {
-const KernelTable kTableF16 = make_table<__half>(&prepare_update_tma<__half>, &launch_update_tma<__half>);
-const KernelTable kTableBF16 =
-    make_table<__nv_bfloat16>(&prepare_update_tma<__nv_bfloat16>, &launch_update_tma<__nv_bfloat16>);
+const KernelTable kTableF16 =
+    make_table<__half>(&prepare_update_tma<__half>, &launch_update_tma<__half>, &tile_variant_info<__half>);
+const KernelTable kTableBF16 = make_table<__nv_bfloat16>(&prepare_update_tma<__nv_bfloat16>,
+                                                         &launch_update_tma<__nv_bfloat16>,
+                                                         &tile_variant_info<__nv_bfloat16>);
 } // namespace lbm

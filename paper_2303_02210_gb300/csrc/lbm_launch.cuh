@@ -75,13 +75,14 @@ struct Launch {
 template <typename S>
 constexpr KernelTable make_table(cudaError_t (*tma_prepare)(const SimDev &, int) = nullptr,
                                  cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *, int, bool,
-                                                           cudaStream_t) = nullptr)
+                                                           cudaStream_t) = nullptr,
+                                 int (*tma_info)(int, int *, int *, int *) = nullptr)
 {
     return KernelTable{(int)sizeof(S),       &Launch<S>::fill,          &Launch<S>::ghosts,
                        &Launch<S>::scan,     &Launch<S>::plan,          &Launch<S>::inject,
                        &Launch<S>::update,
                        &Launch<S>::fields,   &plan_blocks_per_sm<S>,    &Launch<S>::update_blocks_per_sm,
-                       Launch<S>::UPD_TPB,   tma_prepare,               tma_update,
+                       Launch<S>::UPD_TPB,   tma_prepare,               tma_update,        tma_info,
                        &Launch<S>::batch_inject, &Launch<S>::batch_update, &Launch<S>::batch_plan};
 }
 
@@ -156,13 +157,14 @@ struct Launch7 {
 template <typename S>
 constexpr KernelTable make_table7(cudaError_t (*tma_prepare)(const SimDev &, int) = nullptr,
                                   cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *, int, bool,
-                                                            cudaStream_t) = nullptr)
+                                                            cudaStream_t) = nullptr,
+                                  int (*tma_info)(int, int *, int *, int *) = nullptr)
 {
     return KernelTable{(int)sizeof(S),         &Launch7<S>::fill,          &Launch7<S>::ghosts,
                        &Launch7<S>::scan,      &Launch7<S>::plan,          &Launch7<S>::inject,
                        &Launch7<S>::update,    &Launch7<S>::fields,        &plan_blocks_per_sm<S, Lat7>,
                        &Launch7<S>::update_blocks_per_sm,
-                       Launch7<S>::UPD_TPB,    tma_prepare,                tma_update,
+                       Launch7<S>::UPD_TPB,    tma_prepare,                tma_update,        tma_info,
                        &Launch7<S>::batch_inject, &Launch7<S>::batch_update, &Launch7<S>::batch_plan};
 }
 

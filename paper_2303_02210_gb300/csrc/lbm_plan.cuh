@@ -38,13 +38,13 @@ namespace lbm {
 constexpr int PLAN_NT = 512;
 constexpr int PLAN_WARPS = PLAN_NT / 32;
 constexpr int PLAN_R = 8; // candidates per thread in the first pass
-// a stalled barrier is given up after about two seconds at 2 GHz
-constexpr long long PLAN_WAIT_BUDGET = 4000000000ll;
-
 // Grid barrier on a monotone arrival counter: a block's thread 0 adds one and
 // waits until the counter reaches the next multiple of the grid size (the
-// counter persists across launches, which all use the same grid). The wait
-// is bounded: on timeout ST_TIMEOUT is raised and later barriers no longer wait.
+// counter persists across launches, which all use the same grid; the host
+// zeroes it in lbm_clear_status). The wait is bounded by `budget` clock
+// cycles: on timeout ST_TIMEOUT is raised and later barriers no longer wait.
+// `extra`: arrivals waited for beyond the grid (1 only in the failure-
+// detection test, so that the wait runs out).
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
 {
     unsigned long long v;
@@ -54,7 +54,7 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 
 // (G: the blocks of the grid that plan this simulation; with one block the
 // barrier is the block's own.)
-__device__ __forceinline__ void plan_grid_sync(DevScalars *sc, int *s_dead, int G)
+__device__ __forceinline__ void plan_grid_sync(DevScalars *sc, int *s_dead, int G, long long budget, int extra)
 {
     __syncthreads();
     if (G == 1) return;
@@ -62,11 +62,11 @@ __device__ __forceinline__ void plan_grid_sync(DevScalars *sc, int *s_dead, int 
         __threadfence();
         const unsigned long long g = (unsigned long long)G;
         const unsigned long long old = atomicAdd(&sc->bar_ctr, 1ull);
-        const unsigned long long target = (old / g + 1ull) * g;
+        const unsigned long long target = (old / g + 1ull) * g + (unsigned long long)extra;
         if (!*s_dead) {
             const long long t0 = clock64();
             while (ld_acquire_u64(&sc->bar_ctr) < target) {
-                if (clock64() - t0 > PLAN_WAIT_BUDGET) {
+                if (clock64() - t0 > budget) {
                     *s_dead = 1;
                     atomicOr(&sc->status, ST_TIMEOUT);
                     break;
@@ -216,6 +216,8 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
     const double carry_in = init ? sc->carry : sc->pend_carry;
     const double ratio_in = sc->acc_ratio;
     const bool grow = d.growth_mode != GROW_NONE;
+    const long long wait_budget = sc->wait_budget > 0 ? sc->wait_budget : kWaitBudget;
+    const int wait_extra = (sc->wait_test & WAIT_TEST_BARRIER) ? 1 : 0;
     // what block 0 commits at the end about the step that ran: its pending
     // statistics and the running totals, read before any block may write them
     __shared__ long long s_cm[11];
@@ -319,7 +321,7 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             d.pl_low[blk] = lw;
         }
     }
-    plan_grid_sync(sc, &s_dead, G);
+    plan_grid_sync(sc, &s_dead, G, wait_budget, wait_extra);
 
     // ---- B: Eq. 6 sums, the rear wall, the active mass and the next plan
     // (every block computes the same values from the same partials)
@@ -395,7 +397,7 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
         }
         fm = plan_block_sum(fm, s_ll);
         if (tid == 0) d.pl_mass[blk] = fm;
-        plan_grid_sync(sc, &s_dead, G);
+        plan_grid_sync(sc, &s_dead, G, wait_budget, wait_extra);
         long long a = 0;
         for (int i = tid; i < G; i += PLAN_NT) a += __ldcg(&d.pl_mass[i]);
         frozen = plan_block_sum(a, s_ll);
@@ -410,6 +412,15 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
     }
     __syncthreads();
     const long long mass_fix = mass_acc - frozen;
+    // the window of the coming step (as block 0 commits it below): rows
+    // [nyr, yhi_next) hold all the mass; the window never shrinks
+    int yhi_next;
+    if (d.y_periodic) {
+        yhi_next = d.H;
+    } else {
+        yhi_next = maxmass + 2 < d.H ? maxmass + 2 : d.H;
+        if (!init && y_hi_old > yhi_next) yhi_next = y_hi_old;
+    }
     // proliferation plan (Sec. II): n_s sites, drawn from the active portion
     // restricted by the growth mode
     long long ns_req = 0, ns = 0, kc = 0;
@@ -481,7 +492,7 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             tot_b += t_i;
         }
         if (tid == 0) d.pl_cnt[blk] = tot_b;
-        plan_grid_sync(sc, &s_dead, G);
+        plan_grid_sync(sc, &s_dead, G, wait_budget, wait_extra);
         long long before = 0, total = 0;
         for (int i = tid; i < G; i += PLAN_NT) {
             const long long c = __ldcg(&d.pl_cnt[i]);
@@ -517,7 +528,7 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             const int pr = plan_block_exscan(a ? 1 : 0, &tot_r, s_i);
             int *cnt = d.pl_cnt + (round & 1) * kPlanMaxBlocks;
             if (tid == 0) cnt[blk] = tot_r;
-            plan_grid_sync(sc, &s_dead, G);
+            plan_grid_sync(sc, &s_dead, G, wait_budget, wait_extra);
             long long bf = 0, tt = 0;
             for (int i = tid; i < G; i += PLAN_NT) {
                 const long long c = __ldcg(&cnt[i]);
@@ -573,13 +584,7 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
         sc->hmin = lowa;
         sc->mass_fix = mass_fix;
         sc->quiescent_fix = qfix + frozen;
-        int yhi;
-        if (d.y_periodic) {
-            yhi = d.H;
-        } else {
-            yhi = maxmass + 2 < d.H ? maxmass + 2 : d.H;
-            if (!init && y_hi_old > yhi) yhi = y_hi_old; // the window never shrinks
-        }
+        const int yhi = yhi_next;
         sc->y_copy = y_r;
         sc->y_r = nyr;
         sc->y_hi = yhi;

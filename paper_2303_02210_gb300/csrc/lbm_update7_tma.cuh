@@ -185,6 +185,10 @@ __global__ void __launch_bounds__(Tma7Geom<TY>::NT, CTAS)
     __syncthreads();
     grid_dependency_wait();
     const uint32_t t = (uint32_t)d.sc->step;
+    // bounded waits: the budget (a failure-detection test shortens it and may
+    // withhold the bulk copies, so that the first wait of every thread runs out)
+    const long long budget = d.sc->wait_budget > 0 ? d.sc->wait_budget : kWaitBudget;
+    const bool withhold = (d.sc->wait_test & WAIT_TEST_COPIES) != 0;
     const int cur = (int)(t & 1u);
     const CUtensorMap *tm = cur ? &tm1 : &tm0;
     const float *__restrict__ fin = (const float *)d.f[cur];
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(Tma7Geom<TY>::NT, CTAS)
         }
     };
     // the first tiles' copies run while the divisions are sorted out below
-    if (tid == 0)
+    if (tid == 0 && !withhold)
         while (issued < STAGES && issued < count) issue();
 
     // App. A step 3 for this CTA, as in k_update_tma: the records of its
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(Tma7Geom<TY>::NT, CTAS)
         return (float)((double)d.ev_count[(size_t)(t & 1u) * (size_t)d.ns_max + (size_t)e] * d.half_cell);
     };
     const int mine = nev_all > 0 ? d.bucket_cnt[blockIdx.x] : 0;
-    if (mine <= kBucketCap) {
+    if (mine <= TMA_EV_CAP) { // (the bucket holds kBucketCap >= TMA_EV_CAP records)
         for (int j = tid; j < mine; j += NT) {
             const int e = d.bucket[blockIdx.x * kBucketCap + j];
             const int k = d.rec_k[e];
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(Tma7Geom<TY>::NT, CTAS)
         const uint32_t parity = (uint32_t)((k / STAGES) & 1);
         const int x0 = tx * TMA_TX, y0 = y_r + ty * TY;
         float *stage = s_in + s * G::STRIDE;
-        if (!dead && !mbar_wait_bounded(&full[s], parity, TMA_WAIT_BUDGET)) {
+        if (!dead && !mbar_wait_bounded(&full[s], parity, budget)) {
             dead = true;
             atomicOr(&s_abort, 1);
         }
@@ -323,8 +327,8 @@ __global__ void __launch_bounds__(Tma7Geom<TY>::NT, CTAS)
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        if (tid == 0 && issued < count) {
-            if (!dead && !mbar_wait_bounded(&empty[s], parity, TMA_WAIT_BUDGET)) {
+        if (tid == 0 && issued < count && !withhold) {
+            if (!dead && !mbar_wait_bounded(&empty[s], parity, budget)) {
                 dead = true;
                 atomicOr(&s_abort, 1);
             }
@@ -443,7 +447,7 @@ __global__ void __launch_bounds__(Tma7Geom<TY>::NT, CTAS)
         atomicOr(&d.sc->status, ST_TIMEOUT);
         // let the copies still in flight land before the CTA exits
         for (int k = issued - STAGES > 0 ? issued - STAGES : 0; k < issued; ++k)
-            mbar_wait_bounded(&full[k % STAGES], (uint32_t)((k / STAGES) & 1), TMA_WAIT_BUDGET);
+            mbar_wait_bounded(&full[k % STAGES], (uint32_t)((k / STAGES) & 1), kWaitBudget);
     }
     mass = warp_sum_ll(mass);
     maxrow = warp_max_i(maxrow);

@@ -33,6 +33,7 @@
 #include <type_traits>
 
 #include "lbm_kernels.cuh"
+#include "lbm_pair.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {
@@ -43,9 +44,6 @@ constexpr int TMA_LX = TMA_TX + 8; // staged columns x0 - 4 .. x0 + 131
 // per tile); tiles flagged per CTA.
 constexpr int TMA_EV_CAP = 128;
 constexpr int TMA_KFLAG_WORDS = 32;
-static_assert(kBucketCap <= TMA_EV_CAP, "a full bucket fits in shared memory");
-// a stalled copy is given up after about two seconds at 2 GHz
-constexpr long long TMA_WAIT_BUDGET = 4000000000ll;
 static_assert(kXO % 4 == 0, "tile boxes start on 16-byte boundaries");
 
 template <typename S, int TY>
@@ -109,6 +107,72 @@ __device__ __forceinline__ typename Pair2<S>::T enc_pair(float a, float b, int q
         return __floats2half2_rn(a - pc.shift(q), b - pc.shift(q));
     } else {
         return __floats2bfloat162_rn(a - pc.shift(q), b - pc.shift(q));
+    }
+}
+
+// Decodes a stored pair of plane class q to FP32 (16-bit storage: one packed
+// conversion and one packed add of the shift; per element exactly Pop::ld).
+template <typename S>
+__device__ __forceinline__ float2 dec_pair(typename Pair2<S>::T v, int q, const Pop<S> &pc)
+{
+    if constexpr (sizeof(S) == 4) {
+        return v;
+    } else if constexpr (std::is_same<S, __half>::value) {
+        return add2(__half22float2(v), f2(pc.shift(q)));
+    } else {
+        return add2(__bfloat1622float2(v), f2(pc.shift(q)));
+    }
+}
+
+// Encodes a pair of plane q (per element exactly Pop::st).
+template <typename S>
+__device__ __forceinline__ typename Pair2<S>::T enc_pair2(float2 f, int q, const Pop<S> &pc)
+{
+    if constexpr (sizeof(S) == 4) {
+        return f;
+    } else if constexpr (std::is_same<S, __half>::value) {
+        return __float22half2_rn(sub2(f, f2(pc.shift(q))));
+    } else {
+        return __float22bfloat162_rn(sub2(f, f2(pc.shift(q))));
+    }
+}
+
+// pull2 for a pair held as float2 per direction (the .x node and the .y node).
+template <typename S, int PLANE, bool REAR, bool TOP>
+__device__ __forceinline__ void pull2p(const S *b, float2 g[NQ], const Pop<S> &pc)
+{
+    using P2 = typename Pair2<S>::T;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        const bool own = (ey(i) == 1 && REAR) || (ey(i) == -1 && TOP);
+        P2 v;
+        if (own) {
+            v = *reinterpret_cast<const P2 *>(b + opp(i) * PLANE);
+        } else if (ex(i) == 0) {
+            v = *reinterpret_cast<const P2 *>(b + i * PLANE - ey(i) * TMA_LX);
+        } else {
+            const S *p = b + i * PLANE - ey(i) * TMA_LX - ex(i);
+            v.x = p[0];
+            v.y = p[1];
+        }
+        g[i] = dec_pair<S>(v, i, pc);
+    }
+}
+
+// Stores a node pair from float2 populations; with 16-bit storage m is the
+// pair's mass as stored (the decoded stored values summed in index order).
+template <typename S>
+__device__ __forceinline__ void store_pair(S *o, long long P, const float2 f[NQ], const Pop<S> &pc, float2 &m)
+{
+    using P2 = typename Pair2<S>::T;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        const P2 v = enc_pair2<S>(f[i], i, pc);
+        *reinterpret_cast<P2 *>(o + i * P) = v;
+        if constexpr (Pop<S>::kShifted) {
+            const float2 dv = dec_pair<S>(v, i, pc);
+            m = i == 0 ? dv : add2(m, dv);
+        }
     }
 }
 
@@ -224,6 +288,10 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
     // step t (read from the device, so a captured step replays as is) pulls
     // from copy t & 1 (tensor map tm0 or tm1) and writes the other
     const uint32_t t = (uint32_t)d.sc->step;
+    // bounded waits: the budget (a failure-detection test shortens it and may
+    // withhold the bulk copies, so that the first wait of every thread runs out)
+    const long long budget = d.sc->wait_budget > 0 ? d.sc->wait_budget : kWaitBudget;
+    const bool withhold = (d.sc->wait_test & WAIT_TEST_COPIES) != 0;
     const int cur = (int)(t & 1u);
     const CUtensorMap *tm = cur ? &tm1 : &tm0;
     const S *__restrict__ fin = (const S *)d.f[cur];
@@ -264,7 +332,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
         }
     };
     // the first tiles' copies run while the divisions are sorted out below
-    if (tid == 0)
+    if (tid == 0 && !withhold)
         while (issued < STAGES && issued < count) issue();
 
     // App. A step 3 for this CTA: the planner wrote one record per division
@@ -280,7 +348,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
         return (float)((double)d.ev_count[(size_t)(t & 1u) * (size_t)d.ns_max + (size_t)e] * d.half_cell);
     };
     const int mine = nev_all > 0 ? d.bucket_cnt[blockIdx.x] : 0;
-    if (mine <= kBucketCap) {
+    if (mine <= TMA_EV_CAP) { // (the bucket holds kBucketCap >= TMA_EV_CAP records)
         for (int j = tid; j < mine; j += NT) {
             const int e = d.bucket[blockIdx.x * kBucketCap + j];
             const int k = d.rec_k[e];
@@ -336,7 +404,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
         const uint32_t parity = (uint32_t)((k / STAGES) & 1);
         const int x0 = tx * TMA_TX, y0 = y_r + ty * TY;
         S *stage = s_in + s * G::STRIDE;
-        if (!dead && !mbar_wait_bounded(&full[s], parity, TMA_WAIT_BUDGET)) {
+        if (!dead && !mbar_wait_bounded(&full[s], parity, budget)) {
             dead = true;
             atomicOr(&s_abort, 1);
         }
@@ -369,27 +437,27 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
         // active window hold no mass and are skipped; warp-uniform)
         const int y = y0 + row;
         const bool active = y < y_hi;
-        float ga[NQ], gb[NQ];
+        float2 g2[NQ]; // (first node, second node) per direction
         if (active) {
             const S *b = stage + (row + 1) * TMA_LX + cl + 4;
             const bool rear = y - 1 < y_r, top = y + 1 >= H; // half-way bounce-back walls
             if (!rear && !top)
-                pull2<S, PLANE, false, false>(b, ga, gb, pc);
+                pull2p<S, PLANE, false, false>(b, g2, pc);
             else if (!top)
-                pull2<S, PLANE, true, false>(b, ga, gb, pc);
+                pull2p<S, PLANE, true, false>(b, g2, pc);
             else if (!rear)
-                pull2<S, PLANE, false, true>(b, ga, gb, pc);
+                pull2p<S, PLANE, false, true>(b, g2, pc);
             else
-                pull2<S, PLANE, true, true>(b, ga, gb, pc);
+                pull2p<S, PLANE, true, true>(b, g2, pc);
         }
         // the stage may be refilled (by the async proxy) once every warp has
         // arrived: order this thread's shared-memory reads before that
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        if (tid == 0 && issued < count) {
+        if (tid == 0 && issued < count && !withhold) {
             // refill this stage once every warp has its values
-            if (!dead && !mbar_wait_bounded(&empty[s], parity, TMA_WAIT_BUDGET)) {
+            if (!dead && !mbar_wait_bounded(&empty[s], parity, budget)) {
                 dead = true;
                 atomicOr(&s_abort, 1);
             }
@@ -398,49 +466,61 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
         if (active) {
             const int x = x0 + cl;
             const bool oka = x < W, okb = x + 1 < W;
-            float rhoa = ga[0], rhob = gb[0];
-#pragma unroll
-            for (int i = 1; i < NQ; ++i) {
-                rhoa = rhoa + ga[i];
-                rhob = rhob + gb[i];
-            }
+            // Eq. 1 density of both nodes (index order)
+            const float2 rho2 = rho_pair(g2);
+            const float rhoa = rho2.x, rhob = rho2.y;
             const bool occa = oka && rhoa >= rho_c, occb = okb && rhob >= rho_c;
             if (__all_sync(0xffffffffu, occa && occb)) {
-                // the bulk: all 64 nodes of the warp's segment are occupied
+                // the bulk: all 64 nodes of the warp's segment are occupied;
+                // both nodes at once in packed FP32 (lbm_pair.cuh)
                 const uint32_t n = (uint32_t)(y * W + x);
-                float fa[NQ], fb[NQ];
-                relax_words<float, NOISE>(ga, rhoa, fa, NOISE ? noise_block(n, t, d) : u32x4{0u, 0u, 0u, 0u}, cf);
-                relax_words<float, NOISE>(gb, rhob, fb, NOISE ? noise_block(n + 1u, t, d) : u32x4{0u, 0u, 0u, 0u},
-                                          cf);
-                float mn = fminf(fa[0], fb[0]);
+                const u32x4 wa = NOISE ? noise_block(n, t, d) : u32x4{0u, 0u, 0u, 0u};
+                const u32x4 wb = NOISE ? noise_block(n + 1u, t, d) : u32x4{0u, 0u, 0u, 0u};
+                float2 f2o[NQ];
+                relax_pair<NOISE>(g2, rho2, f2o, wa, wb, cf);
+                float mn = fminf(f2o[0].x, f2o[0].y);
 #pragma unroll
-                for (int i = 1; i < NQ; ++i) mn = fminf(mn, fminf(fa[i], fb[i]));
+                for (int i = 1; i < NQ; ++i) mn = fminf(mn, fminf(f2o[i].x, f2o[i].y));
                 float adda = 0.0f, addb = 0.0f;
                 if (__any_sync(0xffffffffu, mn < 0.0f)) {
+                    float fa[NQ], fb[NQ];
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) {
+                        fa[i] = f2o[i].x;
+                        fb[i] = f2o[i].y;
+                    }
                     adda = fix_negative<float>(fa, negfix);
                     addb = fix_negative<float>(fb, negfix);
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) f2o[i] = make_float2(fa[i], fb[i]);
                     clip += adda + addb;
                 }
                 if ((lane & 15) == 0) d.mask[(long long)y * d.MW + (x0 >> 5) + 2 * half + (lane >> 4)] = 0xffffffffu;
                 S *o = fout + (long long)y * Wp + x;
-                float ma, mb;
-                store_nodes<S>(o, P, fa, fb, true, pc, ma, mb);
+                float2 m2 = f2(0.0f);
+                store_pair<S>(o, P, f2o, pc, m2);
                 const int xw = x0 + 64 * half; // first column of the warp
                 if (xw == 0 || xw + 63 == W - 1) { // a warp at the lattice edge: ghost copies
                     if (x == 0) {
 #pragma unroll
-                        for (int i = 0; i < NQ; ++i) o[i * P + W] = pc.st(fa[i], i);
+                        for (int i = 0; i < NQ; ++i) o[i * P + W] = pc.st(f2o[i].x, i);
                     }
                     if (x + 1 == W - 1) {
 #pragma unroll
-                        for (int i = 0; i < NQ; ++i) o[i * P + 1 - W] = pc.st(fb[i], i);
+                        for (int i = 0; i < NQ; ++i) o[i * P + 1 - W] = pc.st(f2o[i].y, i);
                     }
                 }
-                const float roa = Pop<S>::kShifted ? ma : rhoa + adda;
-                const float rob = Pop<S>::kShifted ? mb : rhob + addb;
+                const float roa = Pop<S>::kShifted ? m2.x : rhoa + adda;
+                const float rob = Pop<S>::kShifted ? m2.y : rhob + addb;
                 mass += fix24<float>(roa) + fix24<float>(rob);
                 if (roa != 0.0f || rob != 0.0f) maxrow = y;
             } else {
+                float ga[NQ], gb[NQ];
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) {
+                    ga[i] = g2[i].x;
+                    gb[i] = g2[i].y;
+                }
                 u32x4 wa{0u, 0u, 0u, 0u}, wb{0u, 0u, 0u, 0u};
                 if (NOISE && (occa || occb)) {
                     const uint32_t n = (uint32_t)(y * W + x);
@@ -503,7 +583,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
         atomicOr(&d.sc->status, ST_TIMEOUT);
         // let the copies still in flight land before the CTA exits
         for (int k = issued - STAGES > 0 ? issued - STAGES : 0; k < issued; ++k)
-            mbar_wait_bounded(&full[k % STAGES], (uint32_t)((k / STAGES) & 1), TMA_WAIT_BUDGET);
+            mbar_wait_bounded(&full[k % STAGES], (uint32_t)((k / STAGES) & 1), kWaitBudget);
     }
     mass = warp_sum_ll(mass);
     maxrow = warp_max_i(maxrow);
@@ -577,6 +657,18 @@ cudaError_t launch_update_tma(const SimDev &d, const CUtensorMap *maps, int vari
                           : launch_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, false>(d, maps, pdl, s);
     return d.noise_on ? launch_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, true>(d, maps, pdl, s)
                       : launch_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, false>(d, maps, pdl, s);
+}
+
+// Geometry of a variant for the host: rows of one bulk copy's box, rows per
+// tile, CTAs per SM; 0 for a variant of this kernel, -1 for none.
+template <typename S>
+int tile_variant_info(int variant, int *box_rows, int *iter_rows, int *ctas_per_sm)
+{
+    if (variant != 0 && variant != 1) return -1;
+    *iter_rows = variant == 1 ? TmaCfg<S>::TY1 : TmaCfg<S>::TY0;
+    *box_rows = *iter_rows + 2;
+    *ctas_per_sm = variant == 1 ? TmaCfg<S>::CTAS1 : TmaCfg<S>::CTAS0;
+    return 0;
 }
 
 } // namespace lbm

@@ -95,6 +95,7 @@ _SIGNATURES = {
     "lbm_last_events": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
     "lbm_stats": (ctypes.c_int, [_P, ctypes.POINTER(lbm_stats_t)]),
     "lbm_clear_status": (ctypes.c_int, [_P]),
+    "lbm_debug_waits": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32]),
     "lbm_timing_enable": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbm_timing_read": (ctypes.c_int, [_P, _P, _P, _P]),
     "lbm_timing_stride": (ctypes.c_int, [_P, ctypes.c_int64]),
@@ -343,6 +344,12 @@ class Simulation:
 
     def lbm_clear_status(self):
         _check(self._lib.lbm_clear_status(self._h), "lbm_clear_status")
+
+    def lbm_debug_waits(self, budget_cycles: int = 0, withhold: int = 0):
+        """Failure-detection test hook: wait budget in clock cycles (0: the
+        default) and what is withheld (bit 0 bulk copies, bit 1 one grid-
+        barrier arrival) so that the bounded waits run out."""
+        _check(self._lib.lbm_debug_waits(self._h, int(budget_cycles), int(withhold)), "lbm_debug_waits")
 
     def lbm_timing_enable(self, max_launches: int):
         _check(self._lib.lbm_timing_enable(self._h, int(max_launches)), "lbm_timing_enable")

@@ -122,7 +122,12 @@ def test_update_kernel_choices_validate():
     for uk, ok64 in (("auto", True), ("plain", True), ("tma", False), ("tma1", False), ("shared", True)):
         q = lbm.make_params(p, "fp64", uk)
         assert (lbm.load_library().lbm_validate(ctypes.byref(q)) == 0) == ok64, uk
+        q = lbm.make_params(p, "fp32", uk)
+        assert lbm.load_library().lbm_validate(ctypes.byref(q)) == 0, uk
     q = lbm.make_params(p, "fp32", 6)
+    assert lbm.load_library().lbm_validate(ctypes.byref(q)) == -1
+    # the staged kernels need walls in y
+    q = lbm.make_params(dict(p, y_periodic=1), "fp32", "tma")
     assert lbm.load_library().lbm_validate(ctypes.byref(q)) == -1
 
 

@@ -129,7 +129,7 @@ def test_tma_bit_exact_with_plain_kernel(name):
     p = TMA_CASES[name]
     a = gpu_sim(p, "fp32", "plain")
     b = gpu_sim(p, "fp32", "tma")
-    assert a.stats()["update_kernel"] == 1 and b.stats()["update_kernel"] == 2
+    assert a.stats()["update_kernel"] == 1 and b.stats()["update_kernel"] >= 2
     for chunk in (1, 9, 90, 200):
         a.step(chunk)
         b.step(chunk)
@@ -155,7 +155,7 @@ def test_tma_full_size_repeatable_on_reused_memory():
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         b = gpu_sim(p, "fp32", "tma")
-        assert b.stats()["update_kernel"] == 2
+        assert b.stats()["update_kernel"] >= 2
         b.step(3)
         fb = b.pops()
         del b

@@ -121,13 +121,17 @@ TMA16_CASES = {
 }
 
 
+@pytest.mark.parametrize("kernel", ["tma", "tma1"])
 @pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("name", sorted(TMA16_CASES))
-def test_tma_bit_exact_with_plain(name, precision):
+def test_tma_bit_exact_with_plain(name, precision, kernel):
+    """Both forms of the TMA-staged kernel (two-row and four-row tiles; the
+    bulk's node pairs in packed FP32) against the plain-load kernel, bit for
+    bit."""
     p = TMA16_CASES[name]
     a = sim(p, precision, "plain")
-    b = sim(p, precision, "tma1" if name == "edge_full_width" else "tma")
-    assert a.stats()["update_kernel"] == 1 and b.stats()["update_kernel"] == 2
+    b = sim(p, precision, kernel)
+    assert a.stats()["update_kernel"] == 1 and b.stats()["update_kernel"] >= 2
     for chunk in (1, 9, 90, 200):
         a.step(chunk)
         b.step(chunk)
@@ -188,7 +192,7 @@ def test_one_step_full_size_edge_workload(precision):
     TMA-staged kernel): one step from the 16-bit initial state."""
     p = wl.lattice_edge(seed=1)
     g, o = _one_step(p, precision, 0)
-    assert g.stats()["update_kernel"] == 2
+    assert g.stats()["update_kernel"] >= 2
     fg, fo = g.pops(), o.pops()
     c = shifts(p, precision)
     bound, div = one_step_bound(o, p, c, MANTISSA[precision])

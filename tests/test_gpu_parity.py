@@ -134,15 +134,17 @@ def test_maximum_extents(name, precision):
         return
     from paper_2303_02210_gb300.lbm import Simulation
     a = Simulation(p, precision="fp32", update_kernel="plain")
-    b = Simulation(p, precision="fp32")
     a.step(6)
-    b.step(6)
-    assert b.stats()["update_kernel"] == 2
-    assert np.array_equal(a.pops(), b.pops())
-    e_rho, e_u = field_errors(b, o)
-    assert e_rho <= RTOL_FP32 and e_u <= RTOL_FP32
-    assert np.array_equal(b.mask(), o.mask())
-    assert b.stats()["ns_total"] == o.stats()["ns_total"]
+    for kernel in ("auto",):
+        b = Simulation(p, precision="fp32", update_kernel=kernel)
+        b.step(6)
+        assert b.stats()["update_kernel"] >= 2
+        assert np.array_equal(a.pops(), b.pops()), kernel
+        e_rho, e_u = field_errors(b, o)
+        assert e_rho <= RTOL_FP32 and e_u <= RTOL_FP32
+        assert np.array_equal(b.mask(), o.mask())
+        assert b.stats()["ns_total"] == o.stats()["ns_total"]
+        b.close()
 
 
 def test_fp64_set_populations_matches_oracle():
@@ -241,14 +243,15 @@ TMA_CASES["ragged_300"] = wl.lattice_small(seed=22, width=300, height=70, front_
 @pytest.mark.parametrize("name", sorted(TMA_CASES))
 def test_fp32_tma_kernel_bit_exact_with_plain_kernel(name, kernel):
     """The TMA-staged FP32 update moves data differently (bulk tensor tiles
-    with halos, zero-filled edges, patched x-wrap, clipped stores) but runs
-    the same arithmetic as the plain-load FP32 kernel: every population,
-    mask bit, height and counter must agree bit for bit."""
+    with halos, ghost columns, divisions added to staged slots, clipped
+    stores) and computes the bulk's node pairs with packed FP32 instructions,
+    but runs the same IEEE operations as the plain-load FP32 kernel: every
+    population, mask bit, height and counter must agree bit for bit."""
     p = TMA_CASES[name]
     from paper_2303_02210_gb300.lbm import Simulation
     a = Simulation(p, precision="fp32", update_kernel="plain")
     b = Simulation(p, precision="fp32", update_kernel=kernel)
-    assert a.stats()["update_kernel"] == 1 and b.stats()["update_kernel"] == 2
+    assert a.stats()["update_kernel"] == 1 and b.stats()["update_kernel"] >= 2
     for chunk in (1, 9, 90, 200):
         a.step(chunk)
         b.step(chunk)
@@ -260,7 +263,8 @@ def test_fp32_tma_kernel_bit_exact_with_plain_kernel(name, kernel):
         assert np.array_equal(a.heights(), b.heights())
 
 
-def test_fp32_tma_repeatable_on_reused_memory():
+@pytest.mark.parametrize("kernel", ["tma"])
+def test_fp32_tma_repeatable_on_reused_memory(kernel):
     """The TMA-staged update refills a shared-memory stage as soon as every
     warp holds its values; a refill that overtakes a pending shared-memory
     read would corrupt one warp's nodes now and then, depending on timing and
@@ -277,7 +281,7 @@ def test_fp32_tma_repeatable_on_reused_memory():
     for trial in range(8):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        b = Simulation(p, precision="fp32", update_kernel="tma")
+        b = Simulation(p, precision="fp32", update_kernel=kernel)
         b.step(3)
         fb = b.pops()
         del b
