@@ -100,7 +100,7 @@ def measured_peak():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("lbm_kernels.cuh", "lbm_common.cuh", "lbm_update_tma.cuh", "lbm_tma.cuh"):
+    for f in ("lbm_kernels.cuh", "lbm_common.cuh", "lbm_update_tma.cuh", "lbm_tma.cuh", "lbm_pair.cuh"):
         with open(os.path.join(ROOT, "paper_2303_02210_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -78,14 +78,19 @@ enum { LBM_D2Q9 = 0, LBM_D2Q7 = 1 };
  *               and for f_i = c_i), FP32 arithmetic, 36 bytes per node
  *               update
  *  update_kernel 0: choose (the TMA-staged kernel for FP32 and 16-bit
- *               storage with walls in y, else the plain-load kernel; its
- *               two-row form up to 4096 columns, the four-row form beyond);
+ *               storage with walls in y, else the plain-load kernel; for
+ *               FP32 its bulk-store form (6) from 2048 columns on when W is
+ *               a multiple of 4, else its two-row form up to 4096 columns and
+ *               the four-row form beyond);
  *               1: plain-load kernel; 2: TMA-staged kernel, two-row form;
  *               3: TMA-staged kernel, four-row form (2-4: not FP64, and
  *               y_periodic = 0 only); 4: the two-row form with the
  *               divisions injected into global memory first; 5: choose for
  *               a simulation that shares the GPU with others (the four-row
- *               form where the TMA-staged kernel applies)
+ *               form where the TMA-staged kernel applies); 6: the two-row form
+ *               whose results leave through a shared output tile and one
+ *               bulk tensor store per tile (FP32 only; widths that are not
+ *               a multiple of 4 take form 2)
  *  lattice      LBM_D2Q9, or LBM_D2Q7: the paper's triangular lattice (Sec.
  *               II; Eq. 3 with 4, 8, 2, weights 1/2 and 1/12), rows of nodes
  *               along x with the odd rows shifted by half a spacing, rows

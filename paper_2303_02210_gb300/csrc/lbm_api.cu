@@ -199,11 +199,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// Population copy as a 3-D tensor {Wp, H, Q} of whole stored rows
-// (coordinate x_stored = x + kXO, so the ghost columns are inside) with row
+// Population copy as a 3-D tensor {nx, H, Q} of stored rows (coordinate
+// x_stored = x + kXO, so the ghost columns are inside when nx = Wp) with row
 // pitch Wp and plane pitch P elements; `bx` x `by` x Q boxes. Out-of-range
-// loads read zeros.
-bool encode_population_map(CUtensorMap *m, void *base, int Wp, int H, long long P, int Q, int bx, int by,
+// loads read zeros; stores are cut at the tensor's edges (nx = W + kXO cuts
+// them at x = W - 1).
+bool encode_population_map(CUtensorMap *m, void *base, int nx, int Wp, int H, long long P, int Q, int bx, int by,
                            int precision)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -212,7 +213,7 @@ bool encode_population_map(CUtensorMap *m, void *base, int Wp, int H, long long 
     const CUtensorMapDataType dt = precision == LBM_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : precision == LBM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const cuuint64_t dims[3] = {(cuuint64_t)Wp, (cuuint64_t)H, (cuuint64_t)Q};
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)H, (cuuint64_t)Q};
     const cuuint64_t strides[2] = {(cuuint64_t)Wp * el, (cuuint64_t)P * el};
     const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)Q};
     const cuuint32_t estr[3] = {1, 1, 1};
@@ -240,7 +241,7 @@ struct lbm_sim {
     // TMA-staged update (FP32, walls in y)
     bool use_tma;
     int tma_grid, tma_variant;
-    CUtensorMap maps[2];
+    CUtensorMap maps[4]; // loads from copy 0, 1; stores into copy 0, 1 (variants that store in bulk)
     // kernel timing
     std::vector<cudaEvent_t> ev;
     int64_t ev_used;
@@ -271,15 +272,17 @@ int lbm_validate(const lbm_params_t *p)
     if (p->negfix_mode != LBM_NEGFIX_LITERAL && p->negfix_mode != LBM_NEGFIX_RESCALE) return LBM_ERR_INVALID_ARG;
     if (p->precision < LBM_FP32 || p->precision > LBM_BF16) return LBM_ERR_INVALID_ARG;
     if (p->y_periodic != 0 && p->y_periodic != 1) return LBM_ERR_INVALID_ARG;
-    if (p->update_kernel < 0 || p->update_kernel > 5) return LBM_ERR_INVALID_ARG;
-    if (p->update_kernel >= 2 && p->update_kernel <= 4 && (p->precision == LBM_FP64 || p->y_periodic))
+    if (p->update_kernel < 0 || p->update_kernel > 6) return LBM_ERR_INVALID_ARG;
+    if (p->update_kernel >= 2 && p->update_kernel != 5 && (p->precision == LBM_FP64 || p->y_periodic))
         return LBM_ERR_INVALID_ARG;
+    // bulk tensor stores: FP32 only (16-bit tiles start off a 16-byte boundary)
+    if (p->update_kernel == 6 && p->precision != LBM_FP32) return LBM_ERR_INVALID_ARG;
     if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D2Q7) return LBM_ERR_INVALID_ARG;
     // D2Q7: FP32 or FP64 storage, the plain-load or the (one) TMA-staged
     // update, an even H when periodic in y
     if (p->lattice == LBM_D2Q7 &&
         ((p->precision != LBM_FP32 && p->precision != LBM_FP64) || p->update_kernel == 3 || p->update_kernel == 4 ||
-         (p->y_periodic && (p->height & 1))))
+         p->update_kernel == 6 || (p->y_periodic && (p->height & 1))))
         return LBM_ERR_INVALID_ARG;
     return LBM_OK;
 }
@@ -445,17 +448,30 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     }
     s->use_tma = false;
     s->tma_grid = nsm;
-    // staged update variant (KernelTable::tma_info): "tma" 0 (two-row tiles)
-    // and "tma1" 1 (four-row tiles). Chosen by the lattice width when
-    // automatic (two-row tiles up to 4096 columns, four-row tiles beyond:
-    // measured 81 against 85 us per step at 4096 x 2048 FP32, and 126 against
-    // 132 us per update at 8192 x 2048 the other way round); the four-row form
-    // for a simulation that shares the GPU (5: 15.1 against 12.5 G node
-    // updates/s aggregate for a hundred concurrent requests). D2Q7: one form.
-    const int variant = p->lattice == LBM_D2Q9 && (p->update_kernel == 3 || p->update_kernel == 5 ||
-                                                   (p->update_kernel == 0 && p->width > 4096))
-                            ? 1
-                            : 0;
+    // staged update variant (KernelTable::tma_info): "tma" 0 (two-row tiles),
+    // "tma1" 1 (four-row tiles), "tma_st" 2 (two-row tiles stored in bulk,
+    // FP32). Automatic: the bulk-store form for FP32 from 2048 columns on
+    // (measured per update launch: 57.3 against 62.7 us at 4096 x 2048, 115
+    // against 124 (four-row tiles) at 8192 x 2048, 32.7 against 33.9 at
+    // 2048), two-row tiles below (19.1 against 21.1 us at 1024, where the
+    // window stays in the L2) and for 16-bit storage up to 4096 columns,
+    // four-row tiles beyond; the four-row form for a simulation that shares
+    // the GPU (5: 15.1 against 12.5 G node updates/s aggregate for a hundred
+    // concurrent requests). D2Q7: one form.
+    // The bulk-store form cuts its stores at x = W - 1, and a bulk store
+    // writes the 16-byte unit that holds its last column whole: with W + 4
+    // not a multiple of 4 elements that would overwrite the ghost column
+    // x = W, so such widths keep the per-lane stores.
+    const bool bulk_ok = p->precision == LBM_FP32 && p->width % 4 == 0;
+    int variant = 0;
+    if (p->lattice == LBM_D2Q9) {
+        if (p->update_kernel == 3 || p->update_kernel == 5)
+            variant = 1;
+        else if (p->update_kernel == 6)
+            variant = bulk_ok ? 2 : 0;
+        else if (p->update_kernel == 0)
+            variant = bulk_ok && p->width >= 2048 ? 2 : (p->width > 4096 ? 1 : 0);
+    }
     s->tma_variant = variant;
     const bool tma_inject = p->update_kernel != 4; // 4: the selector injects into global memory
     int box_rows = 0, iter_rows = 0, ctas_per_sm = 0;
@@ -463,8 +479,13 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     if (kind >= 0 && s->kt->tma_update && !p->y_periodic && p->update_kernel != 1) {
         bool ok = true;
         for (int b = 0; b < 2 && ok; ++b)
-            ok = encode_population_map(&s->maps[b], (char *)d.f[b] - (size_t)kXO * L.elem, d.Wp, d.H, d.P, L.Q,
+            ok = encode_population_map(&s->maps[b], (char *)d.f[b] - (size_t)kXO * L.elem, d.Wp, d.Wp, d.H, d.P, L.Q,
                                        kTmaBoxX + 8, box_rows, p->precision);
+        // bulk stores of a tile's 128 columns, cut at x = W - 1 (the ghost
+        // columns are written by the edge lanes)
+        for (int b = 0; b < 2 && ok && kind == 1; ++b)
+            ok = encode_population_map(&s->maps[2 + b], (char *)d.f[b] - (size_t)kXO * L.elem, p->width + kXO, d.Wp,
+                                       d.H, d.P, L.Q, kTmaBoxX, iter_rows, p->precision);
         s->use_tma = ok;
         d.inject_in_update = ok && tma_inject ? 1 : 0;
         const int ty = iter_rows;
@@ -480,7 +501,7 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
             s->use_tma = false;
             d.inject_in_update = 0;
         }
-        if (!ok && p->update_kernel >= 2 && p->update_kernel <= 4) {
+        if (!ok && p->update_kernel >= 2 && p->update_kernel != 5) {
             if (s->own_arena) cudaFree(s->arena);
             delete s;
             return LBM_ERR_CUDA;

@@ -216,13 +216,16 @@ struct KernelTable {
     int update_tile_x; // columns per block of the update kernel
     // TMA-staged update (lbm_update_tma.cuh, for D2Q7 lbm_update7_tma.cuh;
     // null for FP64 storage). maps[b] loads from copy b (box (kTmaBoxX + 8) x
-    // (rows per tile + 2) x Q, in stored-row coordinates). tma_prepare sets
+    // (rows per tile + 2) x Q, in stored-row coordinates); maps[2 + b] stores
+    // into copy b for the variants that store in bulk (box kTmaBoxX x rows
+    // per tile x Q, columns cut at x = W - 1). tma_prepare sets
     // the kernel attributes a launch needs (the first launch does it too);
     // pdl: launch as a programmatic dependent of the preceding kernel.
     cudaError_t (*tma_prepare)(const SimDev &, int variant);
     cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t);
     // a staged variant's geometry: rows of one bulk copy's box, rows per
-    // tile, CTAs per SM; 0 for a variant the table has, -1 for none
+    // tile, CTAs per SM; 0 for a variant the table has, 1 for one that also
+    // stores in bulk, -1 for none
     int (*tma_info)(int variant, int *box_rows, int *iter_rows, int *ctas_per_sm);
     // One step's kernels for every simulation of a batch in one launch each:
     // ds, the simulations' SimDev in device memory; bm, nb entries (simulation,

@@ -57,11 +57,12 @@ struct TmaGeom {
     static constexpr uint32_t BYTES = (uint32_t)IN_ELEMS * (uint32_t)sizeof(S); // one box copy delivers
 };
 
-template <typename S, int TY, int STAGES>
+// (TSTORE: an output tile [plane][TY][128] more, for bulk tensor stores)
+template <typename S, int TY, int STAGES, bool TSTORE = false>
 constexpr size_t tma_smem_bytes()
 {
-    return 128 + (size_t)STAGES * TmaGeom<S, TY>::STRIDE * sizeof(S) + 16 * STAGES + (size_t)TMA_EV_CAP * 16 +
-           TMA_KFLAG_WORDS * 4;
+    return 128 + (size_t)STAGES * TmaGeom<S, TY>::STRIDE * sizeof(S) + (TSTORE ? (size_t)9 * TY * TMA_TX * sizeof(S) : 0) +
+           16 * STAGES + (size_t)TMA_EV_CAP * 16 + TMA_KFLAG_WORDS * 4;
 }
 
 // Configurations. Variant 0: tiles of two rows, 128 threads, five CTAs per
@@ -70,12 +71,18 @@ constexpr size_t tma_smem_bytes()
 // boxes per CTA for 16-bit storage (half the bytes each). Variant 0 gave
 // 81.0 against 85.1 us per step on the 4096 x 2048 FP32 workload (the two-row
 // boxes re-read more halo rows from the L2, but more, shorter tiles keep
-// more copies in flight).
+// more copies in flight). Variant 2 (FP32 only): variant 0's tiles, the
+// results gathered in a shared output tile and written by one bulk tensor
+// store per tile instead of per-lane stores, four CTAs per SM. (A 16-bit
+// tile starts 4 elements = 8 bytes into a 16-byte unit, and a bulk tensor
+// store must start on a 16-byte boundary.)
 template <typename S>
 struct TmaCfg {
     static constexpr int TY0 = 2, CTAS0 = 5, STAGES0 = sizeof(S) == 4 ? 2 : 4;
     static constexpr int TY1 = 4, CTAS1 = 3, STAGES1 = sizeof(S) == 4 ? 2 : 4;
+    static constexpr int TY2 = 2, CTAS2 = 4, STAGES2 = 2;
 };
+static_assert(4 * (tma_smem_bytes<float, 2, 2, true>() + 1024) <= 228 * 1024, "four CTAs per SM by shared memory");
 static_assert(5 * (tma_smem_bytes<float, 2, 2>() + 1024) <= 228 * 1024, "five CTAs per SM by shared memory");
 static_assert(3 * (tma_smem_bytes<float, 4, 2>() + 1024) <= 228 * 1024, "three CTAs per SM by shared memory");
 static_assert(5 * (tma_smem_bytes<__half, 2, 4>() + 1024) <= 228 * 1024, "five CTAs per SM by shared memory");
@@ -242,11 +249,16 @@ __device__ __forceinline__ float update_node(const float g[NQ], float rho, bool 
     return 0.0f;
 }
 
-// CTAS CTAs per SM (registers are capped so that they fit); NOISE: sigma != 0.
-template <typename S, int TY, int STAGES, int CTAS, bool NOISE>
+// CTAS CTAs per SM (registers are capped so that they fit); NOISE: sigma != 0;
+// TSTORE: results leave through a shared output tile and one bulk tensor
+// store per tile (ts0 / ts1: copy 0 / 1 as [plane][row][stored column] with
+// the columns cut at x = W - 1, boxes of 128 x TY x 9), else per-lane stores.
+template <typename S, int TY, int STAGES, int CTAS, bool NOISE, bool TSTORE>
 __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
-    k_update_tma(SimDev d, const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1)
+    k_update_tma(SimDev d, const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1,
+                 const __grid_constant__ CUtensorMap ts0, const __grid_constant__ CUtensorMap ts1)
 {
+    static_assert(!TSTORE || sizeof(S) == 4, "bulk tensor stores of 16-bit tiles would start off a 16-byte boundary");
     using G = TmaGeom<S, TY>;
     constexpr int NT = G::NT, PLANE = G::PLANE;
     const Pop<S> pc(d);
@@ -254,7 +266,8 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
     // stages on a 128-byte boundary (offset from the array itself, so that
     // every access stays a shared-memory access)
     S *s_in = reinterpret_cast<S *>(smem_f + ((128u - (smem_u32(smem_f) & 127u)) & 127u) / 4u);
-    uint64_t *full = reinterpret_cast<uint64_t *>(s_in + STAGES * G::STRIDE);
+    S *s_out = s_in + STAGES * G::STRIDE; // the output tile (TSTORE), on a 128-byte boundary
+    uint64_t *full = reinterpret_cast<uint64_t *>(s_out + (TSTORE ? 9 * TY * TMA_TX : 0));
     uint64_t *empty = full + STAGES;
     // divisions of this CTA's tiles: local tile index, two staged offsets, amount
     int *ev_k = reinterpret_cast<int *>(empty + STAGES);
@@ -275,6 +288,10 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
         s_nev = 0;
         prefetch_tensormap(&tm0);
         prefetch_tensormap(&tm1);
+        if (TSTORE) {
+            prefetch_tensormap(&ts0);
+            prefetch_tensormap(&ts1);
+        }
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], G::WARPS);
@@ -294,6 +311,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
     const bool withhold = (d.sc->wait_test & WAIT_TEST_COPIES) != 0;
     const int cur = (int)(t & 1u);
     const CUtensorMap *tm = cur ? &tm1 : &tm0;
+    const CUtensorMap *ts = cur ? &ts0 : &ts1; // (the copy this step writes)
     const S *__restrict__ fin = (const S *)d.f[cur];
     S *__restrict__ fout = (S *)d.f[cur ^ 1];
     const int y_r = d.sc->y_r, y_copy = d.sc->y_copy, y_hi = d.sc->y_hi;
@@ -463,6 +481,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
             }
             if (!dead) issue();
         }
+        float2 res[NQ]; // this thread's two nodes' results (TSTORE)
         if (active) {
             const int x = x0 + cl;
             const bool oka = x < W, okb = x + 1 < W;
@@ -498,7 +517,12 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
                 if ((lane & 15) == 0) d.mask[(long long)y * d.MW + (x0 >> 5) + 2 * half + (lane >> 4)] = 0xffffffffu;
                 S *o = fout + (long long)y * Wp + x;
                 float2 m2 = f2(0.0f);
-                store_pair<S>(o, P, f2o, pc, m2);
+                if constexpr (TSTORE) {
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) res[i] = f2o[i];
+                } else {
+                    store_pair<S>(o, P, f2o, pc, m2);
+                }
                 const int xw = x0 + 64 * half; // first column of the warp
                 if (xw == 0 || xw + 63 == W - 1) { // a warp at the lattice edge: ghost copies
                     if (x == 0) {
@@ -541,7 +565,12 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
                 S *o = fout + (long long)y * Wp + x;
                 float ma = 0.0f, mb = 0.0f;
                 // (odd W: the last column alone, x = W is the ghost)
-                if (oka) store_nodes<S>(o, P, fa, fb, okb, pc, ma, mb);
+                if constexpr (TSTORE) {
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) res[i] = make_float2(fa[i], fb[i]);
+                } else {
+                    if (oka) store_nodes<S>(o, P, fa, fb, okb, pc, ma, mb);
+                }
                 // ghost copies of the edge columns for the next step's boxes
                 if (x == 0) {
     #pragma unroll
@@ -572,6 +601,23 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
                 }
             }
         }
+        if constexpr (TSTORE) {
+            // the previous tile's store must have read the output tile
+            if (tid == 0) bulk_wait_read<0>();
+            __syncthreads();
+            // rows past the window get zeros, which they hold anyway; columns
+            // from x = W on are cut by the store's tensor map
+            S *ot = s_out + row * TMA_TX + cl;
+#pragma unroll
+            for (int i = 0; i < NQ; ++i)
+                *reinterpret_cast<float2 *>(ot + i * TY * TMA_TX) = active ? res[i] : f2(0.0f);
+            fence_proxy_async_smem(); // the async proxy reads what these threads wrote
+            __syncthreads();
+            if (tid == 0) {
+                tma_store_3d(ts, x0 + kXO, y0, 0, s_out);
+                bulk_commit();
+            }
+        }
         tx += dtx;
         ty += dty;
         if (tx >= ncx) {
@@ -579,6 +625,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
             ++ty;
         }
     }
+    if (TSTORE && tid == 0) bulk_wait_all(); // the last tiles' stores are done before the CTA exits
     if (tid == 0 && s_abort) {
         atomicOr(&d.sc->status, ST_TIMEOUT);
         // let the copies still in flight land before the CTA exits
@@ -596,7 +643,7 @@ __global__ void __launch_bounds__(TmaGeom<S, TY>::NT, CTAS)
 }
 
 // The kernel's shared-memory opt-in (once per device).
-template <typename S, int TY, int STAGES, int CTAS, bool NOISE>
+template <typename S, int TY, int STAGES, int CTAS, bool NOISE, bool TSTORE>
 cudaError_t prepare_update_tma_variant()
 {
     static bool attr[64] = {};
@@ -604,70 +651,90 @@ cudaError_t prepare_update_tma_variant()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64 || !attr[dev]) {
-        e = cudaFuncSetAttribute(k_update_tma<S, TY, STAGES, CTAS, NOISE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tma_smem_bytes<S, TY, STAGES>());
+        e = cudaFuncSetAttribute(k_update_tma<S, TY, STAGES, CTAS, NOISE, TSTORE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tma_smem_bytes<S, TY, STAGES, TSTORE>());
         if (e != cudaSuccess) return e;
         if (dev < 64) attr[dev] = true;
     }
     return cudaSuccess;
 }
 
-template <typename S>
-cudaError_t prepare_update_tma(const SimDev &d, int variant)
-{
-    using C = TmaCfg<S>;
-    if (variant == 1)
-        return d.noise_on ? prepare_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, true>()
-                          : prepare_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, false>();
-    return d.noise_on ? prepare_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, true>()
-                      : prepare_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, false>();
-}
-
-template <typename S, int TY, int STAGES, int CTAS, bool NOISE>
+// maps[b] loads from population copy b, maps[2 + b] stores into it (TSTORE).
+// Launched as a programmatic dependent of the planner: its CTAs may start
+// (and run the prologue) before the planner has finished, and wait for it in
+// grid_dependency_wait.
+template <typename S, int TY, int STAGES, int CTAS, bool NOISE, bool TSTORE>
 cudaError_t launch_update_tma_variant(const SimDev &d, const CUtensorMap *maps, bool pdl, cudaStream_t s)
 {
-    cudaError_t e = prepare_update_tma_variant<S, TY, STAGES, CTAS, NOISE>();
+    cudaError_t e = prepare_update_tma_variant<S, TY, STAGES, CTAS, NOISE, TSTORE>();
     if (e != cudaSuccess) return e;
-    // maps[b] loads from population copy b. Launched as a programmatic
-    // dependent of the planner: its CTAs may start (and run the prologue)
-    // before the planner has finished, and wait for it in grid_dependency_wait.
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)d.upd_ctas); // at most CTAS per SM
     cfg.blockDim = dim3(TmaGeom<S, TY>::NT);
-    cfg.dynamicSmemBytes = tma_smem_bytes<S, TY, STAGES>();
+    cfg.dynamicSmemBytes = tma_smem_bytes<S, TY, STAGES, TSTORE>();
     cfg.stream = s;
     cudaLaunchAttribute la[1];
     la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     la[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = la;
     cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_update_tma<S, TY, STAGES, CTAS, NOISE>, d, maps[0], maps[1]);
+    return cudaLaunchKernelEx(&cfg, k_update_tma<S, TY, STAGES, CTAS, NOISE, TSTORE>, d, maps[0], maps[1],
+                              maps[TSTORE ? 2 : 0], maps[TSTORE ? 3 : 1]);
 }
 
-// rows per tile and CTAs per SM of the variants (TmaCfg)
-constexpr int tma_rows(int variant) { return variant == 1 ? 4 : 2; }
-constexpr int tma_ctas_per_sm(int variant) { return variant == 1 ? 3 : 5; }
+template <typename S, bool NOISE>
+cudaError_t prepare_update_tma_noise(int variant)
+{
+    using C = TmaCfg<S>;
+    if (variant == 1) return prepare_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, NOISE, false>();
+    if constexpr (sizeof(S) == 4)
+        if (variant == 2) return prepare_update_tma_variant<S, C::TY2, C::STAGES2, C::CTAS2, NOISE, true>();
+    return prepare_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, NOISE, false>();
+}
+
+template <typename S>
+cudaError_t prepare_update_tma(const SimDev &d, int variant)
+{
+    return d.noise_on ? prepare_update_tma_noise<S, true>(variant) : prepare_update_tma_noise<S, false>(variant);
+}
+
+template <typename S, bool NOISE>
+cudaError_t launch_update_tma_noise(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s)
+{
+    using C = TmaCfg<S>;
+    if (variant == 1) return launch_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, NOISE, false>(d, maps, pdl, s);
+    if constexpr (sizeof(S) == 4)
+        if (variant == 2)
+            return launch_update_tma_variant<S, C::TY2, C::STAGES2, C::CTAS2, NOISE, true>(d, maps, pdl, s);
+    return launch_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, NOISE, false>(d, maps, pdl, s);
+}
 
 template <typename S>
 cudaError_t launch_update_tma(const SimDev &d, const CUtensorMap *maps, int variant, bool pdl, cudaStream_t s)
 {
-    using C = TmaCfg<S>;
-    if (variant == 1)
-        return d.noise_on ? launch_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, true>(d, maps, pdl, s)
-                          : launch_update_tma_variant<S, C::TY1, C::STAGES1, C::CTAS1, false>(d, maps, pdl, s);
-    return d.noise_on ? launch_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, true>(d, maps, pdl, s)
-                      : launch_update_tma_variant<S, C::TY0, C::STAGES0, C::CTAS0, false>(d, maps, pdl, s);
+    return d.noise_on ? launch_update_tma_noise<S, true>(d, maps, variant, pdl, s)
+                      : launch_update_tma_noise<S, false>(d, maps, variant, pdl, s);
 }
 
 // Geometry of a variant for the host: rows of one bulk copy's box, rows per
 // tile, CTAs per SM; 0 for a variant of this kernel, -1 for none.
+// (1: the variant also stores through bulk tensor copies, which want the
+// store maps)
 template <typename S>
 int tile_variant_info(int variant, int *box_rows, int *iter_rows, int *ctas_per_sm)
 {
+    using C = TmaCfg<S>;
+    if (variant == 2 && sizeof(S) == 4) {
+        *iter_rows = C::TY2;
+        *box_rows = C::TY2 + 2;
+        *ctas_per_sm = C::CTAS2;
+        return 1;
+    }
     if (variant != 0 && variant != 1) return -1;
-    *iter_rows = variant == 1 ? TmaCfg<S>::TY1 : TmaCfg<S>::TY0;
+    *iter_rows = variant == 1 ? C::TY1 : C::TY0;
     *box_rows = *iter_rows + 2;
-    *ctas_per_sm = variant == 1 ? TmaCfg<S>::CTAS1 : TmaCfg<S>::CTAS0;
+    *ctas_per_sm = variant == 1 ? C::CTAS1 : C::CTAS0;
     return 0;
 }
 

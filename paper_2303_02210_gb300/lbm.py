@@ -33,7 +33,7 @@ STATUS_GROWTH_STARVED = 2
 STATUS_CAPACITY = 4
 STATUS_TIMEOUT = 8
 LATTICES = {"d2q9": 0, "d2q7": 1}
-UPDATE_KERNELS = {"auto": 0, "plain": 1, "tma": 2, "tma1": 3, "tma_sel": 4, "shared": 5}
+UPDATE_KERNELS = {"auto": 0, "plain": 1, "tma": 2, "tma1": 3, "tma_sel": 4, "shared": 5, "tma_st": 6}
 
 
 class LbmError(RuntimeError):

@@ -119,12 +119,15 @@ def test_async_calls_reject_null(lib):
 def test_update_kernel_choices_validate():
     p = wl.lattice_small()
     assert lbm.lbm_validate(p, "fp32") == 0
-    for uk, ok64 in (("auto", True), ("plain", True), ("tma", False), ("tma1", False), ("shared", True)):
+    for uk, ok64 in (("auto", True), ("plain", True), ("tma", False), ("tma1", False), ("shared", True),
+                     ("tma_st", False)):
         q = lbm.make_params(p, "fp64", uk)
         assert (lbm.load_library().lbm_validate(ctypes.byref(q)) == 0) == ok64, uk
         q = lbm.make_params(p, "fp32", uk)
         assert lbm.load_library().lbm_validate(ctypes.byref(q)) == 0, uk
-    q = lbm.make_params(p, "fp32", 6)
+    # the bulk-store form is FP32 only
+    assert lbm.load_library().lbm_validate(ctypes.byref(lbm.make_params(p, "fp16", "tma_st"))) == -1
+    q = lbm.make_params(p, "fp32", 7)
     assert lbm.load_library().lbm_validate(ctypes.byref(q)) == -1
     # the staged kernels need walls in y
     q = lbm.make_params(dict(p, y_periodic=1), "fp32", "tma")
@@ -139,7 +142,7 @@ def test_d2q7_update_kinds_validate():
     p = dict(wl.lattice_small(), lattice="d2q7")
     lib = lbm.load_library()
     for uk, ok in (("auto", True), ("plain", True), ("tma", True), ("shared", True), ("tma1", False),
-                   ("tma_sel", False)):
+                   ("tma_sel", False), ("tma_st", False)):
         q = lbm.make_params(p, "fp32", uk)
         assert (lib.lbm_validate(ctypes.byref(q)) == 0) == ok, uk
     for uk, ok in (("auto", True), ("plain", True), ("tma", False), ("shared", True)):

@@ -135,7 +135,7 @@ def test_maximum_extents(name, precision):
     from paper_2303_02210_gb300.lbm import Simulation
     a = Simulation(p, precision="fp32", update_kernel="plain")
     a.step(6)
-    for kernel in ("auto",):
+    for kernel in ("auto", "tma_st"):
         b = Simulation(p, precision="fp32", update_kernel=kernel)
         b.step(6)
         assert b.stats()["update_kernel"] >= 2
@@ -239,7 +239,7 @@ TMA_CASES["ragged_300"] = wl.lattice_small(seed=22, width=300, height=70, front_
                                            growth_rate=3e-3, sigma=0.05)
 
 
-@pytest.mark.parametrize("kernel", ["tma", "tma1"])
+@pytest.mark.parametrize("kernel", ["tma", "tma1", "tma_st"])
 @pytest.mark.parametrize("name", sorted(TMA_CASES))
 def test_fp32_tma_kernel_bit_exact_with_plain_kernel(name, kernel):
     """The TMA-staged FP32 update moves data differently (bulk tensor tiles
@@ -263,7 +263,7 @@ def test_fp32_tma_kernel_bit_exact_with_plain_kernel(name, kernel):
         assert np.array_equal(a.heights(), b.heights())
 
 
-@pytest.mark.parametrize("kernel", ["tma"])
+@pytest.mark.parametrize("kernel", ["tma", "tma_st"])
 def test_fp32_tma_repeatable_on_reused_memory(kernel):
     """The TMA-staged update refills a shared-memory stage as soon as every
     warp holds its values; a refill that overtakes a pending shared-memory

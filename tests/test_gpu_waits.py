@@ -73,9 +73,9 @@ def _abandon_and_recover(params, withhold, update_kernel="tma"):
     return sim, f0
 
 
-@pytest.mark.parametrize("lattice", ["d2q9", "d2q7"])
-def test_staged_copy_wait_runs_out_and_the_handle_recovers(lattice):
-    sim, _ = _abandon_and_recover(_params(lattice), withhold=1)
+@pytest.mark.parametrize("lattice,kernel", [("d2q9", "tma"), ("d2q9", "tma_st"), ("d2q7", "tma")])
+def test_staged_copy_wait_runs_out_and_the_handle_recovers(lattice, kernel):
+    sim, _ = _abandon_and_recover(_params(lattice), withhold=1, update_kernel=kernel)
     sim.close()
 
 
