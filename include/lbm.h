@@ -306,9 +306,16 @@ typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **out);
 int lbm_batch_step(lbm_batch *batch, int64_t nsteps);
 int lbm_batch_destroy(lbm_batch *batch);
-/* 1 if the batch steps with the batched launches (all members share the
- * storage type and the lattice), 0 if with one graph branch per member;
- * LBM_ERR_INVALID_ARG for NULL. */
+/* 3 if the batch steps with the batched launches and its update is the
+ * TMA-staged one with bulk tensor stores (FP32 members all at least 2048
+ * wide and multiples of 4 wide), 2 if the TMA-staged one with per-lane
+ * stores (all members
+ * D2Q9 with FP32 or the same 16-bit storage and walls in y, at most 256 of
+ * them: one launch deals all members' 128 x 2 tiles; the divisions are added
+ * by the batched injection launch before it),
+ * 1 if with the batched launches and the plain-load update (the members
+ * share the storage type and the lattice), 0 if with one graph branch per
+ * member; LBM_ERR_INVALID_ARG for NULL. */
 int lbm_batch_fused(const lbm_batch *batch);
 
 /* ---- allocation-free variant (the paper has no counterpart) ----

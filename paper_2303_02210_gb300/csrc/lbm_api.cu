@@ -936,8 +936,14 @@ struct lbm_batch {
     bool fused;
     void *dev_mem;
     const SimDev *ds;
-    const int4 *bm_upd, *bm_inj;
-    int nb_upd, nb_inj;
+    const int4 *bm_upd, *bm_inj, *bm_plan;
+    int nb_upd, nb_inj, nb_plan, plan_coop;
+    // the TMA-staged batched update (all members D2Q9, FP32 or 16-bit, walls
+    // in y, at most kTmaBatchMaxSims): two load maps per member, the grid
+    bool tma;
+    const MemberConst *mc;
+    const CUtensorMap *maps;
+    int noise, tstore, tma_grid;
 };
 
 namespace {
@@ -954,8 +960,11 @@ cudaError_t batch_capture(lbm_batch *b, int steps, cudaGraphExec_t *out)
         const KernelTable *kt = b->sims[0]->kt;
         for (int k = 0; k < steps && first == cudaSuccess; ++k) {
             first = kt->batch_inject(b->ds, b->bm_inj, b->nb_inj, b->origin);
-            if (first == cudaSuccess) first = kt->batch_update(b->ds, b->bm_upd, b->nb_upd, b->origin);
-            if (first == cudaSuccess) first = kt->batch_plan(b->ds, (int)b->sims.size(), b->origin);
+            if (first == cudaSuccess)
+                first = b->tma ? kt->batch_update_tma(b->ds, b->mc, b->maps, (int)b->sims.size(), b->noise,
+                                                      b->tstore, b->tma_grid, b->origin)
+                               : kt->batch_update(b->ds, b->bm_upd, b->nb_upd, b->origin);
+            if (first == cudaSuccess) first = kt->batch_plan(b->ds, b->bm_plan, b->nb_plan, b->plan_coop, b->origin);
         }
     } else {
         first = cudaEventRecord(b->fork, b->origin);
@@ -992,7 +1001,28 @@ cudaError_t batch_tables(lbm_batch *b)
     double area = 0.0;
     for (const lbm_sim *s : b->sims) area += (double)s->p.width * (double)s->p.height;
     const double target = 2.0 * nsm * bps;
-    std::vector<int4> upd, inj;
+    std::vector<int4> upd, inj, pln;
+    // planners: a simulation whose own planner grid is larger than two blocks
+    // plans with that grid, the others with one block each (no grid barrier);
+    // the grids are scaled down together until all fit at once (the
+    // cooperative launch needs every block resident)
+    const int pbs = std::max(1, kt->plan_blocks_per_sm());
+    const long long cap = (long long)pbs * nsm;
+    long long want = 0;
+    for (const lbm_sim *s : b->sims) want += s->d.plan_grid > 2 ? s->d.plan_grid : 1;
+    b->plan_coop = 0;
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        const int own = b->sims[i]->d.plan_grid > 2 ? b->sims[i]->d.plan_grid : 1;
+        int g = want <= cap ? own : (int)std::max<long long>(1, own * (cap - (long long)b->sims.size()) / want);
+        if (g < 1) g = 1;
+        if (g > 1) b->plan_coop = 1;
+        for (int j = 0; j < g; ++j) pln.push_back(make_int4((int)i, j, g, 0));
+    }
+    if ((long long)pln.size() > cap) { // (never, by the scaling above; one block each then)
+        pln.clear();
+        b->plan_coop = 0;
+        for (size_t i = 0; i < b->sims.size(); ++i) pln.push_back(make_int4((int)i, 0, 1, 0));
+    }
     for (size_t i = 0; i < b->sims.size(); ++i) {
         const lbm_sim *s = b->sims[i];
         const int ncx = (s->p.width + kt->update_tile_x - 1) / kt->update_tile_x;
@@ -1005,9 +1035,49 @@ cudaError_t batch_tables(lbm_batch *b)
     const size_t n = b->sims.size();
     const size_t off_u = align256(n * sizeof(SimDev));
     const size_t off_i = align256(off_u + upd.size() * sizeof(int4));
+    const size_t off_p = align256(off_i + inj.size() * sizeof(int4));
+    const size_t off_m = align256(off_p + pln.size() * sizeof(int4)); // tensor maps (128-byte aligned)
+    const size_t off_c = align256(off_m + (b->tma ? 4 * n : 0) * sizeof(CUtensorMap)); // member constants
+    std::vector<CUtensorMap> maps(b->tma ? 4 * n : 0);
+    std::vector<MemberConst> mcs(b->tma ? n : 0);
+    for (size_t i = 0; i < n && b->tma; ++i) {
+        const lbm_sim *s = b->sims[i];
+        MemberConst &c = mcs[i];
+        std::memset(&c, 0, sizeof(c));
+        c.f[0] = s->d.f[0];
+        c.f[1] = s->d.f[1];
+        c.mask = s->d.mask;
+        c.sc = s->d.sc;
+        c.P = s->d.P;
+        c.W = s->d.W;
+        c.H = s->d.H;
+        c.Wp = s->d.Wp;
+        c.MW = s->d.MW;
+        c.key0 = s->d.key0;
+        c.key1 = s->d.key1;
+        c.sim = s->d.sim;
+        c.negfix = s->d.negfix;
+        c.rho_c = s->d.f_rho_c;
+        c.om1 = s->d.f_om1;
+        c.ow1 = s->d.f_ow1;
+        c.ow5 = s->d.f_ow5;
+        c.cmu = s->d.f_cmu;
+        c.two_sigma = s->d.f_two_sigma;
+        for (int k = 0; k < 3; ++k) c.pop_shift[k] = s->d.pop_shift[k];
+        for (int c = 0; c < 2; ++c) {
+            char *base_c = (char *)s->d.f[c] - (size_t)kXO * s->L.elem;
+            if (!encode_population_map(&maps[4 * i + c], base_c, s->d.Wp, s->d.Wp, s->d.H, s->d.P, s->L.Q,
+                                       kTmaBoxX + 8, 4, s->p.precision))
+                return cudaErrorInvalidValue;
+            // bulk stores of a tile's 128 columns, cut at x = W - 1
+            if (b->tstore && !encode_population_map(&maps[4 * i + 2 + c], base_c, s->p.width + kXO, s->d.Wp, s->d.H,
+                                                    s->d.P, s->L.Q, kTmaBoxX, 2, s->p.precision))
+                return cudaErrorInvalidValue;
+        }
+    }
     // stream-ordered on the batch's stream (no device-wide synchronisation:
     // batches are built while other work runs, as in the serving loop)
-    e = cudaMallocAsync(&b->dev_mem, off_i + inj.size() * sizeof(int4), b->origin);
+    e = cudaMallocAsync(&b->dev_mem, off_c + mcs.size() * sizeof(MemberConst), b->origin);
     if (e != cudaSuccess) return e;
     std::vector<SimDev> ds(n);
     for (size_t i = 0; i < n; ++i) ds[i] = b->sims[i]->d;
@@ -1017,6 +1087,14 @@ cudaError_t batch_tables(lbm_batch *b)
         e = cudaMemcpyAsync(base + off_u, upd.data(), upd.size() * sizeof(int4), cudaMemcpyHostToDevice, b->origin);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(base + off_i, inj.data(), inj.size() * sizeof(int4), cudaMemcpyHostToDevice, b->origin);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + off_p, pln.data(), pln.size() * sizeof(int4), cudaMemcpyHostToDevice, b->origin);
+    if (e == cudaSuccess && !maps.empty())
+        e = cudaMemcpyAsync(base + off_m, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                            b->origin);
+    if (e == cudaSuccess && !mcs.empty())
+        e = cudaMemcpyAsync(base + off_c, mcs.data(), mcs.size() * sizeof(MemberConst), cudaMemcpyHostToDevice,
+                            b->origin);
     // the host arrays go out of scope: wait for the copies from them
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->origin);
     b->ds = (const SimDev *)base;
@@ -1024,6 +1102,11 @@ cudaError_t batch_tables(lbm_batch *b)
     b->bm_inj = (const int4 *)(base + off_i);
     b->nb_upd = (int)upd.size();
     b->nb_inj = (int)inj.size();
+    b->bm_plan = (const int4 *)(base + off_p);
+    b->nb_plan = (int)pln.size();
+    b->maps = maps.empty() ? nullptr : (const CUtensorMap *)(base + off_m);
+    b->mc = mcs.empty() ? nullptr : (const MemberConst *)(base + off_c);
+    b->tma_grid = (b->tstore ? kTmaBatchCtasPerSmStore : kTmaBatchCtasPerSm) * nsm;
     return e;
 }
 } // namespace
@@ -1048,14 +1131,32 @@ int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **
     b->fork = nullptr;
     b->dev_mem = nullptr;
     b->ds = nullptr;
-    b->bm_upd = b->bm_inj = nullptr;
-    b->nb_upd = b->nb_inj = 0;
+    b->bm_upd = b->bm_inj = b->bm_plan = nullptr;
+    b->nb_upd = b->nb_inj = b->nb_plan = 0;
+    b->plan_coop = 0;
     // one launch per kernel for the whole batch when the members share the
     // storage type (the plain-load update; the results are the same as the
     // TMA-staged one's, bit for bit)
     b->fused = true;
     for (int32_t i = 1; i < n; ++i)
         if (sims[i]->kt != sims[0]->kt) b->fused = false;
+    // the TMA-staged batched update when every member can take it
+    b->tma = b->fused && sims[0]->kt->batch_update_tma && n <= kTmaBatchMaxSims;
+    b->noise = 0;
+    // bulk stores when every member is FP32, at least 2048 wide and a
+    // multiple of 4 wide (see lbm_create); measured: four 4096 x 2048 members
+    // 66.3 against 63.8 G node updates/s, but the 256-member ensemble of
+    // widths 256..2048 53.0 against 56.7 (four CTAs per SM instead of five)
+    b->tstore = b->tma && sims[0]->p.precision == LBM_FP32 ? 1 : 0;
+    for (int32_t i = 0; i < n; ++i)
+        if (sims[i]->p.width % 4 || sims[i]->p.width < 2048) b->tstore = 0;
+    b->maps = nullptr;
+    b->mc = nullptr;
+    b->tma_grid = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (sims[i]->p.lattice != LBM_D2Q9 || sims[i]->p.y_periodic) b->tma = false;
+        if (sims[i]->d.noise_on) b->noise = 1;
+    }
     cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
     if (e == cudaSuccess && b->fused) e = batch_tables(b);
@@ -1111,7 +1212,7 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps)
 int lbm_batch_fused(const lbm_batch *b)
 {
     if (!b) return LBM_ERR_INVALID_ARG;
-    return b->fused ? 1 : 0;
+    return b->fused ? (b->tma ? (b->tstore ? 3 : 2) : 1) : 0;
 }
 
 int lbm_batch_destroy(lbm_batch *b)

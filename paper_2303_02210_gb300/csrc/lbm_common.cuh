@@ -131,7 +131,10 @@ struct DevScalars {
     int pend_starved;     // the selection came up short
     int rec_n;            // division records of the next update
     int pad1;
-    unsigned long long bar_ctr; // grid-barrier arrivals of k_plan (grows by the grid size per barrier)
+    unsigned long long bar_ctr; // grid-barrier arrivals of k_plan (grows by the grid size per barrier;
+                                // zero when a launch starts)
+    unsigned int plan_exit;     // k_plan blocks done with the current launch
+    int pad3;
     // k_plan scratch: n_s from the mass before any freezing, computed by one
     // block while the others scan the front
     long long spec_req;
@@ -196,6 +199,23 @@ struct SimDev {
     int update_grid;     // persistent grid of the update kernel
 };
 
+// What the batched TMA-staged update needs to know about one member besides
+// its step and window: 128 bytes, built once per batch, copied into shared
+// memory together with each tile of that member.
+struct __align__(16) MemberConst {
+    void *f[2];
+    uint32_t *mask;
+    DevScalars *sc;
+    long long P;
+    int W, H, Wp, MW;
+    uint32_t key0, key1, sim;
+    int negfix;
+    float rho_c, om1, ow1, ow5, cmu, two_sigma;
+    float pop_shift[3];
+    int pad[3];
+};
+static_assert(sizeof(MemberConst) == 128, "one 128-byte block per member");
+
 // Launchers of one precision (implemented once per storage type).
 struct KernelTable {
     int elem_bytes;
@@ -230,11 +250,18 @@ struct KernelTable {
     // One step's kernels for every simulation of a batch in one launch each:
     // ds, the simulations' SimDev in device memory; bm, nb entries (simulation,
     // block, blocks) of the update's (a multiple of each simulation's column
-    // tiles) or the injection's block table; the planner takes one block per
-    // simulation.
+    // tiles), the injection's or the planner's block table (the planner: one
+    // block per simulation, or its own grid, then cooperatively).
     cudaError_t (*batch_inject)(const SimDev *ds, const int4 *bm, int nb, cudaStream_t);
     cudaError_t (*batch_update)(const SimDev *ds, const int4 *bm, int nb, cudaStream_t);
-    cudaError_t (*batch_plan)(const SimDev *ds, int n, cudaStream_t);
+    cudaError_t (*batch_plan)(const SimDev *ds, const int4 *bm, int nb, int coop, cudaStream_t);
+    // the TMA-staged update of a whole batch (lbm_update_tma_batch.cuh; null
+    // where there is none): mc[m] member m's constants, maps[4 m + b] loads its
+    // copy b in boxes of (kTmaBoxX + 8) x 4 x 9, maps[4 m + 2 + b] stores into
+    // it (tstore) in boxes of kTmaBoxX x 2 x 9; noise: some member has
+    // sigma != 0
+    cudaError_t (*batch_update_tma)(const SimDev *ds, const MemberConst *mc, const CUtensorMap *maps, int n,
+                                    int noise, int tstore, int grid, cudaStream_t);
 };
 
 extern const KernelTable kTableF32;
@@ -254,5 +281,10 @@ constexpr int kTmaBoxX = 128;
 constexpr int kTmaMaxCtas = 1024; // the reciprocal above is exact for tile < 2^22
 constexpr int kBucketCap = 256;    // division records listed per update CTA (more: full scan)
 constexpr int kPlanMaxBlocks = 1024;
+// The TMA-staged batched update: members one launch takes (its shared-memory
+// tables) and CTAs per SM.
+constexpr int kTmaBatchMaxSims = 256;
+constexpr int kTmaBatchCtasPerSm = 5;
+constexpr int kTmaBatchCtasPerSmStore = 4; // its bulk-store form
 
 } // namespace lbm

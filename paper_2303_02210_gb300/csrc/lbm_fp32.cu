@@ -2,6 +2,7 @@
 #include "lbm_launch.cuh"
 #include "lbm_update7_tma.cuh"
 #include "lbm_update_tma.cuh"
+#include "lbm_update_tma_batch.cuh"
 
 namespace lbm {
 
@@ -16,7 +17,8 @@ static int update7_staged_info(int variant, int *box_rows, int *iter_rows, int *
 }
 
 const KernelTable kTableF32 =
-    make_table<float>(&prepare_update_tma<float>, &launch_update_tma<float>, &tile_variant_info<float>);
+    make_table<float>(&prepare_update_tma<float>, &launch_update_tma<float>, &tile_variant_info<float>,
+                      &launch_update_tma_batch<float>);
 const KernelTable kTableF32Q7 =
     make_table7<float>(&prepare_update7_tma_any, &launch_update7_tma_any, &update7_staged_info);
 

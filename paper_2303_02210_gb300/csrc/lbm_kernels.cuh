@@ -66,6 +66,7 @@ struct Pop {
     using R = S; // arithmetic type
     static constexpr bool kShifted = false;
     __device__ explicit Pop(const SimDev &) {}
+    __device__ explicit Pop(const float *) {} // (from the three shifts)
     __device__ R ld(S v, int) const { return v; }
     __device__ S st(R v, int) const { return v; }
 };
@@ -76,6 +77,7 @@ struct PopShifted {
     static constexpr bool kShifted = true;
     float c0, c1, c2;
     __device__ explicit PopShifted(const SimDev &d) : c0(d.pop_shift[0]), c1(d.pop_shift[1]), c2(d.pop_shift[2]) {}
+    __device__ explicit PopShifted(const float *sh) : c0(sh[0]), c1(sh[1]), c2(sh[2]) {}
     __device__ float shift(int q) const
     {
         const int k = wclass(q);
@@ -95,10 +97,12 @@ struct CvtBf16 {
 template <>
 struct Pop<__half> : PopShifted<__half, CvtHalf> {
     __device__ explicit Pop(const SimDev &d) : PopShifted<__half, CvtHalf>(d) {}
+    __device__ explicit Pop(const float *sh) : PopShifted<__half, CvtHalf>(sh) {}
 };
 template <>
 struct Pop<__nv_bfloat16> : PopShifted<__nv_bfloat16, CvtBf16> {
     __device__ explicit Pop(const SimDev &d) : PopShifted<__nv_bfloat16, CvtBf16>(d) {}
+    __device__ explicit Pop(const float *sh) : PopShifted<__nv_bfloat16, CvtBf16>(sh) {}
 };
 template <typename S>
 using arith_t = typename Pop<S>::R;

@@ -58,10 +58,9 @@ struct Launch {
         k_update_batch<S, UPD_TPB, UPD_NR><<<nb, UPD_TPB, 0, s>>>(ds, bm);
         return cudaGetLastError();
     }
-    static cudaError_t batch_plan(const SimDev *ds, int n, cudaStream_t s)
+    static cudaError_t batch_plan(const SimDev *ds, const int4 *bm, int nb, int coop, cudaStream_t s)
     {
-        k_plan_batch<S><<<n, PLAN_NT, 0, s>>>(ds);
-        return cudaGetLastError();
+        return launch_plan_batch<S>(ds, bm, nb, coop, s);
     }
     static int update_blocks_per_sm()
     {
@@ -76,14 +75,18 @@ template <typename S>
 constexpr KernelTable make_table(cudaError_t (*tma_prepare)(const SimDev &, int) = nullptr,
                                  cudaError_t (*tma_update)(const SimDev &, const CUtensorMap *, int, bool,
                                                            cudaStream_t) = nullptr,
-                                 int (*tma_info)(int, int *, int *, int *) = nullptr)
+                                 int (*tma_info)(int, int *, int *, int *) = nullptr,
+                                 cudaError_t (*batch_update_tma)(const SimDev *, const MemberConst *,
+                                                                 const CUtensorMap *, int, int, int, int,
+                                                                 cudaStream_t) = nullptr)
 {
     return KernelTable{(int)sizeof(S),       &Launch<S>::fill,          &Launch<S>::ghosts,
                        &Launch<S>::scan,     &Launch<S>::plan,          &Launch<S>::inject,
                        &Launch<S>::update,
                        &Launch<S>::fields,   &plan_blocks_per_sm<S>,    &Launch<S>::update_blocks_per_sm,
                        Launch<S>::UPD_TPB,   tma_prepare,               tma_update,        tma_info,
-                       &Launch<S>::batch_inject, &Launch<S>::batch_update, &Launch<S>::batch_plan};
+                       &Launch<S>::batch_inject, &Launch<S>::batch_update, &Launch<S>::batch_plan,
+                       batch_update_tma};
 }
 
 // The triangular D2Q7 lattice (FP32 or FP64 storage; the TMA-staged update
@@ -137,10 +140,9 @@ struct Launch7 {
         k_update7_batch<S, UPD_TPB, UPD_NR><<<nb, UPD_TPB, 0, s>>>(ds, bm);
         return cudaGetLastError();
     }
-    static cudaError_t batch_plan(const SimDev *ds, int n, cudaStream_t s)
+    static cudaError_t batch_plan(const SimDev *ds, const int4 *bm, int nb, int coop, cudaStream_t s)
     {
-        k_plan_batch<S, Lat7><<<n, PLAN_NT, 0, s>>>(ds);
-        return cudaGetLastError();
+        return launch_plan_batch<S, Lat7>(ds, bm, nb, coop, s);
     }
     static int update_blocks_per_sm()
     {
@@ -165,7 +167,8 @@ constexpr KernelTable make_table7(cudaError_t (*tma_prepare)(const SimDev &, int
                        &Launch7<S>::update,    &Launch7<S>::fields,        &plan_blocks_per_sm<S, Lat7>,
                        &Launch7<S>::update_blocks_per_sm,
                        Launch7<S>::UPD_TPB,    tma_prepare,                tma_update,        tma_info,
-                       &Launch7<S>::batch_inject, &Launch7<S>::batch_update, &Launch7<S>::batch_plan};
+                       &Launch7<S>::batch_inject, &Launch7<S>::batch_update, &Launch7<S>::batch_plan,
+                       nullptr};
 }
 
 } // namespace lbm

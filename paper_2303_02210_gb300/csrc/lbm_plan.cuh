@@ -40,9 +40,10 @@ constexpr int PLAN_WARPS = PLAN_NT / 32;
 constexpr int PLAN_R = 8; // candidates per thread in the first pass
 // Grid barrier on a monotone arrival counter: a block's thread 0 adds one and
 // waits until the counter reaches the next multiple of the grid size (the
-// counter persists across launches, which all use the same grid; the host
-// zeroes it in lbm_clear_status). The wait is bounded by `budget` clock
-// cycles: on timeout ST_TIMEOUT is raised and later barriers no longer wait.
+// counter starts every launch at zero: the launch's last block out resets it,
+// so successive launches may use different grids). The wait is bounded by
+// `budget` clock cycles: on timeout ST_TIMEOUT is raised and later barriers
+// no longer wait.
 // `extra`: arrivals waited for beyond the grid (1 only in the failure-
 // detection test, so that the wait runs out).
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
@@ -609,6 +610,20 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
         sc->plan_carry = carry_out;
         sc->rec_n = nsel;
     }
+    // the last block out restarts the barrier counter for the next launch (a
+    // block counts itself out only after passing all its barriers, so no
+    // block waits on the counter any more)
+    if (G > 1) {
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            if (atomicAdd(&sc->plan_exit, 1u) == (unsigned)G - 1u) {
+                sc->bar_ctr = 0ull;
+                sc->plan_exit = 0u;
+                __threadfence();
+            }
+        }
+    }
 }
 
 // The planner of one simulation on a cooperative grid (launch_plan).
@@ -618,13 +633,33 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
     plan_body<S, LT>(d, init, (int)gridDim.x, (int)blockIdx.x);
 }
 
-// The planners of a batch of simulations, one block each (ds[blockIdx.x]):
-// a block's barriers are its own, so the blocks need not be resident
-// together and the launch is an ordinary one.
+// The planners of a batch of simulations: block b plans simulation bm[b].x
+// as its block bm[b].y of bm[b].z. A simulation planned by one block has
+// barriers of its own; one planned by more uses the grid barrier on its own
+// arrival counter with the grid it uses when stepped alone (the counter
+// advances by that grid size per barrier), and the launch is cooperative so
+// that its blocks are resident together.
 template <typename S, typename LT = Lat9>
-__global__ void __launch_bounds__(PLAN_NT) k_plan_batch(const SimDev *__restrict__ ds)
+__global__ void __launch_bounds__(PLAN_NT) k_plan_batch(const SimDev *__restrict__ ds, const int4 *__restrict__ bm)
 {
-    plan_body<S, LT>(ds[blockIdx.x], 0, 1, 0);
+    const int4 a = bm[blockIdx.x];
+    plan_body<S, LT>(ds[a.x], 0, a.z, a.y);
+}
+
+// (coop: some simulation is planned by more than one block)
+template <typename S, typename LT = Lat9>
+cudaError_t launch_plan_batch(const SimDev *ds, const int4 *bm, int nb, int coop, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nb);
+    cfg.blockDim = dim3(PLAN_NT);
+    cfg.stream = s;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeCooperative;
+    la[0].val.cooperative = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = coop ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_plan_batch<S, LT>, ds, bm);
 }
 
 // App. A step 3 for the update kernels that read the populations from global

@@ -405,7 +405,17 @@ class Batch:
     @property
     def fused(self) -> bool:
         """True if a step of the batch is three batched launches."""
-        return self._lib.lbm_batch_fused(self._h) == 1
+        return self._lib.lbm_batch_fused(self._h) >= 1
+
+    @property
+    def staged(self) -> bool:
+        """True if the batched update is the TMA-staged one."""
+        return self._lib.lbm_batch_fused(self._h) >= 2
+
+    @property
+    def bulk_stores(self) -> bool:
+        """True if the staged batched update stores by bulk tensor copies."""
+        return self._lib.lbm_batch_fused(self._h) == 3
 
     def close(self):
         if getattr(self, "_h", None):

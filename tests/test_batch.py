@@ -225,3 +225,59 @@ def test_branch_batch_fp64_members_bit_exact_with_the_oracle():
         else:
             _fp32_close_to_oracle(g, o)
     batch.close()
+
+
+# ---- the TMA-staged batched update (every member D2Q9, walls in y) ----
+STAGED = [
+    (wl.lattice_small(seed=61, growth_rate=3e-3), "auto"),
+    (wl.lattice_small(seed=62, width=300, height=70, front_row=30.0, growth_rate=3e-3, growth_mode="edge",
+                      edge_depth=4, front_kind="sinusoidal", front_amp=2.0), "auto"),
+    (wl.lattice_small(seed=63, width=37, height=29, front_row=9.0, growth_rate=3e-3), "plain"),
+    (wl.lattice_small(seed=64, growth_mode="density", growth_rate=3e-3, sigma=0.0), "auto"),
+    (wl.lattice_small(seed=65, width=64, height=96, front_kind="sinusoidal", front_row=40.0, front_amp=3.0,
+                      front_kmax=4, growth_rate=3e-3, wall_min_gap=2.0), "tma1"),
+    (wl.lattice_small(seed=66, growth_mode="none", width=1, height=24, front_row=8.0), "auto"),
+    (wl.lattice_small(seed=67, growth_mode="band", band_rows=10, growth_rate=3e-3, height=96,
+                      front_row=40.0, wall_min_gap=12.0, sigma=0.05, negfix_mode="rescale"), "auto"),
+    (wl.lattice_small(seed=68, width=512, height=40, front_row=20.0, growth_rate=2e-3, growth_mode="edge"), "tma_st"),
+]
+
+
+@pytest.mark.parametrize("precision,width4", [("fp32", False), ("fp32", True), ("fp16", False), ("bf16", False)])
+def test_staged_batch_matches_single_stepping(precision, width4):
+    """Members that all take the TMA-staged update step with one batched
+    staged launch (tiles of all members dealt together, divisions injected
+    beforehand, members with and without noise mixed): bit for bit what
+    lbm_step gives each alone, whatever kernel that uses, also interleaved
+    with single steps."""
+    from paper_2303_02210_gb300.lbm import Batch
+    staged = STAGED if not width4 else [  # bulk stores: members at least 2048 wide
+        (dict(p, width=2048 + 128 * i, sim_id=i), k) for i, (p, k) in enumerate(STAGED) if p["width"] % 4 == 0]
+    ms = [(p, precision, k if precision == "fp32" or k != "tma_st" else "auto") for p, k in staged]
+    members = [make(m) for m in ms]
+    batch = Batch(members)
+    assert batch.fused and batch.staged
+    assert batch.bulk_stores == width4
+    batch.step(13)
+    members[1].step(2)
+    batch.step(6)
+    for i, (m, g) in enumerate(zip(ms, members)):
+        solo = make(m)
+        solo.step(21 if i == 1 else 19)
+        same(g, solo)
+    batch.close()
+
+
+def test_staged_batch_within_tolerance_of_the_oracle_1000_steps():
+    """The staged batched update against the FP64 oracle over 1000 steps at
+    the workloads' growth rate: every member within 1e-5, no flips, the same
+    divisions."""
+    from paper_2303_02210_gb300.lbm import Batch, Simulation
+    ps = [dict(p, growth_rate=1e-4) for p in ORACLE_MEMBERS]
+    members = [Simulation(p, precision="fp32") for p in ps]
+    batch = Batch(members)
+    assert batch.staged
+    batch.step(1000)
+    for p, g in zip(ps, members):
+        _fp32_close_to_oracle(g, _oracle_after(p, 1000))
+    batch.close()
