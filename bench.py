@@ -191,8 +191,10 @@ class ClockSampler:
 def measure_ensemble(n: int = 256, steps: int = 200, warm: int = 5) -> dict:
     """The batched form: n uneven realisations (widths 256..2048, height =
     width / 2, bulk or edge growth, FP32) advanced together by lbm_batch_step
-    (graph replays of three batched launches per step: injection, update and
-    one planner block per member), against the same simulations stepped one
+    (graph replays of three batched launches per step: injection, the
+    staged update over all members' tiles, and the planners: one block per
+    member or the member's own cooperative grid), against the same
+    simulations stepped one
     after another with lbm_step. Aggregate active-window node updates per
     second, device time by CUDA events around each region."""
     import torch
@@ -324,24 +326,26 @@ def measure_dense(steps: int = 300) -> dict:
     return out
 
 
-def measure_serving(n: int = 100, rate: float = 200.0, steps=(500, 5000), budget_gb: float = 100.0) -> dict:
+def measure_serving(n: int = 500, rate: float = 200.0, steps=(1000, 20000), budget_gb: float = 100.0,
+                    chunk: int = 100, slots: int = 256) -> dict:
     """The served form: a fixed trace of n requests (Poisson arrivals at
     `rate` per second, widths log-uniform 128..4096, height = width / 2, bulk,
     edge or density growth, g log-uniform 1e-5..1e-3, steps uniform in
     `steps`, FP32 or FP16 storage 50/50) through the continuous-batching
-    loop with an HBM budget;
-    time to result per request (arrival to result on the host) and the
-    aggregate node-update rate over the whole run (wall clock)."""
+    loop with an HBM budget, the requests stepped through one slot batch per
+    storage type; time to result per request (arrival to result on the host)
+    and the aggregate node-update rate over the whole run (wall clock, from
+    the first arrival to the last result)."""
     from paper_2303_02210_gb300 import serving
     trace = wl.serving_trace(n, rate=rate, steps=steps)
     reqs = [serving.Request(params=p, steps=k, arrival=t, precision=pr) for t, p, k, pr in trace]
-    srv = serving.Server(hbm_budget=int(budget_gb * 2 ** 30), chunk=100)
+    srv = serving.Server(hbm_budget=int(budget_gb * 2 ** 30), chunk=chunk, slots=slots)
     srv.run(reqs)
     out = serving.summary(reqs, srv)
     out["workload"] = (f"{n} requests, Poisson arrivals at {rate:g}/s, widths log-uniform 128-4096, "
                        f"height = width/2, bulk/edge/density growth, g log-uniform 1e-5..1e-3, "
                        f"{steps[0]}-{steps[1]} steps, FP32 or FP16 storage 50/50, {budget_gb:g} GB budget, "
-                       f"100-step ticks")
+                       f"slot batches of {slots} per storage type, ticks of at most {chunk} steps")
     return out
 
 

@@ -33,6 +33,7 @@ extern "C" {
 #define LBM_ERR_CUDA (-3)        /* a CUDA call failed (see lbm_last_cuda_error) */
 #define LBM_ERR_CAPACITY (-4)    /* one step asked for more divisions than the planner holds */
 #define LBM_ERR_NO_DEVICE (-5)   /* no CUDA device of compute capability 10.3 */
+#define LBM_ERR_BATCH_FULL (-6)  /* lbm_batch_attach: every slot of the batch is taken */
 
 /* ---- device status bits (lbm_stats_t.status; sticky until lbm_clear_status) ---- */
 #define LBM_STATUS_FRONT_AT_TOP 1   /* mass reached row H-1 (the top wall) */
@@ -148,9 +149,11 @@ int lbm_footprint(const lbm_params_t *params, uint64_t *bytes);
 
 /* Divisions per step the planner of such a simulation can hold: four times
  * the initial density's n_s over the whole lattice plus 1024, at most 2^24
- * (more sets LBM_STATUS_CAPACITY). A batch plans each member with one block
- * of 512 threads, which suits members with small values (a few thousand);
- * host only. */
+ * (more sets LBM_STATUS_CAPACITY). The planner's grid grows with this value
+ * and the lattice width (up to a quarter of the SMs); a batch plans members
+ * whose grid is one or two blocks with one block of 512 threads each, the
+ * others with their grids scaled so that all fit on the GPU at once (two
+ * blocks per SM). Host only. */
 int lbm_plan_capacity(const lbm_params_t *params, int64_t *ns_max);
 
 /* Creates a simulation and initialises it on `stream` (a cudaStream_t, NULL =
@@ -285,15 +288,18 @@ const char *lbm_version(void);
  * another they leave most of the GPU idle. A batch advances its simulations
  * together by replaying a CUDA graph. When all members store their
  * populations in the same type on the same lattice, a step of the whole
- * batch is three launches (injection, update, planner), each over a table
- * of every member's blocks, with one planner block per member; otherwise
- * the graph holds, for each
- * simulation, a chain of steps (update + planner) as an independent branch.
- * Each simulation computes exactly what lbm_step would (the same arithmetic
- * and counters, bit for bit).
+ * batch is three or four launches: the injection of every member's
+ * divisions, the update over every member's tiles, and the planners (one
+ * block per member, and a cooperative launch for members whose own planner
+ * grid is larger than two blocks, the grids scaled down so that all fit at
+ * once); otherwise the graph holds, for each simulation, a chain of steps
+ * (update + planner) as an independent branch. Each simulation computes
+ * exactly what lbm_step would (the same arithmetic and counters, bit for
+ * bit).
  *  sims    n distinct handles on one device, created by lbm_create and not
  *          in kernel timing; the batch keeps the pointers, the caller keeps
- *          ownership and must destroy the batch before any of them.
+ *          ownership and must destroy the batch (or detach the member)
+ *          before destroying a member.
  *  stream  cudaStream_t the graphs are launched on (NULL = legacy default).
  * lbm_batch_step enqueues nsteps steps of every member, ordered after the work
  * already on each member's own stream and before the work enqueued there
@@ -301,7 +307,8 @@ const char *lbm_version(void);
  * the result. Between lbm_batch_step calls the members may also be stepped on
  * their own. The graphs are captured in lbm_batch_create (LBM_ERR_CUDA if
  * capture fails); lbm_batch_create allocates streams, events, graphs and
- * the batched launches' tables in device memory. */
+ * the batched launches' tables in device memory. A batch of n members has n
+ * slots. */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **out);
 int lbm_batch_step(lbm_batch *batch, int64_t nsteps);
@@ -309,14 +316,48 @@ int lbm_batch_destroy(lbm_batch *batch);
 /* 3 if the batch steps with the batched launches and its update is the
  * TMA-staged one with bulk tensor stores (FP32 members all at least 2048
  * wide and multiples of 4 wide), 2 if the TMA-staged one with per-lane
- * stores (all members
- * D2Q9 with FP32 or the same 16-bit storage and walls in y, at most 256 of
- * them: one launch deals all members' 128 x 2 tiles; the divisions are added
- * by the batched injection launch before it),
+ * stores (all members D2Q9 with FP32 or the same 16-bit storage and walls
+ * in y, at most 256 slots: one launch deals all members' 128 x 2 tiles; the
+ * divisions are added by the batched injection launch before it),
  * 1 if with the batched launches and the plain-load update (the members
  * share the storage type and the lattice), 0 if with one graph branch per
  * member; LBM_ERR_INVALID_ARG for NULL. */
 int lbm_batch_fused(const lbm_batch *batch);
+
+/* Members joining and leaving a batch that steps with the batched launches
+ * (lbm_batch_fused >= 1), as a serving loop needs: the tables in device
+ * memory have room for more entries than the members use (an unused entry
+ * does nothing), so a change of members rewrites table entries and leaves
+ * the captured graphs as they are. The graphs are captured again (inside the
+ * call) only when a table outgrows its room (its room then doubles) or when
+ * a joining member cannot take the batch's form of the update (the staged
+ * form is captured with and without Eq. 4's noise, and a step replays the
+ * one the current members need; a member periodic in y ends
+ * the staged form, one narrower than 2048 or not a multiple of 4 wide ends
+ * the bulk stores; lbm_batch_fused reports the form in use).
+ * lbm_batch_create_empty: a batch with `slots` empty slots (1..4096; the
+ *     staged update for up to 256) for simulations of one lattice
+ *     (LBM_D2Q9, LBM_D2Q7) and storage type (LBM_FP32 .. LBM_BF16; D2Q7:
+ *     FP32 or FP64) on the current device; LBM_ERR_INVALID_ARG otherwise.
+ * lbm_batch_attach: puts `sim` (same lattice, storage type and device, not
+ *     in kernel timing, not yet a member) into the first free slot and
+ *     writes that slot's index to *slot (may be NULL). LBM_ERR_INVALID_ARG
+ *     for a mismatch or a branch-form batch, LBM_ERR_BATCH_FULL if no slot
+ *     is free. The batch's next steps come after the work already on the
+ *     member's stream. Waits for the batch's stream (the table copies).
+ * lbm_batch_detach: empties `sim`'s slot; the member's stream then waits for
+ *     the batch's steps already enqueued, so it may be queried, stepped
+ *     alone or destroyed. LBM_ERR_INVALID_ARG if `sim` is not a member.
+ *     Waits for the batch's stream.
+ * lbm_batch_members: the number of members (>= 0), or LBM_ERR_INVALID_ARG.
+ * lbm_batch_captures: how many times the batch's graphs have been captured
+ *     (1 after creation), or LBM_ERR_INVALID_ARG.
+ * Stepping a batch with no members enqueues nothing. */
+int lbm_batch_create_empty(int32_t slots, int32_t lattice, int32_t precision, void *stream, lbm_batch **out);
+int lbm_batch_attach(lbm_batch *batch, lbm_sim *sim, int32_t *slot);
+int lbm_batch_detach(lbm_batch *batch, lbm_sim *sim);
+int lbm_batch_members(const lbm_batch *batch);
+int lbm_batch_captures(const lbm_batch *batch);
 
 /* ---- allocation-free variant (the paper has no counterpart) ----
  * Front heights h(x) = 1 + highest set row of column x (0 if none) of a

@@ -44,6 +44,16 @@ int cuda_fail(cudaError_t e)
 
 uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
 
+// The kernels of a lattice and storage type.
+const KernelTable *kernel_table(int lattice, int precision)
+{
+    if (lattice == LBM_D2Q7) return precision == LBM_FP64 ? &kTableF64Q7 : &kTableF32Q7;
+    return precision == LBM_FP64   ? &kTableF64
+           : precision == LBM_FP16 ? &kTableF16
+           : precision == LBM_BF16 ? &kTableBF16
+                                   : &kTableF32;
+}
+
 // 16-bit population storage on the host side: the shift c_k = w_k rho_init
 // rounded to the storage type (weight class k: 0 rest, 1 axis, 2 diagonal),
 // and the same decode (float(s) + c, in FP32) and encode (round f - c to
@@ -330,13 +340,7 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     s->p = *p;
     s->device = dev;
     s->L = make_layout(*p);
-    if (p->lattice == LBM_D2Q7)
-        s->kt = p->precision == LBM_FP64 ? &kTableF64Q7 : &kTableF32Q7;
-    else
-        s->kt = p->precision == LBM_FP64   ? &kTableF64
-                : p->precision == LBM_FP16 ? &kTableF16
-                : p->precision == LBM_BF16 ? &kTableBF16
-                                           : &kTableF32;
+    s->kt = kernel_table(p->lattice, p->precision);
     s->stream = (cudaStream_t)stream;
     s->cur = 0;
     s->step = 0;
@@ -431,7 +435,7 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     const int g0 = nsm * (bps > 0 ? bps : 1);
     d.update_grid = g0 >= ncx ? (g0 / ncx) * ncx : ncx;
     // the planner's blocks must all be resident at once (cooperative launch)
-    const int pbs = s->kt->plan_blocks_per_sm();
+    const int pbs = s->kt->plan_blocks_per_sm(0);
     // one 32-column mask word per warp, about one candidate per thread at
     // the largest n_s; at least two blocks, at most a quarter of the SMs
     // (every grid barrier costs an arrival per block; measured on the edge-
@@ -906,6 +910,7 @@ const char *lbm_strerror(int code)
     case LBM_ERR_CUDA: return "CUDA error";
     case LBM_ERR_CAPACITY: return "too many divisions in one step for the planner";
     case LBM_ERR_NO_DEVICE: return "no usable CUDA device (compute capability 10.3 required)";
+    case LBM_ERR_BATCH_FULL: return "every slot of the batch is taken";
     default: return "unknown error";
     }
 }
@@ -920,51 +925,78 @@ const char *lbm_version(void) { return "0.1.0 sm_103a"; }
 // Batched stepping: independent simulations advanced together by replaying a
 // CUDA graph (the kernels read the step index from each simulation's device
 // scalars, so the same graph serves every step). When every member stores its
-// populations in the same type, a step is three launches for the whole batch
-// (injection, update, planner; each over a table of the members' blocks);
-// otherwise the graph holds one chain of steps per member as parallel branches.
+// populations in the same type, a step is three or four launches for the
+// whole batch (injection over all slots' divisions; the update, staged over
+// all members' tiles or over a table of the members' blocks; the planners,
+// over tables of one block per member and of the members planned by more);
+// otherwise the graph holds one chain of steps per member as parallel
+// branches.
+//
+// The batched form keeps its members in slots: the tables in device memory
+// have room for more entries than the members use (unused entries do nothing),
+// so a member that joins or leaves changes table entries, not the graphs. The
+// graphs are captured again only when a table outgrows its room or when a
+// joining member cannot take the staged update or its bulk stores. (Both
+// forms of the update, with and without Eq. 4's noise, are captured; a step
+// replays the one that the current members need.)
 struct lbm_batch {
-    std::vector<lbm_sim *> sims;
+    std::vector<lbm_sim *> sims; // per slot (nullptr: empty)
+    int members;
     int device;
-    cudaStream_t user;   // the caller's stream
-    cudaStream_t origin; // the batch's own stream, which the graphs are captured from and run on
+    const KernelTable *kt; // the members' kernels (the batched form)
+    cudaStream_t user;     // the caller's stream
+    cudaStream_t origin;   // the batch's own stream, which the graphs are captured from and run on
     std::vector<cudaStream_t> branch;
     cudaEvent_t fork;
     std::vector<cudaEvent_t> join;
-    cudaGraphExec_t exec[2]; // one step, kBatchChain steps
-    // batched launches: the members' SimDev and the block tables, in one allocation
+    cudaGraphExec_t exec[2][2]; // [without, with noise][one step, kBatchChain steps]
+    int captures;            // times the graphs were captured
+    // batched launches: the slots' SimDev and the plain-load update's block
+    // table (its room: that launch's grid), in one allocation; the planners
+    // deal their blocks on the device (a plain launch and a cooperative one
+    // of plan_cap blocks)
     bool fused;
     void *dev_mem;
-    const SimDev *ds;
-    const int4 *bm_upd, *bm_inj, *bm_plan;
-    int nb_upd, nb_inj, nb_plan, plan_coop;
+    SimDev *ds;
+    int4 *bm_upd;
+    int nb_upd, plan_cap;
     // the TMA-staged batched update (all members D2Q9, FP32 or 16-bit, walls
-    // in y, at most kTmaBatchMaxSims): two load maps per member, the grid
+    // in y, at most kTmaBatchMaxSims slots): four maps and a MemberConst per slot
     bool tma;
-    const MemberConst *mc;
-    const CUtensorMap *maps;
+    MemberConst *mc;
+    CUtensorMap *maps;
     int noise, tstore, tma_grid;
+    int nsm;
+    // host copies of the tables
+    std::vector<SimDev> h_ds;
+    std::vector<int4> h_upd;
+    std::vector<CUtensorMap> h_maps;
+    std::vector<MemberConst> h_mc;
 };
 
 namespace {
 constexpr int kBatchChain = 4; // steps per branch in the longer graph
 
 // Captures `steps` steps of every simulation into an executable graph:
-// batched launches, or one branch per simulation.
-cudaError_t batch_capture(lbm_batch *b, int steps, cudaGraphExec_t *out)
+// batched launches (the update with Eq. 4's noise if `noise`), or one branch
+// per simulation.
+cudaError_t batch_capture(lbm_batch *b, int steps, int noise, cudaGraphExec_t *out)
 {
     cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t first = cudaSuccess;
     if (b->fused) {
-        const KernelTable *kt = b->sims[0]->kt;
+        const KernelTable *kt = b->kt;
         for (int k = 0; k < steps && first == cudaSuccess; ++k) {
-            first = kt->batch_inject(b->ds, b->bm_inj, b->nb_inj, b->origin);
+            first = kt->batch_inject(b->ds, (int)b->sims.size(), 2 * b->nsm, b->origin);
             if (first == cudaSuccess)
-                first = b->tma ? kt->batch_update_tma(b->ds, b->mc, b->maps, (int)b->sims.size(), b->noise,
+                first = b->tma ? kt->batch_update_tma(b->ds, b->mc, b->maps, (int)b->sims.size(), noise,
                                                       b->tstore, b->tma_grid, b->origin)
                                : kt->batch_update(b->ds, b->bm_upd, b->nb_upd, b->origin);
-            if (first == cudaSuccess) first = kt->batch_plan(b->ds, b->bm_plan, b->nb_plan, b->plan_coop, b->origin);
+            if (first == cudaSuccess)
+                first = kt->batch_plan(b->ds, (int)b->sims.size(), b->plan_cap, 0, b->origin);
+            if (first == cudaSuccess)
+                first = kt->batch_plan(b->ds, (int)b->sims.size(), b->plan_cap, 1, b->origin);
         }
     } else {
         first = cudaEventRecord(b->fork, b->origin);
@@ -987,127 +1019,237 @@ cudaError_t batch_capture(lbm_batch *b, int steps, cudaGraphExec_t *out)
     return first;
 }
 
-// The batched launches' tables: the members' SimDev, the update's blocks
-// (about two waves of the update kernel for the whole batch, dealt by lattice
-// area, each member a multiple of its column tiles) and the injection's
-// blocks (one per 1024 divisions the member's planner can hold).
-cudaError_t batch_tables(lbm_batch *b)
+cudaError_t batch_recapture(lbm_batch *b)
 {
-    const KernelTable *kt = b->sims[0]->kt;
-    int nsm = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
-    if (e != cudaSuccess) return e;
+    for (auto &pair : b->exec)
+        for (cudaGraphExec_t &g : pair)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    // (the branch form and the plain-load update draw the noise per member)
+    const int forms = b->fused && b->tma ? 2 : 1;
+    cudaError_t e = cudaSuccess;
+    for (int nz = 0; nz < forms && e == cudaSuccess; ++nz) {
+        e = batch_capture(b, 1, nz, &b->exec[nz][0]);
+        if (e == cudaSuccess) e = batch_capture(b, kBatchChain, nz, &b->exec[nz][1]);
+    }
+    ++b->captures;
+    return e;
+}
+
+// Whether some member draws Eq. 4's noise.
+void batch_noise(lbm_batch *b)
+{
+    b->noise = 0;
+    for (const lbm_sim *s : b->sims)
+        if (s && s->d.noise_on) b->noise = 1;
+}
+
+// Whether member s can take the staged update, and its bulk stores.
+bool staged_ok(const lbm_sim *s) { return s->p.lattice == LBM_D2Q9 && !s->p.y_periodic; }
+bool bulk_store_ok(const lbm_sim *s)
+{
+    // measured: four 4096 x 2048 members 66.3 against 63.8 G node updates/s
+    // with bulk stores, but the 256-member ensemble of widths 256..2048 53.0
+    // against 56.7 (four CTAs per SM instead of five)
+    return s->p.precision == LBM_FP32 && s->p.width % 4 == 0 && s->p.width >= 2048;
+}
+
+// The plain-load update's table for the current members (unpadded): about
+// two waves of its kernel for the whole batch, dealt by lattice area, each
+// member a multiple of its column tiles. `upd_bound`: the most entries any
+// subset of the members can need (a member's entries exceed its share of
+// the two waves by less than its column tiles).
+void batch_entries(const lbm_batch *b, std::vector<int4> &upd, long long *upd_bound)
+{
+    const KernelTable *kt = b->kt;
     const int bps = std::max(1, kt->update_blocks_per_sm());
     double area = 0.0;
-    for (const lbm_sim *s : b->sims) area += (double)s->p.width * (double)s->p.height;
-    const double target = 2.0 * nsm * bps;
-    std::vector<int4> upd, inj, pln;
-    // planners: a simulation whose own planner grid is larger than two blocks
-    // plans with that grid, the others with one block each (no grid barrier);
-    // the grids are scaled down together until all fit at once (the
-    // cooperative launch needs every block resident)
-    const int pbs = std::max(1, kt->plan_blocks_per_sm());
-    const long long cap = (long long)pbs * nsm;
-    long long want = 0;
-    for (const lbm_sim *s : b->sims) want += s->d.plan_grid > 2 ? s->d.plan_grid : 1;
-    b->plan_coop = 0;
-    for (size_t i = 0; i < b->sims.size(); ++i) {
-        const int own = b->sims[i]->d.plan_grid > 2 ? b->sims[i]->d.plan_grid : 1;
-        int g = want <= cap ? own : (int)std::max<long long>(1, own * (cap - (long long)b->sims.size()) / want);
-        if (g < 1) g = 1;
-        if (g > 1) b->plan_coop = 1;
-        for (int j = 0; j < g; ++j) pln.push_back(make_int4((int)i, j, g, 0));
-    }
-    if ((long long)pln.size() > cap) { // (never, by the scaling above; one block each then)
-        pln.clear();
-        b->plan_coop = 0;
-        for (size_t i = 0; i < b->sims.size(); ++i) pln.push_back(make_int4((int)i, 0, 1, 0));
-    }
+    for (const lbm_sim *s : b->sims)
+        if (s) area += (double)s->p.width * (double)s->p.height;
+    const double target = 2.0 * b->nsm * bps;
+    upd.clear();
+    *upd_bound = (long long)target;
     for (size_t i = 0; i < b->sims.size(); ++i) {
         const lbm_sim *s = b->sims[i];
+        if (!s) continue;
         const int ncx = (s->p.width + kt->update_tile_x - 1) / kt->update_tile_x;
+        *upd_bound += ncx;
         const double share = target * (double)s->p.width * (double)s->p.height / area;
         const int nbu = std::max(1, (int)std::lround(share / ncx)) * ncx;
         for (int j = 0; j < nbu; ++j) upd.push_back(make_int4((int)i, j, nbu, 0));
-        const int nbi = std::max(1, (s->L.ns_max + 1023) / 1024);
-        for (int j = 0; j < nbi; ++j) inj.push_back(make_int4((int)i, j, nbi, 0));
     }
-    const size_t n = b->sims.size();
-    const size_t off_u = align256(n * sizeof(SimDev));
-    const size_t off_i = align256(off_u + upd.size() * sizeof(int4));
-    const size_t off_p = align256(off_i + inj.size() * sizeof(int4));
-    const size_t off_m = align256(off_p + pln.size() * sizeof(int4)); // tensor maps (128-byte aligned)
-    const size_t off_c = align256(off_m + (b->tma ? 4 * n : 0) * sizeof(CUtensorMap)); // member constants
-    std::vector<CUtensorMap> maps(b->tma ? 4 * n : 0);
-    std::vector<MemberConst> mcs(b->tma ? n : 0);
-    for (size_t i = 0; i < n && b->tma; ++i) {
-        const lbm_sim *s = b->sims[i];
-        MemberConst &c = mcs[i];
-        std::memset(&c, 0, sizeof(c));
-        c.f[0] = s->d.f[0];
-        c.f[1] = s->d.f[1];
-        c.mask = s->d.mask;
-        c.sc = s->d.sc;
-        c.P = s->d.P;
-        c.W = s->d.W;
-        c.H = s->d.H;
-        c.Wp = s->d.Wp;
-        c.MW = s->d.MW;
-        c.key0 = s->d.key0;
-        c.key1 = s->d.key1;
-        c.sim = s->d.sim;
-        c.negfix = s->d.negfix;
-        c.rho_c = s->d.f_rho_c;
-        c.om1 = s->d.f_om1;
-        c.ow1 = s->d.f_ow1;
-        c.ow5 = s->d.f_ow5;
-        c.cmu = s->d.f_cmu;
-        c.two_sigma = s->d.f_two_sigma;
-        for (int k = 0; k < 3; ++k) c.pop_shift[k] = s->d.pop_shift[k];
-        for (int c = 0; c < 2; ++c) {
-            char *base_c = (char *)s->d.f[c] - (size_t)kXO * s->L.elem;
-            if (!encode_population_map(&maps[4 * i + c], base_c, s->d.Wp, s->d.Wp, s->d.H, s->d.P, s->L.Q,
-                                       kTmaBoxX + 8, 4, s->p.precision))
-                return cudaErrorInvalidValue;
-            // bulk stores of a tile's 128 columns, cut at x = W - 1
-            if (b->tstore && !encode_population_map(&maps[4 * i + 2 + c], base_c, s->p.width + kXO, s->d.Wp, s->d.H,
-                                                    s->d.P, s->L.Q, kTmaBoxX, 2, s->p.precision))
-                return cudaErrorInvalidValue;
+}
+
+// Slot i's SimDev, MemberConst and tensor maps (zeros for an empty slot).
+cudaError_t batch_slot(lbm_batch *b, size_t i)
+{
+    const lbm_sim *s = b->sims[i];
+    std::memset(&b->h_ds[i], 0, sizeof(SimDev));
+    if (s) b->h_ds[i] = s->d;
+    if (!b->tma) return cudaSuccess;
+    MemberConst &c = b->h_mc[i];
+    std::memset(&c, 0, sizeof(c));
+    std::memset(&b->h_maps[4 * i], 0, 4 * sizeof(CUtensorMap));
+    if (!s) return cudaSuccess;
+    c.f[0] = s->d.f[0];
+    c.f[1] = s->d.f[1];
+    c.mask = s->d.mask;
+    c.sc = s->d.sc;
+    c.P = s->d.P;
+    c.W = s->d.W;
+    c.H = s->d.H;
+    c.Wp = s->d.Wp;
+    c.MW = s->d.MW;
+    c.key0 = s->d.key0;
+    c.key1 = s->d.key1;
+    c.sim = s->d.sim;
+    c.negfix = s->d.negfix;
+    c.rho_c = s->d.f_rho_c;
+    c.om1 = s->d.f_om1;
+    c.ow1 = s->d.f_ow1;
+    c.ow5 = s->d.f_ow5;
+    c.cmu = s->d.f_cmu;
+    c.two_sigma = s->d.f_two_sigma;
+    for (int k = 0; k < 3; ++k) c.pop_shift[k] = s->d.pop_shift[k];
+    for (int h = 0; h < 2; ++h) {
+        char *base_c = (char *)s->d.f[h] - (size_t)kXO * s->L.elem;
+        if (!encode_population_map(&b->h_maps[4 * i + h], base_c, s->d.Wp, s->d.Wp, s->d.H, s->d.P, s->L.Q,
+                                   kTmaBoxX + 8, 4, s->p.precision))
+            return cudaErrorInvalidValue;
+        // bulk stores of a tile's 128 columns, cut at x = W - 1
+        if (b->tstore && !encode_population_map(&b->h_maps[4 * i + 2 + h], base_c, s->p.width + kXO, s->d.Wp,
+                                                s->d.H, s->d.P, s->L.Q, kTmaBoxX, 2, s->p.precision))
+            return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+// Brings the device tables up to date with the slots: recomputes the entries,
+// lays the tables out again (and captures the graphs again) if one outgrows
+// its room or the planner launch must become cooperative, pads each table
+// with unused entries and copies everything over, stream-ordered on the
+// batch's stream after the steps already enqueued.
+cudaError_t batch_refresh(lbm_batch *b, bool relayout)
+{
+    std::vector<int4> upd;
+    long long upd_bound = 0;
+    batch_entries(b, upd, &upd_bound);
+    if (b->tma) upd.clear(); // (the staged update deals the tiles itself)
+    if (!relayout) relayout = (int)upd.size() > b->nb_upd;
+    cudaError_t e = cudaSuccess;
+    if (relayout) {
+        // room: enough for any subset of the members (members that leave
+        // never force a new layout), twice what they use when growing a
+        // layout that had some (a batch that gains members regrows rarely)
+        const bool grow = b->dev_mem != nullptr;
+        auto room = [&](long long need, int old) {
+            return (int)std::max<long long>(std::max<long long>(1, old), grow ? 2 * need : need);
+        };
+        b->nb_upd = b->tma ? std::max(1, b->nb_upd) : room(std::max<long long>(upd_bound, (long long)upd.size()),
+                                                           b->nb_upd);
+        const size_t n = b->sims.size();
+        const size_t off_u = align256(n * sizeof(SimDev));
+        const size_t off_m = align256(off_u + (size_t)b->nb_upd * sizeof(int4)); // tensor maps (128-byte aligned)
+        const size_t off_c = align256(off_m + (b->tma ? 4 * n : 0) * sizeof(CUtensorMap)); // member constants
+        const size_t bytes = off_c + (b->tma ? n : 0) * sizeof(MemberConst);
+        if (b->dev_mem) {
+            e = cudaFreeAsync(b->dev_mem, b->origin);
+            b->dev_mem = nullptr;
+            if (e != cudaSuccess) return e;
         }
+        e = cudaMallocAsync(&b->dev_mem, bytes, b->origin);
+        if (e != cudaSuccess) return e;
+        char *base = (char *)b->dev_mem;
+        b->ds = (SimDev *)base;
+        b->bm_upd = (int4 *)(base + off_u);
+        b->maps = b->tma ? (CUtensorMap *)(base + off_m) : nullptr;
+        b->mc = b->tma ? (MemberConst *)(base + off_c) : nullptr;
+        b->h_maps.assign(b->tma ? 4 * n : 0, CUtensorMap{});
+        b->h_mc.assign(b->tma ? n : 0, MemberConst{});
+        b->h_ds.assign(n, SimDev{});
+        for (size_t i = 0; i < n && e == cudaSuccess; ++i) e = batch_slot(b, i);
+        if (e != cudaSuccess) return e;
     }
-    // stream-ordered on the batch's stream (no device-wide synchronisation:
-    // batches are built while other work runs, as in the serving loop)
-    e = cudaMallocAsync(&b->dev_mem, off_c + mcs.size() * sizeof(MemberConst), b->origin);
-    if (e != cudaSuccess) return e;
-    std::vector<SimDev> ds(n);
-    for (size_t i = 0; i < n; ++i) ds[i] = b->sims[i]->d;
-    char *base = (char *)b->dev_mem;
-    e = cudaMemcpyAsync(base, ds.data(), n * sizeof(SimDev), cudaMemcpyHostToDevice, b->origin);
+    const int4 unused = make_int4(-1, 0, 1, 0);
+    upd.resize((size_t)b->nb_upd, unused);
+    b->h_upd.swap(upd);
+    const size_t n = b->sims.size();
+    e = cudaMemcpyAsync(b->ds, b->h_ds.data(), n * sizeof(SimDev), cudaMemcpyHostToDevice, b->origin);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + off_u, upd.data(), upd.size() * sizeof(int4), cudaMemcpyHostToDevice, b->origin);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + off_i, inj.data(), inj.size() * sizeof(int4), cudaMemcpyHostToDevice, b->origin);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + off_p, pln.data(), pln.size() * sizeof(int4), cudaMemcpyHostToDevice, b->origin);
-    if (e == cudaSuccess && !maps.empty())
-        e = cudaMemcpyAsync(base + off_m, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(b->bm_upd, b->h_upd.data(), b->h_upd.size() * sizeof(int4), cudaMemcpyHostToDevice,
                             b->origin);
-    if (e == cudaSuccess && !mcs.empty())
-        e = cudaMemcpyAsync(base + off_c, mcs.data(), mcs.size() * sizeof(MemberConst), cudaMemcpyHostToDevice,
+    if (e == cudaSuccess && b->tma)
+        e = cudaMemcpyAsync(b->maps, b->h_maps.data(), b->h_maps.size() * sizeof(CUtensorMap),
+                            cudaMemcpyHostToDevice, b->origin);
+    if (e == cudaSuccess && b->tma)
+        e = cudaMemcpyAsync(b->mc, b->h_mc.data(), b->h_mc.size() * sizeof(MemberConst), cudaMemcpyHostToDevice,
                             b->origin);
-    // the host arrays go out of scope: wait for the copies from them
+    // the host copies change with the next member: wait for the copies from them
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->origin);
-    b->ds = (const SimDev *)base;
-    b->bm_upd = (const int4 *)(base + off_u);
-    b->bm_inj = (const int4 *)(base + off_i);
-    b->nb_upd = (int)upd.size();
-    b->nb_inj = (int)inj.size();
-    b->bm_plan = (const int4 *)(base + off_p);
-    b->nb_plan = (int)pln.size();
-    b->maps = maps.empty() ? nullptr : (const CUtensorMap *)(base + off_m);
-    b->mc = mcs.empty() ? nullptr : (const MemberConst *)(base + off_c);
-    b->tma_grid = (b->tstore ? kTmaBatchCtasPerSmStore : kTmaBatchCtasPerSm) * nsm;
+    b->tma_grid = (b->tstore ? kTmaBatchCtasPerSmStore : kTmaBatchCtasPerSm) * b->nsm;
+    if (e == cudaSuccess && relayout) e = batch_recapture(b);
     return e;
+}
+
+lbm_batch *batch_new(int slots, int device, cudaStream_t user)
+{
+    lbm_batch *b = new lbm_batch();
+    b->sims.assign((size_t)slots, nullptr);
+    b->members = 0;
+    b->device = device;
+    b->kt = nullptr;
+    b->user = user;
+    b->origin = nullptr;
+    b->exec[0][0] = b->exec[0][1] = b->exec[1][0] = b->exec[1][1] = nullptr;
+    b->captures = 0;
+    b->fork = nullptr;
+    b->fused = true;
+    b->dev_mem = nullptr;
+    b->ds = nullptr;
+    b->bm_upd = nullptr;
+    b->nb_upd = b->plan_cap = 0;
+    b->tma = false;
+    b->mc = nullptr;
+    b->maps = nullptr;
+    b->noise = b->tstore = b->tma_grid = 0;
+    b->nsm = 0;
+    return b;
+}
+
+// The streams, events and first tables and graphs of a new batch.
+cudaError_t batch_init(lbm_batch *b)
+{
+    cudaError_t e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+    // one-time kernel attributes are set outside the capture
+    for (lbm_sim *s : b->sims)
+        if (e == cudaSuccess && s && s->use_tma) e = s->kt->tma_prepare(s->d, s->tma_variant);
+    // branch streams and join events for the branch form; the batched form
+    // needs one event (a stream wait takes the event's record at the call)
+    const size_t nj = b->fused ? 1 : b->sims.size();
+    for (size_t i = 0; i < nj && e == cudaSuccess; ++i) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->join.push_back(ev);
+        if (b->fused || e != cudaSuccess) continue;
+        cudaStream_t st = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->branch.push_back(st);
+    }
+    if (e != cudaSuccess) return e;
+    if (!b->fused) return batch_recapture(b);
+    // the cooperative planner launch: every resident block
+    b->plan_cap = std::max(1, b->kt->plan_blocks_per_sm(1)) * b->nsm;
+    if (b->members == 0) {
+        // an empty batch: room for members to come (the plain-load update's
+        // two waves and 32 column tiles more per slot)
+        const int bps = std::max(1, b->kt->update_blocks_per_sm());
+        b->nb_upd = 2 * bps * b->nsm + 32 * (int)b->sims.size();
+    }
+    return batch_refresh(b, true);
 }
 } // namespace
 
@@ -1122,60 +1264,24 @@ int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **
             if (sims[j] == sims[i]) return LBM_ERR_INVALID_ARG;
     }
     CK(cudaSetDevice(sims[0]->device));
-    lbm_batch *b = new lbm_batch();
-    b->sims.assign(sims, sims + n);
-    b->device = sims[0]->device;
-    b->user = (cudaStream_t)stream;
-    b->origin = nullptr;
-    b->exec[0] = b->exec[1] = nullptr;
-    b->fork = nullptr;
-    b->dev_mem = nullptr;
-    b->ds = nullptr;
-    b->bm_upd = b->bm_inj = b->bm_plan = nullptr;
-    b->nb_upd = b->nb_inj = b->nb_plan = 0;
-    b->plan_coop = 0;
+    lbm_batch *b = batch_new(n, sims[0]->device, (cudaStream_t)stream);
+    for (int32_t i = 0; i < n; ++i) b->sims[i] = sims[i];
+    b->members = n;
+    b->kt = sims[0]->kt;
     // one launch per kernel for the whole batch when the members share the
-    // storage type (the plain-load update; the results are the same as the
-    // TMA-staged one's, bit for bit)
-    b->fused = true;
+    // storage type (the plain-load or the TMA-staged update: the same results,
+    // bit for bit), the TMA-staged one when every member can take it
     for (int32_t i = 1; i < n; ++i)
         if (sims[i]->kt != sims[0]->kt) b->fused = false;
-    // the TMA-staged batched update when every member can take it
-    b->tma = b->fused && sims[0]->kt->batch_update_tma && n <= kTmaBatchMaxSims;
-    b->noise = 0;
-    // bulk stores when every member is FP32, at least 2048 wide and a
-    // multiple of 4 wide (see lbm_create); measured: four 4096 x 2048 members
-    // 66.3 against 63.8 G node updates/s, but the 256-member ensemble of
-    // widths 256..2048 53.0 against 56.7 (four CTAs per SM instead of five)
-    b->tstore = b->tma && sims[0]->p.precision == LBM_FP32 ? 1 : 0;
-    for (int32_t i = 0; i < n; ++i)
-        if (sims[i]->p.width % 4 || sims[i]->p.width < 2048) b->tstore = 0;
-    b->maps = nullptr;
-    b->mc = nullptr;
-    b->tma_grid = 0;
+    b->tma = b->fused && b->kt->batch_update_tma && n <= kTmaBatchMaxSims;
+    b->tstore = b->tma ? 1 : 0;
     for (int32_t i = 0; i < n; ++i) {
-        if (sims[i]->p.lattice != LBM_D2Q9 || sims[i]->p.y_periodic) b->tma = false;
-        if (sims[i]->d.noise_on) b->noise = 1;
+        if (!staged_ok(sims[i])) b->tma = false;
+        if (!bulk_store_ok(sims[i])) b->tstore = 0;
     }
-    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
-    if (e == cudaSuccess && b->fused) e = batch_tables(b);
-    // one-time kernel attributes are set outside the capture
-    for (int32_t i = 0; i < n && e == cudaSuccess; ++i)
-        if (sims[i]->use_tma) e = sims[i]->kt->tma_prepare(sims[i]->d, sims[i]->tma_variant);
-    // branch streams and join events for the branch form; the batched form
-    // needs one event (a stream wait takes the event's record at the call)
-    for (int32_t i = 0; i < (b->fused ? 1 : n) && e == cudaSuccess; ++i) {
-        cudaEvent_t ev = nullptr;
-        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) b->join.push_back(ev);
-        if (b->fused || e != cudaSuccess) continue;
-        cudaStream_t st = nullptr;
-        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) b->branch.push_back(st);
-    }
-    if (e == cudaSuccess) e = batch_capture(b, 1, &b->exec[0]);
-    if (e == cudaSuccess) e = batch_capture(b, kBatchChain, &b->exec[1]);
+    batch_noise(b);
+    if (!b->tma) b->tstore = 0;
+    const cudaError_t e = batch_init(b);
     if (e != cudaSuccess) {
         lbm_batch_destroy(b);
         return cuda_fail(e);
@@ -1184,25 +1290,118 @@ int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **
     return LBM_OK;
 }
 
+int lbm_batch_create_empty(int32_t slots, int32_t lattice, int32_t precision, void *stream, lbm_batch **out)
+{
+    if (!out || slots < 1 || slots > kMaxBatchSlots) return LBM_ERR_INVALID_ARG;
+    if ((lattice != LBM_D2Q9 && lattice != LBM_D2Q7) || precision < LBM_FP32 || precision > LBM_BF16)
+        return LBM_ERR_INVALID_ARG;
+    if (lattice == LBM_D2Q7 && precision != LBM_FP32 && precision != LBM_FP64) return LBM_ERR_INVALID_ARG;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    lbm_batch *b = batch_new(slots, dev, (cudaStream_t)stream);
+    b->kt = kernel_table(lattice, precision);
+    b->tma = b->kt->batch_update_tma && slots <= kTmaBatchMaxSims;
+    const cudaError_t e = batch_init(b);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return cuda_fail(e);
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_attach(lbm_batch *b, lbm_sim *s, int32_t *slot)
+{
+    if (!b || !s || !b->fused || s->kt != b->kt || s->device != b->device || s->timing) return LBM_ERR_INVALID_ARG;
+    int free_slot = -1;
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        if (b->sims[i] == s) return LBM_ERR_INVALID_ARG;
+        if (!b->sims[i] && free_slot < 0) free_slot = (int)i;
+    }
+    if (free_slot < 0) return LBM_ERR_BATCH_FULL;
+    CK(cudaSetDevice(b->device));
+    // a member that the current graphs cannot step: capture them again
+    bool relayout = false;
+    if (b->tma && !staged_ok(s)) {
+        b->tma = false;
+        b->tstore = 0;
+        relayout = true;
+    }
+    if (b->tstore && !bulk_store_ok(s)) {
+        b->tstore = 0;
+        relayout = true;
+    }
+    if (s->use_tma) CK(s->kt->tma_prepare(s->d, s->tma_variant));
+    // the batch's steps come after what the member's stream holds
+    CK(cudaEventRecord(b->join[0], s->stream));
+    CK(cudaStreamWaitEvent(b->origin, b->join[0], 0));
+    b->sims[(size_t)free_slot] = s;
+    ++b->members;
+    cudaError_t e = relayout ? cudaSuccess : batch_slot(b, (size_t)free_slot);
+    if (e == cudaSuccess) e = batch_refresh(b, relayout);
+    if (e != cudaSuccess) {
+        b->sims[(size_t)free_slot] = nullptr;
+        --b->members;
+        return cuda_fail(e);
+    }
+    batch_noise(b);
+    if (slot) *slot = free_slot;
+    return LBM_OK;
+}
+
+int lbm_batch_detach(lbm_batch *b, lbm_sim *s)
+{
+    if (!b || !s || !b->fused) return LBM_ERR_INVALID_ARG;
+    size_t i = 0;
+    while (i < b->sims.size() && b->sims[i] != s) ++i;
+    if (i == b->sims.size()) return LBM_ERR_INVALID_ARG;
+    CK(cudaSetDevice(b->device));
+    b->sims[i] = nullptr;
+    --b->members;
+    batch_noise(b);
+    cudaError_t e = batch_slot(b, i);
+    if (e == cudaSuccess) e = batch_refresh(b, false);
+    // what the member's stream gets next comes after the batch's steps
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->origin);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, b->fork, 0);
+    return e == cudaSuccess ? LBM_OK : cuda_fail(e);
+}
+
+int lbm_batch_members(const lbm_batch *b)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    return b->members;
+}
+
+int lbm_batch_captures(const lbm_batch *b)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    return b->captures;
+}
+
 int lbm_batch_step(lbm_batch *b, int64_t nsteps)
 {
     if (!b || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    if (b->members == 0 || nsteps == 0) return LBM_OK;
     CK(cudaSetDevice(b->device));
-    // after whatever the caller's stream and each simulation's own stream hold ...
+    // after whatever the caller's stream and each member's own stream hold ...
     CK(cudaEventRecord(b->fork, b->user));
     CK(cudaStreamWaitEvent(b->origin, b->fork, 0));
     for (size_t i = 0; i < b->sims.size(); ++i) {
+        if (!b->sims[i]) continue;
         cudaEvent_t ev = b->join[b->fused ? 0 : i];
         CK(cudaEventRecord(ev, b->sims[i]->stream));
         CK(cudaStreamWaitEvent(b->origin, ev, 0));
     }
+    cudaGraphExec_t *exec = b->exec[b->exec[1][0] ? b->noise : 0];
     int64_t left = nsteps;
-    for (; left >= kBatchChain; left -= kBatchChain) CK(cudaGraphLaunch(b->exec[1], b->origin));
-    for (; left > 0; --left) CK(cudaGraphLaunch(b->exec[0], b->origin));
+    for (; left >= kBatchChain; left -= kBatchChain) CK(cudaGraphLaunch(exec[1], b->origin));
+    for (; left > 0; --left) CK(cudaGraphLaunch(exec[0], b->origin));
     // ... and before whatever comes next on it
     CK(cudaEventRecord(b->fork, b->origin));
     CK(cudaStreamWaitEvent(b->user, b->fork, 0));
     for (lbm_sim *s : b->sims) {
+        if (!s) continue;
         CK(cudaStreamWaitEvent(s->stream, b->fork, 0));
         for (int64_t k = 0; k < nsteps; ++k) advance_host_step(s);
     }
@@ -1220,13 +1419,17 @@ int lbm_batch_destroy(lbm_batch *b)
     if (!b) return LBM_OK;
     cudaSetDevice(b->device);
     if (b->origin) cudaStreamSynchronize(b->origin);
-    for (int i = 0; i < 2; ++i)
-        if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+    for (auto &pair : b->exec)
+        for (cudaGraphExec_t g : pair)
+            if (g) cudaGraphExecDestroy(g);
     for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->dev_mem) cudaFreeAsync(b->dev_mem, b->origin);
-    if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->origin) {
+        cudaStreamSynchronize(b->origin);
+        cudaStreamDestroy(b->origin);
+    }
     delete b;
     return LBM_OK;
 }

@@ -145,6 +145,10 @@ struct DevScalars {
     long long wait_budget;
     int wait_test;
     int pad2;
+    // a batch's estimate of this member's planner work (candidates drawn for
+    // the latest selection): copied from pend_cand by the batched injection
+    // launch, read by the batched planner launches that follow it
+    long long plan_work;
 };
 enum { WAIT_TEST_COPIES = 1, WAIT_TEST_BARRIER = 2 };
 // Default budget of the bounded waits: about two seconds at 2 GHz.
@@ -231,7 +235,7 @@ struct KernelTable {
     cudaError_t (*inject)(const SimDev &, cudaStream_t);
     cudaError_t (*update)(const SimDev &, cudaStream_t);
     cudaError_t (*fields)(const SimDev &, int cur, double *rho, double *ux, double *uy, cudaStream_t);
-    int (*plan_blocks_per_sm)();
+    int (*plan_blocks_per_sm)(int batch); // of the own planner (0) or the batched one (1)
     int (*update_blocks_per_sm)();
     int update_tile_x; // columns per block of the update kernel
     // TMA-staged update (lbm_update_tma.cuh, for D2Q7 lbm_update7_tma.cuh;
@@ -252,9 +256,9 @@ struct KernelTable {
     // block, blocks) of the update's (a multiple of each simulation's column
     // tiles), the injection's or the planner's block table (the planner: one
     // block per simulation, or its own grid, then cooperatively).
-    cudaError_t (*batch_inject)(const SimDev *ds, const int4 *bm, int nb, cudaStream_t);
+    cudaError_t (*batch_inject)(const SimDev *ds, int nslots, int grid, cudaStream_t);
     cudaError_t (*batch_update)(const SimDev *ds, const int4 *bm, int nb, cudaStream_t);
-    cudaError_t (*batch_plan)(const SimDev *ds, const int4 *bm, int nb, int coop, cudaStream_t);
+    cudaError_t (*batch_plan)(const SimDev *ds, int nslots, int cap, int coop, cudaStream_t);
     // the TMA-staged update of a whole batch (lbm_update_tma_batch.cuh; null
     // where there is none): mc[m] member m's constants, maps[4 m + b] loads its
     // copy b in boxes of (kTmaBoxX + 8) x 4 x 9, maps[4 m + 2 + b] stores into
@@ -284,6 +288,7 @@ constexpr int kPlanMaxBlocks = 1024;
 // The TMA-staged batched update: members one launch takes (its shared-memory
 // tables) and CTAs per SM.
 constexpr int kTmaBatchMaxSims = 256;
+constexpr int kMaxBatchSlots = 4096; // slots of a batch (the staged batched update: kTmaBatchMaxSims)
 constexpr int kTmaBatchCtasPerSm = 5;
 constexpr int kTmaBatchCtasPerSmStore = 4; // its bulk-store form
 

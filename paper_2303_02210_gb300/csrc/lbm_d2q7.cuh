@@ -496,6 +496,7 @@ template <typename S, int TPB, int NR>
 __global__ void __launch_bounds__(TPB) k_update7_batch(const SimDev *__restrict__ ds, const int4 *__restrict__ bm)
 {
     const int4 a = bm[blockIdx.x];
+    if (a.x < 0) return; // an unused entry
     update7_body<S, TPB, NR>(ds[a.x], a.y, a.z);
 }
 

@@ -745,11 +745,13 @@ __global__ void __launch_bounds__(TPB) k_update(SimDev d)
 
 // The updates of a batch of simulations in one launch: block b works for
 // simulation bm[b].x as its block bm[b].y of bm[b].z, a multiple of that
-// simulation's column tiles (a table built once per batch).
+// simulation's column tiles (a table rebuilt when the members change;
+// bm[b].x < 0: an unused entry, nothing to do).
 template <typename S, int TPB, int NR>
 __global__ void __launch_bounds__(TPB) k_update_batch(const SimDev *__restrict__ ds, const int4 *__restrict__ bm)
 {
     const int4 a = bm[blockIdx.x];
+    if (a.x < 0) return;
     update_body<S, TPB, NR>(ds[a.x], a.y, a.z);
 }
 

@@ -48,9 +48,9 @@ struct Launch {
         k_fields<S><<<4 * 152, 256, 0, s>>>(d, cur, rho, ux, uy);
         return cudaGetLastError();
     }
-    static cudaError_t batch_inject(const SimDev *ds, const int4 *bm, int nb, cudaStream_t s)
+    static cudaError_t batch_inject(const SimDev *ds, int nslots, int grid, cudaStream_t s)
     {
-        k_inject_batch<S><<<nb, 128, 0, s>>>(ds, bm);
+        k_inject_batch<S><<<grid, INJ_NT, 0, s>>>(ds, nslots);
         return cudaGetLastError();
     }
     static cudaError_t batch_update(const SimDev *ds, const int4 *bm, int nb, cudaStream_t s)
@@ -58,9 +58,9 @@ struct Launch {
         k_update_batch<S, UPD_TPB, UPD_NR><<<nb, UPD_TPB, 0, s>>>(ds, bm);
         return cudaGetLastError();
     }
-    static cudaError_t batch_plan(const SimDev *ds, const int4 *bm, int nb, int coop, cudaStream_t s)
+    static cudaError_t batch_plan(const SimDev *ds, int nslots, int cap, int coop, cudaStream_t s)
     {
-        return launch_plan_batch<S>(ds, bm, nb, coop, s);
+        return launch_plan_batch<S>(ds, nslots, cap, coop, s);
     }
     static int update_blocks_per_sm()
     {
@@ -130,9 +130,9 @@ struct Launch7 {
         k_fields7<S><<<4 * 152, 256, 0, s>>>(d, cur, rho, ux, uy);
         return cudaGetLastError();
     }
-    static cudaError_t batch_inject(const SimDev *ds, const int4 *bm, int nb, cudaStream_t s)
+    static cudaError_t batch_inject(const SimDev *ds, int nslots, int grid, cudaStream_t s)
     {
-        k_inject_batch<S, Lat7><<<nb, 128, 0, s>>>(ds, bm);
+        k_inject_batch<S, Lat7><<<grid, INJ_NT, 0, s>>>(ds, nslots);
         return cudaGetLastError();
     }
     static cudaError_t batch_update(const SimDev *ds, const int4 *bm, int nb, cudaStream_t s)
@@ -140,9 +140,9 @@ struct Launch7 {
         k_update7_batch<S, UPD_TPB, UPD_NR><<<nb, UPD_TPB, 0, s>>>(ds, bm);
         return cudaGetLastError();
     }
-    static cudaError_t batch_plan(const SimDev *ds, const int4 *bm, int nb, int coop, cudaStream_t s)
+    static cudaError_t batch_plan(const SimDev *ds, int nslots, int cap, int coop, cudaStream_t s)
     {
-        return launch_plan_batch<S, Lat7>(ds, bm, nb, coop, s);
+        return launch_plan_batch<S, Lat7>(ds, nslots, cap, coop, s);
     }
     static int update_blocks_per_sm()
     {

@@ -513,20 +513,34 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             }
         }
         acc = total;
-        // more draws, a grid-wide round at a time, while short of n_s
+        // more draws, a grid-wide round at a time, while short of n_s: a
+        // round is PLAN_R candidates per thread, thread tid of block blk
+        // taking the PLAN_R consecutive ones from base + (blk PLAN_NT + tid)
+        // PLAN_R, so that one block scan per round ranks them in draw order
+        // (a member that accepts few candidates, whose growth starves, draws
+        // up to the cap every step: fewer rounds, fewer barriers)
         long long base = kc;
         int round = 1;
+        __syncthreads(); // (the first pass's entries of s_key, s_lr are read by other threads than the next writers)
         while (acc < ns && base < cap) { // uniform
-            const long long k = base + (long long)blk * PLAN_NT + tid;
-            bool a = false;
-            uint32_t key = 0u;
-            if (k < cap) {
-                const Candidate c = draw_candidate<LT>(d, k, tn, ylo, nwin);
-                a = plan_accept<S, LT>(d, f, nyr, c);
-                key = pack_key(c.x, c.y, c.pair);
+            const long long k0 = base + ((long long)blk * PLAN_NT + tid) * PLAN_R;
+            int mine = 0;
+#pragma unroll 1
+            for (int i = 0; i < PLAN_R; ++i) {
+                const long long k = k0 + i;
+                bool a = false;
+                uint32_t key = 0u;
+                if (k < cap) {
+                    const Candidate c = draw_candidate<LT>(d, k, tn, ylo, nwin);
+                    a = plan_accept<S, LT>(d, f, nyr, c);
+                    key = pack_key(c.x, c.y, c.pair);
+                }
+                s_key[tid * PLAN_R + i] = key;
+                s_lr[tid * PLAN_R + i] = a ? mine : -1;
+                mine += a ? 1 : 0;
             }
             int tot_r;
-            const int pr = plan_block_exscan(a ? 1 : 0, &tot_r, s_i);
+            const int pr = plan_block_exscan(mine, &tot_r, s_i);
             int *cnt = d.pl_cnt + (round & 1) * kPlanMaxBlocks;
             if (tid == 0) cnt[blk] = tot_r;
             plan_grid_sync(sc, &s_dead, G, wait_budget, wait_extra);
@@ -538,11 +552,16 @@ __device__ __forceinline__ void plan_body(const SimDev &d, int init, int G, int 
             }
             bf = plan_block_sum(bf, s_ll);
             tt = plan_block_sum(tt, s_ll);
-            const long long rank = acc + bf + pr;
-            if (a && rank == ns - 1) s_kstop = (unsigned long long)(k + 1);
-            if (a && rank < ns) plan_select<R, LT>(d, key, (int)rank, buf, nyr);
+#pragma unroll 1
+            for (int i = 0; i < PLAN_R; ++i) {
+                const int lr = s_lr[tid * PLAN_R + i];
+                if (lr < 0) continue;
+                const long long rank = acc + bf + pr + lr;
+                if (rank == ns - 1) s_kstop = (unsigned long long)(k0 + i + 1);
+                if (rank < ns) plan_select<R, LT>(d, s_key[tid * PLAN_R + i], (int)rank, buf, nyr);
+            }
             acc += tt;
-            base += (long long)G * PLAN_NT;
+            base += (long long)G * PLAN_NT * PLAN_R;
             ++round;
         }
         __syncthreads();
@@ -633,25 +652,105 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
     plan_body<S, LT>(d, init, (int)gridDim.x, (int)blockIdx.x);
 }
 
-// The planners of a batch of simulations: block b plans simulation bm[b].x
-// as its block bm[b].y of bm[b].z. A simulation planned by one block has
-// barriers of its own; one planned by more uses the grid barrier on its own
-// arrival counter with the grid it uses when stepped alone (the counter
-// advances by that grid size per barrier), and the launch is cooperative so
-// that its blocks are resident together.
-template <typename S, typename LT = Lat9>
-__global__ void __launch_bounds__(PLAN_NT) k_plan_batch(const SimDev *__restrict__ ds, const int4 *__restrict__ bm)
+// The planners of a batch's slots, in two launches: a plain one in which
+// each member planned by one block gets a block, and a cooperative one (all
+// blocks resident at once) in which each member planned by more gets its
+// grid. The blocks are dealt on the device, every step, from the members'
+// planner work: w = the candidates drawn for the latest selection (plan_work,
+// copied by the injection launch before this one, so that it holds still
+// while the planners run) + the lattice width (the front scans) + a fixed
+// floor (the barriers and the commit). With m members and m <= cap (the
+// cooperative launch's blocks), all are planned there, member i by
+// G = 1 + floor(w (cap - m) / sum of w) blocks; with more members, by
+// G = floor(w cap / sum of w) blocks, and those with G < 2 by one block each
+// in the plain launch (G at most kPlanMaxBlocks). Every block computes
+// the same deal from the same integers and finds its member and its block
+// index by a prefix over the slots, in slot order; a member planned by more
+// blocks uses the grid barrier on its own arrival counter (reset at the end
+// of each launch, so the grid may change from step to step).
+constexpr long long kPlanWorkFloor = 4096;
+
+__device__ __forceinline__ long long plan_slot_work(const SimDev *__restrict__ ds, int i)
 {
-    const int4 a = bm[blockIdx.x];
-    plan_body<S, LT>(ds[a.x], 0, a.z, a.y);
+    const DevScalars *sc = ds[i].sc;
+    if (!sc) return -1; // an empty slot
+    const long long c = sc->plan_work;
+    return (c > 0 ? c : 0) + ds[i].W + kPlanWorkFloor;
 }
 
-// (coop: some simulation is planned by more than one block)
+__device__ __forceinline__ int plan_slot_grid(long long w, long long wsum, int m, int cap)
+{
+    if (w < 0) return 0;
+    const long long g = m <= cap ? 1 + w * (long long)(cap - m) / wsum : w * (long long)cap / wsum;
+    return (int)(g < kPlanMaxBlocks ? g : kPlanMaxBlocks);
+}
+
+// Whether a slot's member is planned in the cooperative launch.
+__device__ __forceinline__ bool plan_slot_coop(int g, int m, int cap) { return m <= cap ? g >= 1 : g >= 2; }
+
 template <typename S, typename LT = Lat9>
-cudaError_t launch_plan_batch(const SimDev *ds, const int4 *bm, int nb, int coop, cudaStream_t s)
+__global__ void __launch_bounds__(PLAN_NT, 2) k_plan_batch(const SimDev *__restrict__ ds, int nslots, int cap, int coop)
+{
+    __shared__ int s_pre[kMaxBatchSlots + 1];
+    __shared__ long long s_red[PLAN_WARPS];
+    __shared__ int s_wi[PLAN_WARPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    long long wsum = 0, mm = 0;
+    for (int i = tid; i < nslots; i += PLAN_NT) {
+        const long long w = plan_slot_work(ds, i);
+        wsum += w > 0 ? w : 0;
+        mm += w >= 0 ? 1 : 0;
+    }
+    wsum = plan_block_sum(wsum, s_red);
+    const int m = (int)plan_block_sum(mm, s_red);
+    if (!coop && m <= cap) return; // (uniform: all members are in the cooperative launch)
+    // entries per slot: its grid in the cooperative launch, one block in the
+    // plain launch; their exclusive prefix over the slots
+    int run = 0;
+    for (int base = 0; base < nslots; base += PLAN_NT) {
+        const int i = base + tid;
+        int n = 0;
+        if (i < nslots) {
+            const long long w = plan_slot_work(ds, i);
+            const int g = plan_slot_grid(w, wsum, m, cap);
+            const bool c = plan_slot_coop(g, m, cap);
+            n = w < 0 ? 0 : (coop ? (c ? g : 0) : (c ? 0 : 1));
+        }
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_wi[warp] = incl;
+        __syncthreads();
+        int before = run + incl - n, chunk = 0;
+        for (int k = 0; k < PLAN_WARPS; ++k) {
+            if (k < warp) before += s_wi[k];
+            chunk += s_wi[k];
+        }
+        if (i < nslots) s_pre[i] = before;
+        run += chunk;
+        __syncthreads();
+    }
+    const int b = (int)blockIdx.x;
+    if (b >= run) return; // (uniform: an unused block)
+    int lo = 0, hi = nslots - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pre[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const int G = coop ? plan_slot_grid(plan_slot_work(ds, lo), wsum, m, cap) : 1;
+    plan_body<S, LT>(ds[lo], 0, G, b - s_pre[lo]);
+}
+
+// The plain launch (`coop` 0: a block per slot) or the cooperative one
+// (`coop` 1: `cap` blocks, at most the resident count).
+template <typename S, typename LT = Lat9>
+cudaError_t launch_plan_batch(const SimDev *ds, int nslots, int cap, int coop, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)nb);
+    cfg.gridDim = dim3((unsigned)(coop ? cap : nslots));
     cfg.blockDim = dim3(PLAN_NT);
     cfg.stream = s;
     cudaLaunchAttribute la[1];
@@ -659,7 +758,7 @@ cudaError_t launch_plan_batch(const SimDev *ds, const int4 *bm, int nb, int coop
     la[0].val.cooperative = 1;
     cfg.attrs = la;
     cfg.numAttrs = coop ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_plan_batch<S, LT>, ds, bm);
+    return cudaLaunchKernelEx(&cfg, k_plan_batch<S, LT>, ds, nslots, cap, coop);
 }
 
 // App. A step 3 for the update kernels that read the populations from global
@@ -667,35 +766,40 @@ cudaError_t launch_plan_batch(const SimDev *ds, const int4 *bm, int nb, int coop
 // (node, pair) of step t, right before the update of step t. Distinct
 // (node, pair) never share a slot (each slot streams into exactly one
 // direction of one node).
+// Division e (draw rank) of the step's selection.
 template <typename S, typename LT = Lat9>
-__device__ __forceinline__ void inject_body(const SimDev &d, int blk, int nblk)
+__device__ __forceinline__ void inject_division(const SimDev &d, S *f, int y_r, size_t buf, int e)
 {
     using R = arith_t<S>;
     const Pop<S> pc(d);
+    const int cnt = d.ev_count[buf + e];
+    if (cnt == 0) return; // a repeat, counted at its first rank
+    const uint32_t key = d.ev_key[buf + e];
+    const int x = key_x(key), y = key_y(key), p = key_pair(key);
+    const R add = (R)((double)cnt * d.half_cell);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = h == 0 ? LT::pa(p) : LT::pb(p);
+        const long long o = LT::slot(d, y_r, x, y, q);
+        // (the slot is in plane q or opp(q): one weight class)
+        const S v = pc.st(pc.ld(f[o], q) + add, q);
+        f[o] = v;
+        // the ghost copy of an edge column (read by the TMA-staged update)
+        const int xc = (int)((o % d.P) % d.Wp);
+        if (xc == 0) f[o + d.W] = v;
+        if (xc == d.W - 1) f[o - d.W] = v;
+    }
+}
+
+template <typename S, typename LT = Lat9>
+__device__ __forceinline__ void inject_body(const SimDev &d, int blk, int nblk)
+{
     const uint32_t t = (uint32_t)d.sc->step;
-    const int cur = (int)(t & 1u);
-    S *f = (S *)d.f[cur];
+    S *f = (S *)d.f[t & 1u];
     const int n = d.sc->rec_n, y_r = d.sc->y_r;
     const size_t buf = (size_t)(t & 1u) * (size_t)d.ns_max;
-    for (int e = blk * (int)blockDim.x + (int)threadIdx.x; e < n; e += nblk * (int)blockDim.x) {
-        const int cnt = d.ev_count[buf + e];
-        if (cnt == 0) continue; // a repeat, counted at its first rank
-        const uint32_t key = d.ev_key[buf + e];
-        const int x = key_x(key), y = key_y(key), p = key_pair(key);
-        const R add = (R)((double)cnt * d.half_cell);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int q = h == 0 ? LT::pa(p) : LT::pb(p);
-            const long long o = LT::slot(d, y_r, x, y, q);
-            // (the slot is in plane q or opp(q): one weight class)
-            const S v = pc.st(pc.ld(f[o], q) + add, q);
-            f[o] = v;
-            // the ghost copy of an edge column (read by the TMA-staged update)
-            const int xc = (int)((o % d.P) % d.Wp);
-            if (xc == 0) f[o + d.W] = v;
-            if (xc == d.W - 1) f[o - d.W] = v;
-        }
-    }
+    for (int e = blk * (int)blockDim.x + (int)threadIdx.x; e < n; e += nblk * (int)blockDim.x)
+        inject_division<S, LT>(d, f, y_r, buf, e);
 }
 
 template <typename S, typename LT = Lat9>
@@ -704,13 +808,63 @@ __global__ void k_inject(SimDev d)
     inject_body<S, LT>(d, (int)blockIdx.x, (int)gridDim.x);
 }
 
-// Block b of a batched launch works for simulation bm[b].x as its block
-// bm[b].y of bm[b].z (a table built once per batch).
+// The injections of a batch's slots in one launch: every block forms, in
+// shared memory, the exclusive prefix of the members' division counts (slot
+// after slot; an empty slot, ds[m].sc == nullptr, has none) and the grid
+// deals the batch's divisions, member after member, as one list. No table:
+// members may come and go, and their planner capacities play no part.
+constexpr int INJ_NT = 256;
 template <typename S, typename LT = Lat9>
-__global__ void k_inject_batch(const SimDev *__restrict__ ds, const int4 *__restrict__ bm)
+__global__ void __launch_bounds__(INJ_NT) k_inject_batch(const SimDev *__restrict__ ds, int nslots)
 {
-    const int4 a = bm[blockIdx.x];
-    inject_body<S, LT>(ds[a.x], a.y, a.z);
+    __shared__ int s_pre[kMaxBatchSlots + 1];
+    __shared__ int s_wsum[INJ_NT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int run = 0; // divisions of the slots before this chunk
+    for (int base = 0; base < nslots; base += INJ_NT) {
+        const int m = base + tid;
+        int n = 0;
+        if (m < nslots) {
+            const DevScalars *sc = ds[m].sc;
+            if (sc) n = sc->rec_n;
+        }
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        int before = run + incl - n, chunk = 0;
+        for (int i = 0; i < INJ_NT / 32; ++i) {
+            if (i < warp) before += s_wsum[i];
+            chunk += s_wsum[i];
+        }
+        if (m < nslots) s_pre[m] = before;
+        run += chunk;
+        __syncthreads(); // (s_wsum is written again by the next chunk)
+    }
+    if (tid == 0) s_pre[nslots] = run;
+    // the planners' work estimates, taken before they run (block 0)
+    if (blockIdx.x == 0)
+        for (int m = tid; m < nslots; m += INJ_NT) {
+            DevScalars *sc = ds[m].sc;
+            if (sc) sc->plan_work = sc->pend_cand;
+        }
+    __syncthreads();
+    const int total = run;
+    for (int g = (int)blockIdx.x * INJ_NT + tid; g < total; g += (int)gridDim.x * INJ_NT) {
+        // the member of division g: the last m with s_pre[m] <= g
+        int lo = 0, hi = nslots - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[mid] <= g) lo = mid; else hi = mid - 1;
+        }
+        const SimDev &d = ds[lo];
+        const uint32_t t = (uint32_t)d.sc->step;
+        inject_division<S, LT>(d, (S *)d.f[t & 1u], d.sc->y_r, (size_t)(t & 1u) * (size_t)d.ns_max, g - s_pre[lo]);
+    }
 }
 
 template <typename S, typename LT = Lat9>
@@ -730,12 +884,15 @@ cudaError_t launch_plan(const SimDev &d, int init, cudaStream_t s)
     return cudaLaunchKernelEx(&cfg, k_plan<S, LT>, d, init);
 }
 
+// Resident blocks per SM of the planners: of k_plan (a simulation's own
+// planner grid), or of k_plan_batch (`batch`: a batch's cooperative launch).
 template <typename S, typename LT = Lat9>
-int plan_blocks_per_sm()
+int plan_blocks_per_sm(int batch)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plan<S, LT>, PLAN_NT, 0) != cudaSuccess) return 0;
-    return n;
+    const cudaError_t e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plan_batch<S, LT>, PLAN_NT, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_plan<S, LT>, PLAN_NT, 0);
+    return e == cudaSuccess ? n : 0;
 }
 
 } // namespace lbm

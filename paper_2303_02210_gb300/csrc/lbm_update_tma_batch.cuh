@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(TmaGeom<S, 2>::NT, CTAS)
     for (int j = 0; j < K; ++j) {
         const int m = tid * K + j;
         cnt[j] = 0;
-        if (m < nsims) {
-            const DevScalars *sc = mc[m].sc;
+        const DevScalars *sc = m < nsims ? mc[m].sc : nullptr;
+        if (m < nsims && !sc) s_step[m] = s_yr[m] = s_yhi[m] = s_ncx[m] = 0; // an empty slot: no tiles
+        if (sc) {
             const int y_r = sc->y_r, y_hi = sc->y_hi;
             s_step[m] = (int)sc->step;
             s_yr[m] = y_r;

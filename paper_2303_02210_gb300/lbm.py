@@ -110,6 +110,12 @@ _SIGNATURES = {
     "lbm_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbm_batch_destroy": (ctypes.c_int, [_P]),
     "lbm_batch_fused": (ctypes.c_int, [_P]),
+    "lbm_batch_create_empty": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
+                                              ctypes.POINTER(_P)]),
+    "lbm_batch_attach": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_batch_detach": (ctypes.c_int, [_P, _P]),
+    "lbm_batch_members": (ctypes.c_int, [_P]),
+    "lbm_batch_captures": (ctypes.c_int, [_P]),
 }
 
 _lib = None
@@ -379,7 +385,11 @@ class Simulation:
 class Batch:
     """Independent simulations stepped together (``lbm_batch_create`` ...
     ``lbm_batch_destroy``): one CUDA-graph replay advances every member, the
-    members' kernels running side by side. Keeps the members alive."""
+    members' kernels running side by side. Keeps the members alive.
+
+    ``Batch.empty(slots, precision, lattice)`` makes a batch with free slots
+    (``lbm_batch_create_empty``); ``attach``/``detach`` let members join and
+    leave it without capturing its graphs again."""
 
     def __init__(self, sims, stream=None):
         import torch
@@ -396,6 +406,45 @@ class Batch:
             _check(lib.lbm_batch_create(ctypes.cast(arr, _P), len(self.sims), _P(self.stream.cuda_stream),
                                         ctypes.byref(h)), "lbm_batch_create")
         self._h = h
+
+    @classmethod
+    def empty(cls, slots: int, precision: str = "fp32", lattice: str = "d2q9", device: int = 0, stream=None):
+        """A batch with `slots` free slots for simulations of one lattice and
+        storage type on `device`."""
+        import torch
+        self = cls.__new__(cls)
+        self._lib = lib = load_library()
+        self.sims = []
+        with torch.cuda.device(device):
+            self.stream = torch.cuda.current_stream(device) if stream is None else stream
+            h = _P()
+            _check(lib.lbm_batch_create_empty(int(slots), LATTICES[lattice], PRECISIONS[precision],
+                                              _P(self.stream.cuda_stream), ctypes.byref(h)),
+                   "lbm_batch_create_empty")
+        self._h = h
+        return self
+
+    def attach(self, sim) -> int:
+        """Puts `sim` into a free slot and returns the slot's index; raises
+        LbmError if none is free (LBM_ERR_BATCH_FULL) or `sim` does not fit
+        the batch."""
+        slot = ctypes.c_int32(-1)
+        _check(self._lib.lbm_batch_attach(self._h, sim._h, ctypes.byref(slot)), "lbm_batch_attach")
+        self.sims.append(sim)
+        return slot.value
+
+    def detach(self, sim):
+        _check(self._lib.lbm_batch_detach(self._h, sim._h), "lbm_batch_detach")
+        self.sims = [s for s in self.sims if s is not sim]
+
+    @property
+    def members(self) -> int:
+        return self._lib.lbm_batch_members(self._h)
+
+    @property
+    def captures(self) -> int:
+        """How many times the batch's graphs were captured (1 after creation)."""
+        return self._lib.lbm_batch_captures(self._h)
 
     def lbm_batch_step(self, n: int = 1):
         _check(self._lib.lbm_batch_step(self._h, int(n)), "lbm_batch_step")

@@ -2,20 +2,26 @@
 
 Requests (a lattice to grow for a number of steps) arrive over time. The loop
 admits queued requests while their device footprint (``lbm_footprint``) fits
-in an HBM budget, keeps every admitted simulation resident with its own CUDA
-stream, and advances all of them in ticks of ``chunk`` steps, each on its own
-stream, so the kernels of different requests overlap on the GPU. Optionally
-(``batch``), the resident requests with at least ``chunk`` steps to go and a
-planner small enough for one block (``lbm_plan_capacity`` at most
-``batch_max_divisions``) are stepped as batches instead (one per storage
-type: three batched launches per step for all of them, see
-``lbm_batch_create``; a batch is rebuilt when its membership changes). That
-pays for many small requests; on a trace dominated by large lattices the
-rebuilds cost more than the batched launches save. A request that has run its steps is
-read back (front heights, Eq. 6 sums, counters, optionally the populations)
-and released, which frees memory for the queue at the next tick. Every
-simulation draws its own counter-based random streams, so a result does not
-depend on what else was resident, nor on whether it was batched.
+in an HBM budget and keeps every admitted simulation resident. Resident
+requests are stepped through slot batches (``lbm_batch_create_empty``): one
+per lattice and storage type, made once with a fixed number of slots. A
+request joins its batch when it is admitted and leaves it when it has run its
+steps (``lbm_batch_attach`` / ``lbm_batch_detach``). Neither rewrites more
+than table entries in device memory, so the batch's captured graphs serve the
+whole run. A tick advances every batch by ``chunk`` steps, or by fewer when a
+member has fewer left, so that no member runs past its own step count. A step
+of a batch is three launches for all of its members. A request that finds no
+free slot (or none for its kind: a lattice periodic in y would take the
+staged update from its whole batch) is stepped on its own stream, its kernels
+overlapping with the batches'.
+
+Each tick enqueues the steps first and then creates the simulations of
+newly admitted requests while the GPU works. After the tick's
+synchronisation, finished requests leave their batches and are read back
+(front heights, Eq. 6 sums, counters, optionally the populations) and
+released, and the new ones join. Every simulation draws its own
+counter-based random streams, so a result does not depend on what else was
+resident, nor on whether it was batched.
 """
 from __future__ import annotations
 
@@ -46,52 +52,69 @@ class Request:
         return None if self.finished is None else self.finished - self.arrival
 
 
+class _Resident:
+    __slots__ = ("req", "sim", "done", "batch")
+
+    def __init__(self, req, sim):
+        self.req, self.sim, self.done, self.batch = req, sim, 0, None
+
+    @property
+    def left(self) -> int:
+        return self.req.steps - self.done
+
+
 class Server:
     """Continuous-batching loop over resident simulations.
 
     hbm_budget  bytes of device memory the resident simulations may use
                 together (their arenas, as ``lbm_footprint`` reports);
-    chunk       steps enqueued per resident simulation and tick;
+    chunk       steps per tick (fewer when a batch member has fewer left);
     clock       a monotonic clock in seconds;
     simulation, footprint, new_stream, synchronize
                 the simulation class, lbm_footprint, a CUDA stream factory and
                 a device-wide wait (the defaults use this library and torch;
                 tests of the loop's own logic pass stand-ins);
-    batch       a factory of batches (list of simulations -> object with
-                step(n) and close()), e.g. the library's Batch; None: no
-                batching;
-    capacity    divisions per step a request's planner holds (params,
-                precision -> int; lbm_plan_capacity by default);
-    batch_max_divisions  the largest capacity that is batched.
+    batch       a factory of slot batches, (slots, precision, lattice) ->
+                object with attach(sim), detach(sim), step(n), close()
+                (attach raises when the batch is full); the library's
+                ``Batch.empty`` by default; None: every request on its own;
+    slots       slots per batch.
     """
 
     def __init__(self, hbm_budget: int, chunk: int = 100, clock: Callable[[], float] = time.perf_counter,
-                 simulation=None, footprint=None, new_stream=None, synchronize=None, batch=None,
-                 capacity=None, batch_max_divisions: int = 8192):
-        if hbm_budget <= 0 or chunk <= 0:
-            raise ValueError("hbm_budget and chunk must be positive")
+                 simulation=None, footprint=None, new_stream=None, synchronize=None, batch="default",
+                 slots: int = 256):
+        if hbm_budget <= 0 or chunk <= 0 or slots <= 0:
+            raise ValueError("hbm_budget, chunk and slots must be positive")
         self.hbm_budget = int(hbm_budget)
         self.chunk = int(chunk)
+        self.slots = int(slots)
         self.clock = clock
         self.node_updates = 0
         self.ticks = 0
         self.peak_resident = 0
+        self.batched_requests = 0
+        if batch == "default":
+            from .lbm import Batch
+            batch = Batch.empty
+        self.batch = batch
         if simulation is None:
-            # resident requests share the GPU: the update kernel's form for that
-            # (15.1 against 12.5 G node updates/s aggregate on a hundred requests)
+            # requests stepped on their own share the GPU with the batches:
+            # the update kernel's form for that
             def simulation(params, precision="fp32", stream=None):
-                return Simulation(params, precision=precision, stream=stream, update_kernel="shared")
+                kernel = "auto" if batch is not None else "shared"
+                return Simulation(params, precision=precision, stream=stream, update_kernel=kernel)
         self.simulation = simulation
         self.footprint = footprint or lbm_footprint
         self.new_stream = new_stream
         self.synchronize = synchronize
-        self.batch = batch
-        self.batches_built = 0
-        if capacity is None and batch is not None:
-            from .lbm import lbm_plan_capacity
-            capacity = lbm_plan_capacity
-        self.capacity = capacity
-        self.batch_max_divisions = int(batch_max_divisions)
+
+    @staticmethod
+    def batch_key(r: Request):
+        """The slot batch a request can join (None: stepped on its own)."""
+        if r.params.get("y_periodic"):
+            return None
+        return (r.params.get("lattice", "d2q9"), r.precision)
 
     def run(self, requests: List[Request]) -> List[Request]:
         """Serves `requests` (arrival times relative to the start of the run)
@@ -102,65 +125,82 @@ class Server:
             self.synchronize = self.synchronize or torch.cuda.synchronize
         for r in requests:
             r.footprint = self.footprint(r.params, r.precision)
-            r.batchable = self.batch is not None and \
-                self.capacity(r.params, r.precision) <= self.batch_max_divisions
             if r.footprint > self.hbm_budget:
                 raise ValueError(f"a {r.params['width']} x {r.params['height']} request needs {r.footprint} bytes, "
                                  f"more than the budget of {self.hbm_budget}")
         pending = sorted(requests, key=lambda r: r.arrival)
-        active = []  # [request, simulation, stream, steps done]
-        batches = {}  # storage type -> (member ids, batch)
+        active: List[_Resident] = []
+        joining: List[_Resident] = []  # created during the last tick, not yet in a batch
+        batches = {}                   # batch key -> [batch, members]
         used = 0
         t0 = self.clock()
-        while pending or active:
+
+        def admit():
+            nonlocal used
+            # in arrival order while the footprint fits (a request that does
+            # not fit waits, and so does everything behind it)
             now = self.clock() - t0
-            # admission in arrival order while the footprint fits (a request
-            # that does not fit waits, and so does everything behind it)
             while pending and pending[0].arrival <= now and used + pending[0].footprint <= self.hbm_budget:
                 r = pending.pop(0)
-                stream = self.new_stream()
-                sim = self.simulation(r.params, precision=r.precision, stream=stream)
+                sim = self.simulation(r.params, precision=r.precision, stream=self.new_stream())
                 r.admitted = self.clock() - t0
                 used += r.footprint
-                active.append([r, sim, stream, 0])
+                joining.append(_Resident(r, sim))
+
+        def join():
+            for a in joining:
+                key = self.batch_key(a.req) if self.batch is not None else None
+                if key is not None:
+                    if key not in batches:
+                        batches[key] = [self.batch(self.slots, key[1], key[0]), 0]
+                    entry = batches[key]
+                    if entry[1] < self.slots:
+                        entry[0].attach(a.sim)
+                        entry[1] += 1
+                        a.batch = key
+                        self.batched_requests += 1
+                active.append(a)
+            joining.clear()
+
+        while pending or active or joining:
+            join()
             if not active:
-                wait = pending[0].arrival - (self.clock() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 0.005))
+                admit()
+                if not joining and pending:
+                    wait = pending[0].arrival - (self.clock() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.005))
                 continue
             self.peak_resident = max(self.peak_resident, len(active))
-            # one tick: `chunk` steps of the requests with that many to go,
-            # as one batch per storage type; the rest finish on their own
-            # streams (their kernels overlap with the batches')
-            groups = {}
+            # one tick: each batch by the steps its members all have left (at
+            # most `chunk`), the rest on their own streams
+            for key, entry in batches.items():
+                left = [a.left for a in active if a.batch == key]
+                if not left:
+                    continue
+                n = min(self.chunk, min(left))
+                entry[0].step(n)
+                for a in active:
+                    if a.batch == key:
+                        a.done += n
             for a in active:
-                if a[0].batchable and a[0].steps - a[3] >= self.chunk:
-                    groups.setdefault(a[0].precision, []).append(a)
-                else:
-                    n = min(self.chunk, a[0].steps - a[3])
-                    a[1].step(n)
-                    a[3] += n
-            for prec, group in groups.items():
-                key = tuple(id(a[1]) for a in group)
-                if prec not in batches or batches[prec][0] != key:
-                    if prec in batches:
-                        batches.pop(prec)[1].close()
-                    batches[prec] = (key, self.batch([a[1] for a in group]))
-                    self.batches_built += 1
-                batches[prec][1].step(self.chunk)
-                for a in group:
-                    a[3] += self.chunk
+                if a.batch is None:
+                    n = min(self.chunk, a.left)
+                    a.sim.step(n)
+                    a.done += n
+            admit()  # while the GPU works
             self.synchronize()
             self.ticks += 1
-            # a batch goes before any of its members is released
-            done = {id(a[1]) for a in active if a[3] >= a[0].steps}
-            for prec in [p for p, (key, _) in batches.items() if done.intersection(key)]:
-                batches.pop(prec)[1].close()
             still = []
-            for r, sim, stream, done in active:
-                if done < r.steps:
-                    still.append([r, sim, stream, done])
+            for a in active:
+                if a.left > 0:
+                    still.append(a)
                     continue
+                if a.batch is not None:
+                    entry = batches[a.batch]
+                    entry[0].detach(a.sim)
+                    entry[1] -= 1
+                r, sim = a.req, a.sim
                 st = sim.stats()
                 h, hbar, w = sim.front_heights()
                 r.result = {"stats": st, "heights": h, "hbar": hbar, "w": w}
@@ -171,8 +211,9 @@ class Server:
                 sim.close()
                 used -= r.footprint
             active = still
-        for _, b in batches.values():
-            b.close()
+        for entry in batches.values():
+            entry[0].close()
+        self.batches_built = len(batches)
         self.makespan = self.clock() - t0
         return requests
 
@@ -190,5 +231,6 @@ def summary(requests: List[Request], server: Server) -> dict:
         "offered_req_per_s": (len(requests) - 1) / span if span > 0 else None,
         "sustained_req_per_s": len(requests) / server.makespan,
         "peak_resident": server.peak_resident,
+        "batched_requests": server.batched_requests,
         "ticks": server.ticks,
     }

@@ -281,3 +281,84 @@ def test_staged_batch_within_tolerance_of_the_oracle_1000_steps():
     for p, g in zip(ps, members):
         _fp32_close_to_oracle(g, _oracle_after(p, 1000))
     batch.close()
+
+
+@pytest.mark.parametrize("precision,lattice", [("fp32", "d2q9"), ("fp16", "d2q9"), ("fp64", "d2q9"),
+                                               ("fp32", "d2q7")])
+def test_slot_batch_members_join_and_leave(precision, lattice):
+    """A batch made with free slots (lbm_batch_create_empty): members join
+    after stepping alone, leave, join again, share the batch with members
+    that came later; the graphs are captured once (noisy and quiet members
+    mixed, the room of the tables enough), a full batch refuses a member,
+    and every member ends bit for bit where it ends stepped alone for the
+    same number of steps."""
+    from paper_2303_02210_gb300.lbm import Batch, LbmError
+    if lattice == "d2q7":
+        ps = [dict(wl.lattice_small(seed=80 + i, width=64 + 32 * i, growth_rate=3e-3), lattice="d2q7",
+                   sigma=0.02 * (i % 2)) for i in range(4)]
+    else:
+        ps = [dict(p, sim_id=i) for i, (p, _) in enumerate(STAGED[:4])]
+    ms = [(p, precision, "auto") for p in ps]
+    sims = [make(m) for m in ms]
+    steps = [0] * 4
+    batch = Batch.empty(3, precision, lattice)
+    assert batch.members == 0 and batch.captures == 1
+    assert batch.fused and batch.staged == (lattice == "d2q9" and precision != "fp64")
+    batch.step(3)  # nothing to step
+    sims[0].step(2)
+    steps[0] += 2
+    assert batch.attach(sims[0]) == 0
+    assert batch.attach(sims[1]) == 1
+    batch.step(5)
+    steps[0] += 5
+    steps[1] += 5
+    assert batch.attach(sims[2]) == 2
+    with pytest.raises(LbmError):
+        batch.attach(sims[3])  # full
+    batch.step(6)
+    for i in range(3):
+        steps[i] += 6
+    batch.detach(sims[1])
+    sims[1].step(3)
+    steps[1] += 3
+    assert batch.attach(sims[3]) == 1  # the freed slot
+    batch.step(9)
+    for i in (0, 2, 3):
+        steps[i] += 9
+    batch.detach(sims[0])
+    assert batch.attach(sims[1]) == 0
+    batch.step(4)
+    for i in (1, 2, 3):
+        steps[i] += 4
+    assert batch.members == 3 and batch.captures == 1
+    for i, (m, g) in enumerate(zip(ms, sims)):
+        solo = make(m)
+        solo.step(steps[i])
+        same(g, solo)
+        solo.close()
+    batch.close()
+
+
+def test_slot_batch_recaptures_only_for_a_member_it_cannot_step():
+    """A batch with bulk stores (made from two wide members: two slots) gives
+    them up for a narrow member that takes a freed slot (one capture more),
+    and the results stay exact."""
+    from paper_2303_02210_gb300.lbm import Batch
+    wide = [(dict(p, width=2048 + 128 * i, sim_id=i), "fp32", "auto")
+            for i, (p, k) in enumerate(STAGED) if p["width"] % 4 == 0][:2]
+    narrow = (dict(STAGED[0][0], sim_id=9), "fp32", "auto")
+    sims = [make(m) for m in wide]
+    batch = Batch(sims)
+    assert batch.bulk_stores and batch.captures == 1
+    batch.step(4)
+    batch.detach(sims[1])
+    s_n = make(narrow)
+    assert batch.attach(s_n) == 1
+    assert not batch.bulk_stores and batch.staged and batch.captures == 2
+    batch.step(7)
+    for m, g, k in zip(wide + [narrow], [sims[0], sims[1], s_n], [11, 4, 7]):
+        solo = make(m)
+        solo.step(k)
+        same(g, solo)
+        solo.close()
+    batch.close()

@@ -1,7 +1,8 @@
 """The serving loop (continuous batching): admission by footprint in arrival
-order, ticks over the resident simulations, release on completion — the
-loop's logic with stand-ins on the CPU, and on the GPU that every served
-result equals the same request run alone."""
+order, slot batches that requests join and leave, ticks over the resident
+simulations, release on completion — the loop's logic with stand-ins on the
+CPU, and on the GPU that every served result equals the same request run
+alone and the oracle's run of it."""
 import numpy as np
 import pytest
 
@@ -45,7 +46,7 @@ def test_loop_admits_by_footprint_in_arrival_order_and_finishes_all():
     FakeSim.live = FakeSim.peak = 0
     reqs = [serving.Request(params={"width": w, "height": w // 2}, steps=s, arrival=a)
             for a, w, s in [(0.0, 64, 250), (0.0, 64, 100), (0.002, 128, 300), (0.003, 64, 50), (0.05, 32, 120)]]
-    srv = serving.Server(hbm_budget=200, chunk=100, clock=FakeClock(), simulation=FakeSim,
+    srv = serving.Server(hbm_budget=200, chunk=100, clock=FakeClock(), simulation=FakeSim, batch=None,
                          footprint=lambda p, prec: p["width"], new_stream=lambda: None, synchronize=lambda: None)
     srv.run(reqs)
     assert FakeSim.live == 0 and FakeSim.peak <= 3  # never more than the budget holds (64+64+64 or 64+128)
@@ -59,61 +60,86 @@ def test_loop_admits_by_footprint_in_arrival_order_and_finishes_all():
     assert s["p50_s"] <= s["p99_s"] and s["requests"] == 5
 
 
-class FakeBatch:
-    """Stands in for Batch: steps its members; members must outlive it."""
-    open_members = set()
-    built = 0
+class FakeSlotBatch:
+    """Stands in for Batch.empty: fixed slots, members join and leave; every
+    member must be in the batch while it is stepped through it, and leave
+    before it is released."""
+    made = []
 
-    def __init__(self, sims):
-        self.sims = list(sims)
-        assert not FakeBatch.open_members.intersection(id(m) for m in self.sims)
-        FakeBatch.open_members.update(id(m) for m in self.sims)
-        FakeBatch.built += 1
+    def __init__(self, slots, precision, lattice):
+        self.slots, self.precision, self.lattice = slots, precision, lattice
+        self.members = []
+        self.closed = False
+        FakeSlotBatch.made.append(self)
+
+    def attach(self, sim):
+        assert not self.closed and sim not in self.members
+        assert sim.precision == self.precision
+        if len(self.members) >= self.slots:
+            raise RuntimeError("full")
+        self.members.append(sim)
+        sim.in_batch = self
+
+    def detach(self, sim):
+        self.members.remove(sim)
+        sim.in_batch = None
 
     def step(self, n):
-        for m in self.sims:
+        assert n >= 1
+        for m in self.members:
             m.step(n)
+            assert m.n <= m.steps_wanted, "a member ran past its step count"
 
     def close(self):
-        FakeBatch.open_members.difference_update(id(m) for m in self.sims)
+        assert not self.members
+        self.closed = True
 
 
-class FakeSimInBatch(FakeSim):
+class FakeSimForBatch(FakeSim):
+    wanted = {}
+
+    def __init__(self, params, precision="fp32", stream=None):
+        super().__init__(params, precision, stream)
+        self.precision = precision
+        self.in_batch = None
+        self.steps_wanted = FakeSimForBatch.wanted[id(params)]
+
     def close(self):
-        assert id(self) not in FakeBatch.open_members, "released while its batch was open"
+        assert self.in_batch is None, "released while in its batch"
         super().close()
 
 
-def test_loop_batches_requests_with_a_chunk_to_go():
-    """Requests with at least a chunk of steps left are stepped through one
-    batch per storage type (rebuilt when the membership changes, closed
-    before a member is released); the rest finish alone; every request still
-    runs exactly its steps."""
+def test_loop_steps_requests_through_slot_batches():
+    """Requests join the slot batch of their storage type at admission and
+    leave it when done; a batch is made once per storage type and never
+    rebuilt; a tick steps a batch by what its members all have left (at most
+    a chunk), so every request runs exactly its steps; requests that find
+    their batch full and requests periodic in y run on their own."""
     FakeSim.live = FakeSim.peak = 0
-    FakeBatch.open_members, FakeBatch.built = set(), 0
-    specs = [(0.0, 64, 250, "fp32"), (0.0, 64, 100, "fp16"), (0.0, 32, 430, "fp32"), (0.001, 32, 90, "fp32"),
-             (0.002, 64, 300, "fp16"), (0.003, 32, 200, "fp32")]
-    reqs = [serving.Request(params={"width": w, "height": w // 2}, steps=k, arrival=a, precision=pr)
-            for a, w, k, pr in specs]
-    srv = serving.Server(hbm_budget=10_000, chunk=100, clock=FakeClock(), simulation=FakeSimInBatch,
+    FakeSlotBatch.made = []
+    specs = [(0.0, 64, 250, "fp32", 0), (0.0, 64, 100, "fp16", 0), (0.0, 32, 430, "fp32", 0),
+             (0.001, 32, 90, "fp32", 0), (0.002, 64, 300, "fp16", 0), (0.003, 32, 200, "fp32", 0),
+             (0.003, 32, 170, "fp32", 1), (0.004, 16, 333, "fp32", 0)]
+    reqs = []
+    FakeSimForBatch.wanted = {}
+    for a, w, k, pr, yp in specs:
+        p = {"width": w, "height": w // 2, "y_periodic": yp}
+        FakeSimForBatch.wanted[id(p)] = k
+        reqs.append(serving.Request(params=p, steps=k, arrival=a, precision=pr))
+    srv = serving.Server(hbm_budget=10_000, chunk=100, clock=FakeClock(), simulation=FakeSimForBatch,
                          footprint=lambda p, prec: p["width"], new_stream=lambda: None, synchronize=lambda: None,
-                         batch=FakeBatch, capacity=lambda p, prec: 100 * p["width"], batch_max_divisions=5000)
+                         batch=FakeSlotBatch, slots=3)
     srv.run(reqs)
-    assert FakeSim.live == 0 and not FakeBatch.open_members
-    assert FakeBatch.built >= 1 and srv.batches_built == FakeBatch.built
-    # planner capacity 100 W against 5000: the 32-wide requests are batched
-    assert [r.batchable for r in reqs] == [False, False, True, True, False, True]
+    assert FakeSim.live == 0
+    assert sorted((b.lattice, b.precision) for b in FakeSlotBatch.made) == [("d2q9", "fp16"), ("d2q9", "fp32")]
+    assert all(b.closed and not b.members for b in FakeSlotBatch.made)
     for r in reqs:
         assert r.result["stats"]["step"] == r.steps
     assert srv.node_updates == sum(r.steps * r.params["width"] for r in reqs)
-
-
-def test_request_larger_than_the_budget_is_refused():
-    r = serving.Request(params={"width": 512, "height": 256}, steps=10)
-    srv = serving.Server(hbm_budget=100, simulation=FakeSim, footprint=lambda p, prec: p["width"],
-                         new_stream=lambda: None, synchronize=lambda: None)
-    with pytest.raises(ValueError):
-        srv.run([r])
+    # the y-periodic request never joins; with three slots per batch, at
+    # least one of the five plain fp32 requests had to wait its turn alone
+    assert 0 < srv.batched_requests < len(reqs)
+    assert serving.Server.batch_key(reqs[6]) is None
 
 
 @pytest.mark.gpu
@@ -128,7 +154,7 @@ def test_served_results_equal_requests_run_alone():
     reqs = [serving.Request(params=p, steps=n, arrival=t, precision=pr, keep_populations=True)
             for t, p, n, pr in trace]
     budget = 3 * max(lbm_footprint(r.params, "fp32") for r in reqs)
-    srv = serving.Server(hbm_budget=budget, chunk=64)
+    srv = serving.Server(hbm_budget=budget, chunk=64, batch=None)
     srv.run(reqs)
     for r in reqs:
         alone = Simulation(r.params, precision=r.precision)
@@ -142,19 +168,44 @@ def test_served_results_equal_requests_run_alone():
 
 
 @pytest.mark.gpu
-def test_served_results_equal_requests_run_alone_with_batching():
-    """The same with the small requests stepped through batches (rebuilt as
-    requests come and go): bit for bit what each request gives alone."""
+@pytest.mark.parametrize("slots", [1, 256])
+def test_served_results_equal_requests_run_alone_with_batching(slots):
+    """The same through slot batches (members joining and leaving as
+    requests come and go; with one slot per batch most requests run alone
+    beside them): bit for bit what each request gives alone, and the
+    batches' graphs captured once."""
     from paper_2303_02210_gb300.lbm import Batch, Simulation, lbm_footprint
     trace = wl.serving_trace(10, rate=500.0, steps=(100, 400), seed=8)
     trace = [(t, dict(p, width=min(p["width"], 512), height=min(p["width"], 512) // 2,
                       front_row=float(min(p["width"], 512) // 8)), n, pr) for t, p, n, pr in trace]
     reqs = [serving.Request(params=p, steps=n, arrival=t, precision=pr, keep_populations=True)
             for t, p, n, pr in trace]
-    budget = 4 * max(lbm_footprint(r.params, "fp32") for r in reqs)
-    srv = serving.Server(hbm_budget=budget, chunk=32, batch=Batch)
-    srv.run(reqs)
-    assert srv.batches_built > 0 and any(r.batchable for r in reqs)
+    made = []
+
+    def batch(n, precision, lattice):
+        b = Batch.empty(n, precision, lattice)
+        made.append(b)
+        return b
+
+    captures = {}
+    orig_close = Batch.close
+
+    def close(self):
+        if getattr(self, "_h", None):
+            captures[id(self)] = self.captures
+        orig_close(self)
+
+    Batch.close = close
+    try:
+        budget = 4 * max(lbm_footprint(r.params, "fp32") for r in reqs)
+        srv = serving.Server(hbm_budget=budget, chunk=32, batch=batch, slots=slots)
+        srv.run(reqs)
+    finally:
+        Batch.close = orig_close
+    assert made and srv.batched_requests > 0
+    if slots == 1:
+        assert srv.batched_requests < len(reqs)
+    assert all(captures[id(b)] == 1 for b in made), captures
     for r in reqs:
         alone = Simulation(r.params, precision=r.precision)
         alone.step(r.steps)
@@ -180,7 +231,7 @@ def test_served_results_against_the_oracle(batching):
         reqs.append(serving.Request(params=p, steps=n, arrival=t, precision="fp64" if i % 2 else "fp32",
                                     keep_populations=True))
     budget = 3 * max(lbm_footprint(r.params, "fp64") for r in reqs)
-    srv = serving.Server(hbm_budget=budget, chunk=32, batch=Batch if batching else None)
+    srv = serving.Server(hbm_budget=budget, chunk=32, batch=Batch.empty if batching else None, slots=4)
     srv.run(reqs)
     for r in reqs:
         o = OracleSim(r.params)
