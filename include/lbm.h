@@ -150,10 +150,8 @@ int lbm_footprint(const lbm_params_t *params, uint64_t *bytes);
 /* Divisions per step the planner of such a simulation can hold: four times
  * the initial density's n_s over the whole lattice plus 1024, at most 2^24
  * (more sets LBM_STATUS_CAPACITY). The planner's grid grows with this value
- * and the lattice width (up to a quarter of the SMs); a batch plans members
- * whose grid is one or two blocks with one block of 512 threads each, the
- * others with their grids scaled so that all fit on the GPU at once (two
- * blocks per SM). Host only. */
+ * and the lattice width (up to a quarter of the SMs); in a batch, members
+ * get planner blocks by the work they did last step instead. Host only. */
 int lbm_plan_capacity(const lbm_params_t *params, int64_t *ns_max);
 
 /* Creates a simulation and initialises it on `stream` (a cudaStream_t, NULL =
@@ -288,11 +286,12 @@ const char *lbm_version(void);
  * another they leave most of the GPU idle. A batch advances its simulations
  * together by replaying a CUDA graph. When all members store their
  * populations in the same type on the same lattice, a step of the whole
- * batch is three or four launches: the injection of every member's
- * divisions, the update over every member's tiles, and the planners (one
- * block per member, and a cooperative launch for members whose own planner
- * grid is larger than two blocks, the grids scaled down so that all fit at
- * once); otherwise the graph holds, for each simulation, a chain of steps
+ * batch is three launches: the injection of every member's divisions, the
+ * update over every member's tiles, and the planners, one cooperative
+ * launch whose blocks are dealt on the device every step by the members'
+ * planner work (the candidates they drew last step, their widths): a heavy
+ * member gets blocks in proportion, light ones share blocks, planned one
+ * after another; otherwise the graph holds, for each simulation, a chain of steps
  * (update + planner) as an independent branch. Each simulation computes
  * exactly what lbm_step would (the same arithmetic and counters, bit for
  * bit).
@@ -335,7 +334,7 @@ int lbm_batch_fused(const lbm_batch *batch);
  * one the current members need; a member periodic in y ends
  * the staged form, one narrower than 2048 or not a multiple of 4 wide ends
  * the bulk stores; lbm_batch_fused reports the form in use).
- * lbm_batch_create_empty: a batch with `slots` empty slots (1..4096; the
+ * lbm_batch_create_empty: a batch with `slots` empty slots (1..1024; the
  *     staged update for up to 256) for simulations of one lattice
  *     (LBM_D2Q9, LBM_D2Q7) and storage type (LBM_FP32 .. LBM_BF16; D2Q7:
  *     FP32 or FP64) on the current device; LBM_ERR_INVALID_ARG otherwise.

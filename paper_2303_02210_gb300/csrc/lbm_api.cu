@@ -953,8 +953,8 @@ struct lbm_batch {
     int captures;            // times the graphs were captured
     // batched launches: the slots' SimDev and the plain-load update's block
     // table (its room: that launch's grid), in one allocation; the planners
-    // deal their blocks on the device (a plain launch and a cooperative one
-    // of plan_cap blocks)
+    // deal their blocks on the device (a cooperative launch of plan_cap
+    // blocks)
     bool fused;
     void *dev_mem;
     SimDev *ds;
@@ -993,10 +993,7 @@ cudaError_t batch_capture(lbm_batch *b, int steps, int noise, cudaGraphExec_t *o
                 first = b->tma ? kt->batch_update_tma(b->ds, b->mc, b->maps, (int)b->sims.size(), noise,
                                                       b->tstore, b->tma_grid, b->origin)
                                : kt->batch_update(b->ds, b->bm_upd, b->nb_upd, b->origin);
-            if (first == cudaSuccess)
-                first = kt->batch_plan(b->ds, (int)b->sims.size(), b->plan_cap, 0, b->origin);
-            if (first == cudaSuccess)
-                first = kt->batch_plan(b->ds, (int)b->sims.size(), b->plan_cap, 1, b->origin);
+            if (first == cudaSuccess) first = kt->batch_plan(b->ds, (int)b->sims.size(), b->plan_cap, b->origin);
         }
     } else {
         first = cudaEventRecord(b->fork, b->origin);
@@ -1242,7 +1239,7 @@ cudaError_t batch_init(lbm_batch *b)
     if (e != cudaSuccess) return e;
     if (!b->fused) return batch_recapture(b);
     // the cooperative planner launch: every resident block
-    b->plan_cap = std::max(1, b->kt->plan_blocks_per_sm(1)) * b->nsm;
+    b->plan_cap = std::max(2, b->kt->plan_blocks_per_sm(1) * b->nsm);
     if (b->members == 0) {
         // an empty batch: room for members to come (the plain-load update's
         // two waves and 32 column tiles more per slot)

@@ -258,7 +258,7 @@ struct KernelTable {
     // block per simulation, or its own grid, then cooperatively).
     cudaError_t (*batch_inject)(const SimDev *ds, int nslots, int grid, cudaStream_t);
     cudaError_t (*batch_update)(const SimDev *ds, const int4 *bm, int nb, cudaStream_t);
-    cudaError_t (*batch_plan)(const SimDev *ds, int nslots, int cap, int coop, cudaStream_t);
+    cudaError_t (*batch_plan)(const SimDev *ds, int nslots, int cap, cudaStream_t);
     // the TMA-staged update of a whole batch (lbm_update_tma_batch.cuh; null
     // where there is none): mc[m] member m's constants, maps[4 m + b] loads its
     // copy b in boxes of (kTmaBoxX + 8) x 4 x 9, maps[4 m + 2 + b] stores into
@@ -288,7 +288,7 @@ constexpr int kPlanMaxBlocks = 1024;
 // The TMA-staged batched update: members one launch takes (its shared-memory
 // tables) and CTAs per SM.
 constexpr int kTmaBatchMaxSims = 256;
-constexpr int kMaxBatchSlots = 4096; // slots of a batch (the staged batched update: kTmaBatchMaxSims)
+constexpr int kMaxBatchSlots = 1024; // slots of a batch (the staged batched update: kTmaBatchMaxSims)
 constexpr int kTmaBatchCtasPerSm = 5;
 constexpr int kTmaBatchCtasPerSmStore = 4; // its bulk-store form
 

@@ -58,9 +58,9 @@ struct Launch {
         k_update_batch<S, UPD_TPB, UPD_NR><<<nb, UPD_TPB, 0, s>>>(ds, bm);
         return cudaGetLastError();
     }
-    static cudaError_t batch_plan(const SimDev *ds, int nslots, int cap, int coop, cudaStream_t s)
+    static cudaError_t batch_plan(const SimDev *ds, int nslots, int cap, cudaStream_t s)
     {
-        return launch_plan_batch<S>(ds, nslots, cap, coop, s);
+        return launch_plan_batch<S>(ds, nslots, cap, s);
     }
     static int update_blocks_per_sm()
     {
@@ -140,9 +140,9 @@ struct Launch7 {
         k_update7_batch<S, UPD_TPB, UPD_NR><<<nb, UPD_TPB, 0, s>>>(ds, bm);
         return cudaGetLastError();
     }
-    static cudaError_t batch_plan(const SimDev *ds, int nslots, int cap, int coop, cudaStream_t s)
+    static cudaError_t batch_plan(const SimDev *ds, int nslots, int cap, cudaStream_t s)
     {
-        return launch_plan_batch<S, Lat7>(ds, nslots, cap, coop, s);
+        return launch_plan_batch<S, Lat7>(ds, nslots, cap, s);
     }
     static int update_blocks_per_sm()
     {

@@ -652,22 +652,20 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
     plan_body<S, LT>(d, init, (int)gridDim.x, (int)blockIdx.x);
 }
 
-// The planners of a batch's slots, in two launches: a plain one in which
-// each member planned by one block gets a block, and a cooperative one (all
-// blocks resident at once) in which each member planned by more gets its
-// grid. The blocks are dealt on the device, every step, from the members'
+// The planners of a batch's slots in one cooperative launch of `cap` blocks
+// (all resident at once), dealt on the device, every step, by the members'
 // planner work: w = the candidates drawn for the latest selection (plan_work,
 // copied by the injection launch before this one, so that it holds still
 // while the planners run) + the lattice width (the front scans) + a fixed
-// floor (the barriers and the commit). With m members and m <= cap (the
-// cooperative launch's blocks), all are planned there, member i by
-// G = 1 + floor(w (cap - m) / sum of w) blocks; with more members, by
-// G = floor(w cap / sum of w) blocks, and those with G < 2 by one block each
-// in the plain launch (G at most kPlanMaxBlocks). Every block computes
-// the same deal from the same integers and finds its member and its block
-// index by a prefix over the slots, in slot order; a member planned by more
-// blocks uses the grid barrier on its own arrival counter (reset at the end
-// of each launch, so the grid may change from step to step).
+// floor (the barriers and the commit). With tau = ceil(sum of w / (cap - 1)),
+// a member with w >= tau is planned by G = floor(w / tau) blocks (at most
+// kPlanMaxBlocks; the grid barrier on its own arrival counter, reset at the
+// end of each launch, so the grid may change from step to step); the others
+// go, in slot order, into bins of about tau work, bin k holding the members
+// whose prefix of light work lies in [k tau, (k + 1) tau), and a bin's block
+// plans them one after another. The heavy members' blocks and the bins
+// number at most sum w / tau + 1 <= cap. Every block computes the same deal
+// from the same integers (prefixes over the slots, in slot order).
 constexpr long long kPlanWorkFloor = 4096;
 
 __device__ __forceinline__ long long plan_slot_work(const SimDev *__restrict__ ds, int i)
@@ -678,87 +676,113 @@ __device__ __forceinline__ long long plan_slot_work(const SimDev *__restrict__ d
     return (c > 0 ? c : 0) + ds[i].W + kPlanWorkFloor;
 }
 
-__device__ __forceinline__ int plan_slot_grid(long long w, long long wsum, int m, int cap)
-{
-    if (w < 0) return 0;
-    const long long g = m <= cap ? 1 + w * (long long)(cap - m) / wsum : w * (long long)cap / wsum;
-    return (int)(g < kPlanMaxBlocks ? g : kPlanMaxBlocks);
-}
-
-// Whether a slot's member is planned in the cooperative launch.
-__device__ __forceinline__ bool plan_slot_coop(int g, int m, int cap) { return m <= cap ? g >= 1 : g >= 2; }
-
 template <typename S, typename LT = Lat9>
-__global__ void __launch_bounds__(PLAN_NT, 2) k_plan_batch(const SimDev *__restrict__ ds, int nslots, int cap, int coop)
+__global__ void __launch_bounds__(PLAN_NT, 2) k_plan_batch(const SimDev *__restrict__ ds, int nslots)
 {
-    __shared__ int s_pre[kMaxBatchSlots + 1];
+    __shared__ int s_hpre[kMaxBatchSlots + 1];       // heavy members' blocks, exclusive prefix
+    __shared__ long long s_lpre[kMaxBatchSlots + 1]; // light members' work, exclusive prefix
     __shared__ long long s_red[PLAN_WARPS];
-    __shared__ int s_wi[PLAN_WARPS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    long long wsum = 0, mm = 0;
+    const int cap = (int)gridDim.x;
+    long long wsum = 0;
     for (int i = tid; i < nslots; i += PLAN_NT) {
         const long long w = plan_slot_work(ds, i);
         wsum += w > 0 ? w : 0;
-        mm += w >= 0 ? 1 : 0;
     }
     wsum = plan_block_sum(wsum, s_red);
-    const int m = (int)plan_block_sum(mm, s_red);
-    if (!coop && m <= cap) return; // (uniform: all members are in the cooperative launch)
-    // entries per slot: its grid in the cooperative launch, one block in the
-    // plain launch; their exclusive prefix over the slots
-    int run = 0;
+    if (wsum == 0) return; // (uniform: no members)
+    const long long tau = (wsum + cap - 2) / (cap - 1);
+    long long hrun = 0, lrun = 0;
     for (int base = 0; base < nslots; base += PLAN_NT) {
         const int i = base + tid;
-        int n = 0;
+        long long hg = 0, lw = 0;
         if (i < nslots) {
             const long long w = plan_slot_work(ds, i);
-            const int g = plan_slot_grid(w, wsum, m, cap);
-            const bool c = plan_slot_coop(g, m, cap);
-            n = w < 0 ? 0 : (coop ? (c ? g : 0) : (c ? 0 : 1));
+            if (w >= tau) hg = w / tau < kPlanMaxBlocks ? w / tau : kPlanMaxBlocks;
+            else if (w >= 0) lw = w;
         }
-        int incl = n;
+        // two exclusive block scans (64-bit: the work sums)
+        long long ih = hg, il = lw;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
+            const long long uh = __shfl_up_sync(0xffffffffu, ih, o);
+            const long long ul = __shfl_up_sync(0xffffffffu, il, o);
+            if (lane >= o) {
+                ih += uh;
+                il += ul;
+            }
         }
-        if (lane == 31) s_wi[warp] = incl;
+        __shared__ long long s_wh[PLAN_WARPS], s_wl[PLAN_WARPS];
+        if (lane == 31) {
+            s_wh[warp] = ih;
+            s_wl[warp] = il;
+        }
         __syncthreads();
-        int before = run + incl - n, chunk = 0;
+        long long bh = hrun + ih - hg, bl = lrun + il - lw, ch = 0, cl = 0;
         for (int k = 0; k < PLAN_WARPS; ++k) {
-            if (k < warp) before += s_wi[k];
-            chunk += s_wi[k];
+            if (k < warp) {
+                bh += s_wh[k];
+                bl += s_wl[k];
+            }
+            ch += s_wh[k];
+            cl += s_wl[k];
         }
-        if (i < nslots) s_pre[i] = before;
-        run += chunk;
+        if (i < nslots) {
+            s_hpre[i] = (int)bh;
+            s_lpre[i] = bl;
+        }
+        hrun += ch;
+        lrun += cl;
         __syncthreads();
     }
-    const int b = (int)blockIdx.x;
-    if (b >= run) return; // (uniform: an unused block)
-    int lo = 0, hi = nslots - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_pre[mid] <= b) lo = mid; else hi = mid - 1;
+    if (tid == 0) {
+        s_hpre[nslots] = (int)hrun;
+        s_lpre[nslots] = lrun;
     }
-    const int G = coop ? plan_slot_grid(plan_slot_work(ds, lo), wsum, m, cap) : 1;
-    plan_body<S, LT>(ds[lo], 0, G, b - s_pre[lo]);
+    __syncthreads();
+    const int b = (int)blockIdx.x;
+    if (b < (int)hrun) {
+        // a heavy member's block: the last slot with s_hpre <= b
+        int lo = 0, hi = nslots - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_hpre[mid] <= b) lo = mid; else hi = mid - 1;
+        }
+        const long long w = plan_slot_work(ds, lo);
+        const int G = (int)(w / tau < kPlanMaxBlocks ? w / tau : kPlanMaxBlocks);
+        plan_body<S, LT>(ds[lo], 0, G, b - s_hpre[lo]);
+        return;
+    }
+    // bin k: the light members whose work prefix lies in [k tau, (k + 1) tau)
+    const long long k = b - hrun, lo_w = k * tau, hi_w = lo_w + tau;
+    if (lo_w >= lrun) return; // (uniform: no such bin)
+    int lo = 0, hi = nslots; // the first slot with s_lpre >= lo_w
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_lpre[mid] < lo_w) lo = mid + 1; else hi = mid;
+    }
+    for (int i = lo; i < nslots && s_lpre[i] < hi_w; ++i) {
+        const long long w = plan_slot_work(ds, i);
+        if (w < 0 || w >= tau) continue; // empty, or heavy
+        plan_body<S, LT>(ds[i], 0, 1, 0);
+    }
 }
 
-// The plain launch (`coop` 0: a block per slot) or the cooperative one
-// (`coop` 1: `cap` blocks, at most the resident count).
+// The batched planners' cooperative launch: `cap` blocks, at most the
+// resident count.
 template <typename S, typename LT = Lat9>
-cudaError_t launch_plan_batch(const SimDev *ds, int nslots, int cap, int coop, cudaStream_t s)
+cudaError_t launch_plan_batch(const SimDev *ds, int nslots, int cap, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(coop ? cap : nslots));
+    cfg.gridDim = dim3((unsigned)cap);
     cfg.blockDim = dim3(PLAN_NT);
     cfg.stream = s;
     cudaLaunchAttribute la[1];
     la[0].id = cudaLaunchAttributeCooperative;
     la[0].val.cooperative = 1;
     cfg.attrs = la;
-    cfg.numAttrs = coop ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_plan_batch<S, LT>, ds, nslots, cap, coop);
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_plan_batch<S, LT>, ds, nslots);
 }
 
 // App. A step 3 for the update kernels that read the populations from global
