@@ -13,7 +13,7 @@ paper grows in x, with y along the front). A mode of wavenumber k has
 q = 2 pi k / W.
 
 Run ``python -m paper_2303_02210_gb300.experiments dispersion`` (or
-``bias``, or ``roughness``) for a JSON summary.
+``bias``, ``roughness``, ``kpz``) for a JSON summary.
 """
 from __future__ import annotations
 
@@ -244,19 +244,187 @@ def measure_roughness(width: int = 1024, seeds: int = 16, steps: int = 20000, ev
             "beta": {f"{lo}-{hi}": growth_exponent(times, w, lo, hi) for lo, hi in windows}}
 
 
+def kpz_exponents(times: Sequence[float], ws_by_width: Dict[int, np.ndarray], beta_window: Sequence[float],
+                  sat_from: float, resamples: int = 200, seed: int = 0,
+                  t_end: Optional[Dict[int, float]] = None) -> dict:
+    """The KPZ exponents of an ensemble with error bars over its seeds.
+
+    ws_by_width[L][time, seed] are the Eq. 6 widths of the realisations of
+    width L. beta (w ~ t^beta, Eq. 6 and Sec. III) is fitted to each L's
+    ensemble width (ensemble_width) over beta_window = (lo, hi); hi = None
+    ends each L's window at its crossover t_x, the first sample at which its
+    ensemble width reaches 0.8 of its saturated width (fixed from the whole
+    ensemble, before any resampling; no fit if t_x <= 2 lo); alpha
+    (w_sat ~ L^alpha) to the saturated widths, each L's ensemble width
+    averaged over the samples with t >= sat_from, against L on log-log axes.
+    Error bars: the standard deviation over `resamples` bootstrap ensembles
+    (the seeds of each width drawn with replacement). t_end[L], if given,
+    drops L's samples after that time (e.g. once a front nears the top
+    wall)."""
+    t = np.asarray(times, dtype=np.float64)
+    Ls = sorted(ws_by_width)
+    rng = np.random.default_rng(seed)
+    lo, hi = beta_window
+    end = {L: (t_end or {}).get(L, np.inf) for L in Ls}
+    sat = {L: (t >= sat_from) & (t <= end[L]) for L in Ls}
+    his = {}
+    for L in Ls:
+        if hi is not None:
+            his[L] = min(hi, end[L])
+            continue
+        w = ensemble_width(np.asarray(ws_by_width[L], dtype=np.float64))
+        reach = np.nonzero(w >= 0.8 * np.mean(w[sat[L]]))[0] if sat[L].any() else []
+        tx = float(t[reach[0]]) if len(reach) else float(t[-1])
+        his[L] = min(tx, end[L]) if tx > 2 * lo else lo  # (lo: too short, growth_exponent gives None)
+
+    def fits(sample):
+        betas = {L: growth_exponent(t, ensemble_width(sample[L]), lo, his[L]) for L in Ls}
+        wsat = np.array([float(np.mean(ensemble_width(sample[L])[sat[L]])) if sat[L].any() else np.nan
+                         for L in Ls])
+        ok = np.isfinite(wsat) & (wsat > 0)
+        alpha = float(np.polyfit(np.log(np.array(Ls, dtype=np.float64)[ok]), np.log(wsat[ok]), 1)[0]) \
+            if ok.sum() >= 2 else None
+        return betas, wsat, alpha
+
+    betas, wsat, alpha = fits({L: np.asarray(ws_by_width[L], dtype=np.float64) for L in Ls})
+    boot_b = {L: [] for L in Ls}
+    boot_a = []
+    for _ in range(resamples):
+        smp = {}
+        for L in Ls:
+            w = np.asarray(ws_by_width[L], dtype=np.float64)
+            smp[L] = w[:, rng.integers(0, w.shape[1], w.shape[1])]
+        b, _, a = fits(smp)
+        for L in Ls:
+            if b[L] is not None:
+                boot_b[L].append(b[L])
+        if a is not None:
+            boot_a.append(a)
+    return {
+        "beta": {L: betas[L] for L in Ls},
+        "beta_err": {L: float(np.std(boot_b[L])) if boot_b[L] else None for L in Ls},
+        "beta_window": {L: [float(lo), float(his[L])] for L in Ls},
+        "w_sat": {L: float(v) for L, v in zip(Ls, wsat)},
+        "alpha": alpha,
+        "alpha_err": float(np.std(boot_a)) if boot_a else None,
+        "sat_from": float(sat_from),
+    }
+
+
+def kpz_params(width: int, seed: int, height: int, front_row: float = 60.0, **kw) -> dict:
+    """One realisation in the paper's own regime (App. A parameter list): the
+    triangular D2Q7 lattice, rho_init = 0.1 with the U[0.9, 1.1] jitter,
+    sigma = 0.01, tau = 1, mu = 0.001, g = 1e-3, rho_cell = 0.01, bulk
+    growth, the rear wall max(50, 10 w) behind the front, a flat front at
+    `front_row` with seeded noise of amplitude 0.5."""
+    from . import workloads as wl
+    p = wl.paper_params(width=width, height=height, lattice="d2q7", growth_mode="bulk", wall_mode="advance",
+                        wall_min_gap=50.0, wall_w_factor=10.0, front_kind="flat", front_row=front_row,
+                        front_amp=0.5, seed=seed, sim_id=seed)
+    p.update(kw)
+    return p
+
+
+def measure_kpz(widths: Sequence[int] = (64, 128, 256, 512), seeds: int = 32, steps: int = 40000,
+                every: int = 200, height: int = 4096, beta_window: Optional[Sequence[float]] = None,
+                sat_from: Optional[float] = None, precision: str = "fp32", simulation=None, batch=None,
+                **kw) -> dict:
+    """The roughening check of Sec. III in the paper's regime (kpz_params):
+    `seeds` realisations of each width, all stepped together as one batch,
+    Eq. 6's w and the mean height of each sampled every `every` steps (kept
+    per realisation); kpz_exponents over them (beta over beta_window, default
+    from 4 every to a tenth of the run; alpha from the last third of the run
+    by default; each width's samples only up to the last one before any of
+    its fronts came within 256 rows of the top wall), the mean front
+    position, and per width the mass the literal negative-population fix
+    (App. A step 7) added against the mass the divisions added."""
+    if simulation is None or batch is None:
+        from .lbm import Batch, Simulation
+        simulation = simulation or Simulation
+        batch = batch or Batch
+    members = [(L, s) for L in widths for s in range(seeds)]
+    sims = [simulation(kpz_params(L, 1 + 1000 * i + s, height, **kw), precision=precision)
+            for i, L in enumerate(widths) for s in range(seeds)]
+    b = batch(sims)
+    times, ws, hbar = [], [], []
+    try:
+        for k in range(steps // every):
+            b.step(every)
+            fh = [sm.front_heights() for sm in sims]
+            times.append((k + 1) * every)
+            ws.append([f[2] for f in fh])
+            hbar.append([f[1] for f in fh])
+        stats = [sm.stats() for sm in sims]
+    finally:
+        b.close()
+        for sm in sims:
+            sm.close()
+    ws = np.array(ws)
+    hb = np.array(hbar)
+    by = {L: ws[:, [j for j, (l, _) in enumerate(members) if l == L]] for L in widths}
+    rho_cell = kpz_params(widths[0], 1, height, **kw)["rho_cell"]
+    hby = {L: hb[:, [j for j, (l, _) in enumerate(members) if l == L]] for L in widths}
+    t_end = {}
+    for L in widths:
+        near = np.nonzero(hby[L].max(axis=1) > height - 256)[0] if len(times) else []
+        t_end[L] = float(times[near[0] - 1]) if len(near) and near[0] > 0 else (float(times[-1]) if len(near) == 0
+                                                                                  else 0.0)
+    out = {"widths": list(widths), "seeds": seeds, "steps": steps, "every": every, "height": height,
+           "t": times, "w": {L: [float(v) for v in ensemble_width(by[L])] for L in widths},
+           "hbar": {L: [float(v) for v in hby[L].mean(1)] for L in widths},
+           "w_seeds": {L: by[L].tolist() for L in widths}, "hbar_seeds": {L: hby[L].tolist() for L in widths},
+           "t_end": t_end, "status": sorted({int(st["status"]) for st in stats})}
+    neg = {}
+    for L in widths:
+        sel = [st for st, (l, _) in zip(stats, members) if l == L]
+        clip = float(np.mean([st["clip_mass"] for st in sel]))
+        div = float(np.mean([st["div_total"] for st in sel])) * rho_cell
+        neg[L] = {"negfix_mass_per_step": clip / steps, "division_mass_per_step": div / steps,
+                  "negfix_share": clip / (clip + div) if clip + div > 0 else None}
+    out["mass_sources"] = neg
+    if times:
+        lo, hi = beta_window if beta_window is not None else (4 * every, max(5 * every, steps / 10))
+        out["fit"] = kpz_exponents(times, by, (lo, hi), sat_from if sat_from is not None else 2 * steps / 3,
+                                   t_end=t_end)
+    return out
+
+
 def main(argv: Optional[List[str]] = None) -> None:
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("what", choices=["dispersion", "bias", "roughness"])
+    ap.add_argument("what", choices=["dispersion", "bias", "roughness", "kpz"])
     ap.add_argument("--width", type=int, default=None)
     ap.add_argument("--steps", type=int, default=None)
-    ap.add_argument("--seeds", type=int, default=None, help="realisations (roughness)")
+    ap.add_argument("--seeds", type=int, default=None, help="realisations (roughness, kpz)")
+    ap.add_argument("--widths", type=int, nargs="+", default=None, help="lattice widths (kpz)")
+    ap.add_argument("--height", type=int, default=None)
+    ap.add_argument("--every", type=int, default=None, help="steps between samples (roughness, kpz)")
+    ap.add_argument("--negfix", choices=["literal", "rescale"], default=None,
+                    help="reading of the negative-population fix (kpz)")
+    ap.add_argument("--beta-from", type=float, default=None, help="start of the beta window (kpz)")
+    ap.add_argument("--sat-from", type=float, default=None, help="start of the saturated samples (kpz)")
+    ap.add_argument("--save", default=None, help="write the full output (per realisation) as JSON here (kpz)")
     args = ap.parse_args(argv)
     kw = {k: v for k, v in (("width", args.width), ("steps", args.steps)) if v is not None}
     if args.what == "dispersion":
         out = measure_dispersion(**kw)
     elif args.what == "bias":
         out = measure_bias(**kw)
+    elif args.what == "kpz":
+        kw.pop("width", None)
+        for name, v in (("seeds", args.seeds), ("height", args.height), ("every", args.every),
+                        ("sat_from", args.sat_from), ("negfix_mode", args.negfix)):
+            if v is not None:
+                kw[name] = v
+        if args.widths:
+            kw["widths"] = tuple(args.widths)
+        if args.beta_from is not None:
+            kw["beta_window"] = (args.beta_from, None)
+        out = measure_kpz(**kw)
+        if args.save:
+            with open(args.save, "w") as fh:
+                json.dump(out, fh)
+        out = {k: v for k, v in out.items() if k not in ("w_seeds", "hbar_seeds")}
     else:
         if args.seeds is not None:
             kw["seeds"] = args.seeds
