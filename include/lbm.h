@@ -79,10 +79,11 @@ enum { LBM_D2Q9 = 0, LBM_D2Q7 = 1 };
  *               and for f_i = c_i), FP32 arithmetic, 36 bytes per node
  *               update
  *  update_kernel 0: choose (the TMA-staged kernel for FP32 and 16-bit
- *               storage with walls in y, else the plain-load kernel; for
- *               FP32 its bulk-store form (6) from 2048 columns on when W is
- *               a multiple of 4, else its two-row form up to 4096 columns and
- *               the four-row form beyond);
+ *               storage with walls in y, else the plain-load kernel; its
+ *               form from the library's tuned table, a sweep of the forms
+ *               and planner grids measured per storage type and lattice
+ *               width (the entry of the largest tuned width not above W);
+ *               the bulk-store form (6) only when W is a multiple of 4);
  *               1: plain-load kernel; 2: TMA-staged kernel, two-row form;
  *               3: TMA-staged kernel, four-row form (2-4: not FP64, and
  *               y_periodic = 0 only); 4: the two-row form with the
@@ -101,6 +102,12 @@ enum { LBM_D2Q9 = 0, LBM_D2Q7 = 1 };
  *               D2Q7 kernel, two-row tiles, for FP32 with walls in y, else
  *               the plain-load kernel; 3 and 4 are refused), an even H if
  *               y_periodic. Populations have 7 planes instead of 9
+ *  plan_blocks  blocks of the planner's cooperative grid: 0 = the tuned
+ *               table's value for the storage type and width (else one block
+ *               per 16 mask words or 512 divisions of the capacity, at least
+ *               2, at most a quarter of the SMs); 1..1024 = that many, at
+ *               most the resident count (more: LBM_ERR_INVALID_ARG). The
+ *               results do not depend on it.
  */
 typedef struct {
     double tau, mu, rho_c, rho_cell, sigma, rho0, growth_rate;
@@ -112,6 +119,7 @@ typedef struct {
     int32_t precision;
     int32_t update_kernel;
     int32_t lattice;
+    int32_t plan_blocks;
 } lbm_params_t;
 
 /* Counters and observables after the latest completed step. */
@@ -313,8 +321,9 @@ int lbm_batch_create(lbm_sim *const *sims, int32_t n, void *stream, lbm_batch **
 int lbm_batch_step(lbm_batch *batch, int64_t nsteps);
 int lbm_batch_destroy(lbm_batch *batch);
 /* 3 if the batch steps with the batched launches and its update is the
- * TMA-staged one with bulk tensor stores (FP32 members all at least 2048
- * wide and multiples of 4 wide), 2 if the TMA-staged one with per-lane
+ * TMA-staged one with bulk tensor stores (FP32 members all multiples of 4
+ * wide and at least as wide as the tuned table's threshold, 4096 columns
+ * on GB300), 2 if the TMA-staged one with per-lane
  * stores (all members D2Q9 with FP32 or the same 16-bit storage and walls
  * in y, at most 256 slots: one launch deals all members' 128 x 2 tiles; the
  * divisions are added by the batched injection launch before it),
@@ -329,11 +338,12 @@ int lbm_batch_fused(const lbm_batch *batch);
  * does nothing), so a change of members rewrites table entries and leaves
  * the captured graphs as they are. The graphs are captured again (inside the
  * call) only when a table outgrows its room (its room then doubles) or when
- * a joining member cannot take the batch's form of the update (the staged
- * form is captured with and without Eq. 4's noise, and a step replays the
- * one the current members need; a member periodic in y ends
- * the staged form, one narrower than 2048 or not a multiple of 4 wide ends
- * the bulk stores; lbm_batch_fused reports the form in use).
+ * a joining member cannot take the batch's form of the update: a member
+ * periodic in y ends the staged form, one narrower than the tuned
+ * bulk-store width or not a multiple of 4 wide ends the bulk stores
+ * (lbm_batch_fused reports the form in use). The staged form is captured
+ * with and without Eq. 4's noise, and a step replays the one the current
+ * members need.
  * lbm_batch_create_empty: a batch with `slots` empty slots (1..1024; the
  *     staged update for up to 256) for simulations of one lattice
  *     (LBM_D2Q9, LBM_D2Q7) and storage type (LBM_FP32 .. LBM_BF16; D2Q7:

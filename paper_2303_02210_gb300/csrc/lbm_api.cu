@@ -13,6 +13,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_common.cuh"
+#include "lbm_tuned.h"
 
 using namespace lbm;
 
@@ -43,6 +44,21 @@ int cuda_fail(cudaError_t e)
     } while (0)
 
 uint64_t align256(uint64_t v) { return (v + 255u) & ~uint64_t(255u); }
+
+// The tuned entry for a storage type and width: the largest tuned width not
+// above W (the smallest tuned width if all are); nullptr if the table has no
+// entry for the storage type.
+const TunedShape *tuned_shape(int precision, int width)
+{
+    const TunedShape *best = nullptr, *least = nullptr;
+    for (int i = 0; i < kTunedShapeCount; ++i) {
+        const TunedShape &t = kTunedShapes[i];
+        if (t.precision != precision) continue;
+        if (!least || t.width < least->width) least = &t;
+        if (t.width <= width && (!best || t.width > best->width)) best = &t;
+    }
+    return best ? best : least;
+}
 
 // The kernels of a lattice and storage type.
 const KernelTable *kernel_table(int lattice, int precision)
@@ -283,6 +299,7 @@ int lbm_validate(const lbm_params_t *p)
     if (p->precision < LBM_FP32 || p->precision > LBM_BF16) return LBM_ERR_INVALID_ARG;
     if (p->y_periodic != 0 && p->y_periodic != 1) return LBM_ERR_INVALID_ARG;
     if (p->update_kernel < 0 || p->update_kernel > 6) return LBM_ERR_INVALID_ARG;
+    if (p->plan_blocks < 0 || p->plan_blocks > kPlanMaxBlocks) return LBM_ERR_INVALID_ARG;
     if (p->update_kernel >= 2 && p->update_kernel != 5 && (p->precision == LBM_FP64 || p->y_periodic))
         return LBM_ERR_INVALID_ARG;
     // bulk tensor stores: FP32 only (16-bit tiles start off a 16-byte boundary)
@@ -443,7 +460,20 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     // 76.6, 76.3 and 77.4 us at 4096 x 2048 and 147.6, 143.1, 142.8 and
     // 142.4 us at 8192 x 2048)
     const long long want = std::max<long long>((L.MW + 15) / 16, (L.ns_max + 511) / 512);
-    const int pg = (int)std::min<long long>(std::max(2, nsm / 4), std::max<long long>(2, want));
+    int pg = (int)std::min<long long>(std::max(2, nsm / 4), std::max<long long>(2, want));
+    // the tuned table's grid for this storage type and width (D2Q9), or the
+    // caller's; at most the resident count
+    const TunedShape *tuned = p->lattice == LBM_D2Q9 ? tuned_shape(p->precision, p->width) : nullptr;
+    if (p->plan_blocks > 0) {
+        if (p->plan_blocks > pbs * nsm) {
+            if (s->own_arena) cudaFree(s->arena);
+            delete s;
+            return LBM_ERR_INVALID_ARG;
+        }
+        pg = p->plan_blocks;
+    } else if (tuned && tuned->plan_blocks > 0) {
+        pg = std::min(tuned->plan_blocks, pbs * nsm);
+    }
     d.plan_grid = pbs > 0 ? std::min(pg, kPlanMaxBlocks) : 0;
     if (d.plan_grid < 1) {
         if (s->own_arena) cudaFree(s->arena);
@@ -454,12 +484,14 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
     s->tma_grid = nsm;
     // staged update variant (KernelTable::tma_info): "tma" 0 (two-row tiles),
     // "tma1" 1 (four-row tiles), "tma_st" 2 (two-row tiles stored in bulk,
-    // FP32). Automatic: the bulk-store form for FP32 from 2048 columns on
+    // FP32). Automatic: the tuned table's form for the storage type and
+    // width (lbm_tuned.h, written by the autotuner's sweep); without an entry
+    // the hand-set rule: the bulk-store form for FP32 from 2048 columns on
     // (measured per update launch: 57.3 against 62.7 us at 4096 x 2048, 115
     // against 124 (four-row tiles) at 8192 x 2048, 32.7 against 33.9 at
     // 2048), two-row tiles below (19.1 against 21.1 us at 1024, where the
     // window stays in the L2) and for 16-bit storage up to 4096 columns,
-    // four-row tiles beyond; the four-row form for a simulation that shares
+    // four-row tiles beyond. The four-row form for a simulation that shares
     // the GPU (5: 15.1 against 12.5 G node updates/s aggregate for a hundred
     // concurrent requests). D2Q7: one form.
     // The bulk-store form cuts its stores at x = W - 1, and a bulk store
@@ -473,8 +505,10 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
             variant = 1;
         else if (p->update_kernel == 6)
             variant = bulk_ok ? 2 : 0;
-        else if (p->update_kernel == 0)
-            variant = bulk_ok && p->width >= 2048 ? 2 : (p->width > 4096 ? 1 : 0);
+        else if (p->update_kernel == 0) {
+            variant = tuned ? tuned->variant : (bulk_ok && p->width >= 2048 ? 2 : (p->width > 4096 ? 1 : 0));
+            if (variant == 2 && !bulk_ok) variant = 0;
+        }
     }
     s->tma_variant = variant;
     const bool tma_inject = p->update_kernel != 4; // 4: the selector injects into global memory
@@ -1047,10 +1081,12 @@ void batch_noise(lbm_batch *b)
 bool staged_ok(const lbm_sim *s) { return s->p.lattice == LBM_D2Q9 && !s->p.y_periodic; }
 bool bulk_store_ok(const lbm_sim *s)
 {
-    // measured: four 4096 x 2048 members 66.3 against 63.8 G node updates/s
-    // with bulk stores, but the 256-member ensemble of widths 256..2048 53.0
-    // against 56.7 (four CTAs per SM instead of five)
-    return s->p.precision == LBM_FP32 && s->p.width % 4 == 0 && s->p.width >= 2048;
+    // from the tuned table's width on (the narrowest width from which the
+    // single-lattice sweep's fastest FP32 form stores in bulk); measured:
+    // four 4096 x 2048 members 66.3 against 63.8 G node updates/s with bulk
+    // stores, but the 256-member ensemble of widths 256..2048 53.0 against
+    // 56.7 (four CTAs per SM instead of five)
+    return s->p.precision == LBM_FP32 && s->p.width % 4 == 0 && s->p.width >= kTunedBatchBulkMinWidth;
 }
 
 // The plain-load update's table for the current members (unpadded): about

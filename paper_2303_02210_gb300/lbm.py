@@ -55,7 +55,7 @@ class lbm_params_t(ctypes.Structure):
         ("front_kmax", ctypes.c_int32), ("wall_mode", ctypes.c_int32),
         ("negfix_mode", ctypes.c_int32), ("y_periodic", ctypes.c_int32),
         ("sim_id", ctypes.c_uint32), ("precision", ctypes.c_int32), ("update_kernel", ctypes.c_int32),
-        ("lattice", ctypes.c_int32),
+        ("lattice", ctypes.c_int32), ("plan_blocks", ctypes.c_int32),
     ]
 
 
@@ -164,6 +164,8 @@ def make_params(d: dict, precision: str = "fp32", update_kernel: str = "auto") -
         elif name == "lattice":
             v = d.get("lattice", "d2q9")
             v = LATTICES[v] if isinstance(v, str) else int(v)
+        elif name == "plan_blocks":
+            v = int(d.get("plan_blocks", 0))
         else:
             v = d[name]
             if name == "growth_mode" and isinstance(v, str):

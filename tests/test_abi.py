@@ -26,8 +26,9 @@ def test_exports_every_declared_function(lib):
 
 def test_struct_layouts_match_header():
     # 13 doubles, 1 uint64, 15 int32 words, padded to a multiple of 8 bytes
-    assert ctypes.sizeof(lbm.lbm_params_t) == 13 * 8 + 8 + 15 * 4 + 4
+    assert ctypes.sizeof(lbm.lbm_params_t) == 13 * 8 + 8 + 16 * 4
     assert lbm.lbm_params_t.lattice.offset == 13 * 8 + 8 + 14 * 4
+    assert lbm.lbm_params_t.plan_blocks.offset == 13 * 8 + 8 + 15 * 4
     assert ctypes.sizeof(lbm.lbm_stats_t) == 13 * 8 + 6 * 8 + 6 * 4
 
 

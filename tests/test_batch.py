@@ -251,8 +251,8 @@ def test_staged_batch_matches_single_stepping(precision, width4):
     lbm_step gives each alone, whatever kernel that uses, also interleaved
     with single steps."""
     from paper_2303_02210_gb300.lbm import Batch
-    staged = STAGED if not width4 else [  # bulk stores: members at least 2048 wide
-        (dict(p, width=2048 + 128 * i, sim_id=i), k) for i, (p, k) in enumerate(STAGED) if p["width"] % 4 == 0]
+    staged = STAGED if not width4 else [  # bulk stores: members at least the tuned width (4096) wide
+        (dict(p, width=4096 + 128 * i, sim_id=i), k) for i, (p, k) in enumerate(STAGED) if p["width"] % 4 == 0]
     ms = [(p, precision, k if precision == "fp32" or k != "tma_st" else "auto") for p, k in staged]
     members = [make(m) for m in ms]
     batch = Batch(members)
@@ -344,7 +344,7 @@ def test_slot_batch_recaptures_only_for_a_member_it_cannot_step():
     them up for a narrow member that takes a freed slot (one capture more),
     and the results stay exact."""
     from paper_2303_02210_gb300.lbm import Batch
-    wide = [(dict(p, width=2048 + 128 * i, sim_id=i), "fp32", "auto")
+    wide = [(dict(p, width=4096 + 128 * i, sim_id=i), "fp32", "auto")
             for i, (p, k) in enumerate(STAGED) if p["width"] % 4 == 0][:2]
     narrow = (dict(STAGED[0][0], sim_id=9), "fp32", "auto")
     sims = [make(m) for m in wide]
