@@ -535,7 +535,8 @@ int lbm_create(const lbm_params_t *p, void *stream, void *arena, uint64_t arena_
         const long long tiles = (long long)((p->width + kTmaBoxX - 1) / kTmaBoxX) * ((p->height + ty - 1) / ty);
         d.upd_ctas = (int)std::max<long long>(2, std::min<long long>((long long)ctas_per_sm * nsm, (tiles + 7) / 8));
         d.upd_magic = (uint32_t)((((uint64_t)1 << 32) + (uint64_t)d.upd_ctas - 1) / (uint64_t)d.upd_ctas);
-        if (d.upd_ctas > kTmaMaxCtas || tiles >= (1LL << 22)) {
+        // (tile / upd_ctas by the reciprocal is exact while tile * upd_ctas < 2^32)
+        if (d.upd_ctas > kTmaMaxCtas || tiles * (long long)d.upd_ctas >= (1LL << 32)) {
             s->use_tma = false;
             d.inject_in_update = 0;
         }

@@ -282,7 +282,7 @@ int lbm_record_cuda_error(cudaError_t e);
 // column W - 1.
 constexpr int kXO = 4;
 constexpr int kTmaBoxX = 128;
-constexpr int kTmaMaxCtas = 1024; // the reciprocal above is exact for tile < 2^22
+constexpr int kTmaMaxCtas = 2048; // the reciprocal above is exact for tile * upd_ctas < 2^32
 constexpr int kBucketCap = 256;    // division records listed per update CTA (more: full scan)
 constexpr int kPlanMaxBlocks = 1024;
 // The TMA-staged batched update: members one launch takes (its shared-memory

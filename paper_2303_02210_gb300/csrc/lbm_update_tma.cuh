@@ -66,26 +66,31 @@ constexpr size_t tma_smem_bytes()
 }
 
 // Configurations. Variant 0: tiles of two rows, 128 threads, five CTAs per
-// SM (20 warps, ten tiles in flight per SM); variant 1: tiles of four rows,
-// 256 threads, three CTAs per SM (24 warps, six tiles). Twice the staged
-// boxes per CTA for 16-bit storage (half the bytes each). Variant 0 gave
-// 81.0 against 85.1 us per step on the 4096 x 2048 FP32 workload (the two-row
-// boxes re-read more halo rows from the L2, but more, shorter tiles keep
-// more copies in flight). Variant 2 (FP32 only): variant 0's tiles, the
+// SM with two stages each (FP32: 20 warps, ten tiles in flight per SM), six
+// CTAs with two stages for 16-bit storage (its boxes are half the bytes;
+// measured at 8192 x 2048 FP16: 0.452 of the copy peak against 0.436 with
+// five CTAs of four stages; seven CTAs 0.246); variant 1: tiles of four
+// rows, 256 threads, three CTAs per SM (24 warps, six tiles). Variant 0 gave
+// 81.0 against 85.1 us per step on the 4096 x 2048 FP32 workload (the
+// two-row boxes re-read more halo rows from the L2, but more, shorter tiles
+// keep more copies in flight). Variant 2 (FP32 only): variant 0's tiles, the
 // results gathered in a shared output tile and written by one bulk tensor
-// store per tile instead of per-lane stores, four CTAs per SM. (A 16-bit
-// tile starts 4 elements = 8 bytes into a 16-byte unit, and a bulk tensor
-// store must start on a 16-byte boundary.)
+// store per tile instead of per-lane stores; one stage per CTA and six CTAs
+// per SM (the kernel is latency-bound: more warps beat a second stage; per
+// step at 4096 x 2048: 71.7 us against 73.2 with four CTAs of two stages,
+// 74.7 with five of one, 72.4 with seven of one). (A 16-bit tile starts 4
+// elements = 8 bytes into a 16-byte unit, and a bulk tensor store must start
+// on a 16-byte boundary.)
 template <typename S>
 struct TmaCfg {
-    static constexpr int TY0 = 2, CTAS0 = 5, STAGES0 = sizeof(S) == 4 ? 2 : 4;
+    static constexpr int TY0 = 2, CTAS0 = sizeof(S) == 4 ? 5 : 6, STAGES0 = sizeof(S) == 4 ? 2 : 2;
     static constexpr int TY1 = 4, CTAS1 = 3, STAGES1 = sizeof(S) == 4 ? 2 : 4;
-    static constexpr int TY2 = 2, CTAS2 = 4, STAGES2 = 2;
+    static constexpr int TY2 = 2, CTAS2 = 6, STAGES2 = 1;
 };
-static_assert(4 * (tma_smem_bytes<float, 2, 2, true>() + 1024) <= 228 * 1024, "four CTAs per SM by shared memory");
+static_assert(6 * (tma_smem_bytes<float, 2, 1, true>() + 1024) <= 228 * 1024, "six CTAs per SM by shared memory");
 static_assert(5 * (tma_smem_bytes<float, 2, 2>() + 1024) <= 228 * 1024, "five CTAs per SM by shared memory");
 static_assert(3 * (tma_smem_bytes<float, 4, 2>() + 1024) <= 228 * 1024, "three CTAs per SM by shared memory");
-static_assert(5 * (tma_smem_bytes<__half, 2, 4>() + 1024) <= 228 * 1024, "five CTAs per SM by shared memory");
+static_assert(6 * (tma_smem_bytes<__half, 2, 2>() + 1024) <= 228 * 1024, "six CTAs per SM by shared memory");
 static_assert(3 * (tma_smem_bytes<__half, 4, 4>() + 1024) <= 228 * 1024, "three CTAs per SM by shared memory");
 
 // Two adjacent stored elements as one access.
