@@ -290,6 +290,6 @@ constexpr int kPlanMaxBlocks = 1024;
 constexpr int kTmaBatchMaxSims = 256;
 constexpr int kMaxBatchSlots = 1024; // slots of a batch (the staged batched update: kTmaBatchMaxSims)
 constexpr int kTmaBatchCtasPerSm = 5;
-constexpr int kTmaBatchCtasPerSmStore = 4; // its bulk-store form
+constexpr int kTmaBatchCtasPerSmStore = 6; // its bulk-store form
 
 } // namespace lbm

@@ -41,9 +41,13 @@ constexpr size_t tma_batch_smem_bytes()
 template <typename S>
 struct TmaBatchCfg {
     static constexpr int STAGES = sizeof(S) == 4 ? 2 : 4, CTAS = kTmaBatchCtasPerSm;
-    static constexpr int CTAS_ST = 4; // the bulk-store form (FP32): the output tile takes a CTA's room
+    // the bulk-store form (FP32): one stage and six CTAs per SM, as the
+    // single-lattice bulk-store form (latency-bound: more warps beat a
+    // second stage)
+    static constexpr int STAGES_ST = 1, CTAS_ST = kTmaBatchCtasPerSmStore;
 };
-static_assert(4 * (tma_batch_smem_bytes<float, 2, true>() + 1024) <= 228 * 1024, "four CTAs per SM");
+static_assert(kTmaBatchCtasPerSmStore * (tma_batch_smem_bytes<float, 1, true>() + 1024) <= 228 * 1024,
+              "the bulk-store form's CTAs per SM by shared memory");
 static_assert(5 * (tma_batch_smem_bytes<float, 2>() + 1024) <= 228 * 1024, "five CTAs per SM");
 static_assert(5 * (tma_batch_smem_bytes<__half, 4>() + 1024) <= 228 * 1024, "five CTAs per SM");
 
@@ -431,19 +435,20 @@ cudaError_t launch_update_tma_batch_n(const MemberConst *mc, const CUtensorMap *
 {
     using C = TmaBatchCfg<S>;
     constexpr int CTAS = TSTORE ? C::CTAS_ST : C::CTAS;
+    constexpr int ST = TSTORE ? C::STAGES_ST : C::STAGES;
     static bool attr[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64 || !attr[dev]) {
-        e = cudaFuncSetAttribute(k_update_tma_batch<S, C::STAGES, CTAS, NOISE, TSTORE>,
+        e = cudaFuncSetAttribute(k_update_tma_batch<S, ST, CTAS, NOISE, TSTORE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tma_batch_smem_bytes<S, C::STAGES, TSTORE>());
+                                 (int)tma_batch_smem_bytes<S, ST, TSTORE>());
         if (e != cudaSuccess) return e;
         if (dev < 64) attr[dev] = true;
     }
-    k_update_tma_batch<S, C::STAGES, CTAS, NOISE, TSTORE>
-        <<<grid, TmaGeom<S, 2>::NT, tma_batch_smem_bytes<S, C::STAGES, TSTORE>(), s>>>(mc, maps, n);
+    k_update_tma_batch<S, ST, CTAS, NOISE, TSTORE>
+        <<<grid, TmaGeom<S, 2>::NT, tma_batch_smem_bytes<S, ST, TSTORE>(), s>>>(mc, maps, n);
     return cudaGetLastError();
 }
 
