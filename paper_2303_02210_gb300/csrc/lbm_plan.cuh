@@ -660,12 +660,15 @@ __global__ void __launch_bounds__(PLAN_NT) k_plan(SimDev d, int init)
 // floor (the barriers and the commit). With tau = ceil(sum of w / (cap - 1)),
 // a member with w >= tau is planned by G = floor(w / tau) blocks (at most
 // kPlanMaxBlocks; the grid barrier on its own arrival counter, reset at the
-// end of each launch, so the grid may change from step to step); the others
-// go, in slot order, into bins of about tau work, bin k holding the members
-// whose prefix of light work lies in [k tau, (k + 1) tau), and a bin's block
-// plans them one after another. The heavy members' blocks and the bins
-// number at most sum w / tau + 1 <= cap. Every block computes the same deal
-// from the same integers (prefixes over the slots, in slot order).
+// end of each launch, so the grid may change from step to step). The others
+// (light) each get a block of their own when the heavy members' blocks and
+// one per light member fit in the launch (a member's plan is mostly latency,
+// so two in one block take twice as long); else they go, in slot order, into
+// bins of about tau work, bin k holding the members whose prefix of light
+// work lies in [k tau, (k + 1) tau), and a bin's block plans them one after
+// another. The heavy members' blocks and the bins number at most
+// sum w / tau + 1 <= cap. Every block computes the same deal from the same
+// integers (counts and prefixes over the slots, in slot order).
 constexpr long long kPlanWorkFloor = 4096;
 
 __device__ __forceinline__ long long plan_slot_work(const SimDev *__restrict__ ds, int i)
@@ -692,6 +695,16 @@ __global__ void __launch_bounds__(PLAN_NT, 2) k_plan_batch(const SimDev *__restr
     wsum = plan_block_sum(wsum, s_red);
     if (wsum == 0) return; // (uniform: no members)
     const long long tau = (wsum + cap - 2) / (cap - 1);
+    // one block per light member if that fits with the heavy members' blocks
+    long long need = 0;
+    for (int i = tid; i < nslots; i += PLAN_NT) {
+        const long long w = plan_slot_work(ds, i);
+        if (w >= tau) need += w / tau < kPlanMaxBlocks ? w / tau : kPlanMaxBlocks;
+        else if (w >= 0) need += 1;
+    }
+    need = plan_block_sum(need, s_red);
+    const bool own = need <= cap;           // (uniform)
+    const long long bin = own ? 1 : tau;    // a bin's size in light-member units
     long long hrun = 0, lrun = 0;
     for (int base = 0; base < nslots; base += PLAN_NT) {
         const int i = base + tid;
@@ -699,7 +712,7 @@ __global__ void __launch_bounds__(PLAN_NT, 2) k_plan_batch(const SimDev *__restr
         if (i < nslots) {
             const long long w = plan_slot_work(ds, i);
             if (w >= tau) hg = w / tau < kPlanMaxBlocks ? w / tau : kPlanMaxBlocks;
-            else if (w >= 0) lw = w;
+            else if (w >= 0) lw = own ? 1 : w;
         }
         // two exclusive block scans (64-bit: the work sums)
         long long ih = hg, il = lw;
@@ -753,8 +766,9 @@ __global__ void __launch_bounds__(PLAN_NT, 2) k_plan_batch(const SimDev *__restr
         plan_body<S, LT>(ds[lo], 0, G, b - s_hpre[lo]);
         return;
     }
-    // bin k: the light members whose work prefix lies in [k tau, (k + 1) tau)
-    const long long k = b - hrun, lo_w = k * tau, hi_w = lo_w + tau;
+    // bin k: the light members whose prefix (of work, or of members when
+    // each has its own block) lies in [k bin, (k + 1) bin)
+    const long long k = b - hrun, lo_w = k * bin, hi_w = lo_w + bin;
     if (lo_w >= lrun) return; // (uniform: no such bin)
     int lo = 0, hi = nslots; // the first slot with s_lpre >= lo_w
     while (lo < hi) {
