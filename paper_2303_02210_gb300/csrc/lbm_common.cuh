@@ -291,5 +291,6 @@ constexpr int kTmaBatchMaxSims = 256;
 constexpr int kMaxBatchSlots = 1024; // slots of a batch (the staged batched update: kTmaBatchMaxSims)
 constexpr int kTmaBatchCtasPerSm = 5;
 constexpr int kTmaBatchCtasPerSmStore = 6; // its bulk-store form
+constexpr int kTmaBatchChunk = 8;          // consecutive tiles dealt to one CTA of the staged batched update
 
 } // namespace lbm

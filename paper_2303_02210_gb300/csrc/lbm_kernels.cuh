@@ -83,16 +83,28 @@ struct PopShifted {
         const int k = wclass(q);
         return k == 0 ? c0 : (k == 1 ? c1 : c2);
     }
-    __device__ float ld(S v, int q) const { return Cvt::to_f(v) + shift(q); }
+    __device__ float ld(S v, int q) const { return Cvt::add(v, shift(q)); }
     __device__ S st(float v, int q) const { return Cvt::from_f(v - shift(q)); }
 };
+// add(v, s) = to_f(v) + s. BF16: one mixed-precision add (sm_100 and later;
+// the 16-bit operand is widened exactly and the sum rounded once to nearest
+// in FP32, the same value as the conversion followed by an FP32 add), which
+// measured 0.7% faster per update than the conversion and add at 8192 x 2048;
+// FP16 keeps the conversion and add (the mixed add measured 2.4% slower).
 struct CvtHalf {
     static __device__ float to_f(__half v) { return __half2float(v); }
     static __device__ __half from_f(float v) { return __float2half_rn(v); }
+    static __device__ float add(__half v, float s) { return __half2float(v) + s; }
 };
 struct CvtBf16 {
     static __device__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+    static __device__ float add(__nv_bfloat16 v, float s)
+    {
+        float r;
+        asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(__bfloat16_as_ushort(v)), "f"(s));
+        return r;
+    }
 };
 template <>
 struct Pop<__half> : PopShifted<__half, CvtHalf> {

@@ -122,8 +122,8 @@ __device__ __forceinline__ typename Pair2<S>::T enc_pair(float a, float b, int q
     }
 }
 
-// Decodes a stored pair of plane class q to FP32 (16-bit storage: one packed
-// conversion and one packed add of the shift; per element exactly Pop::ld).
+// Decodes a stored pair of plane class q to FP32 (FP16: one packed conversion
+// and one packed add of the shift; per element exactly Pop::ld).
 template <typename S>
 __device__ __forceinline__ float2 dec_pair(typename Pair2<S>::T v, int q, const Pop<S> &pc)
 {
@@ -132,7 +132,7 @@ __device__ __forceinline__ float2 dec_pair(typename Pair2<S>::T v, int q, const 
     } else if constexpr (std::is_same<S, __half>::value) {
         return add2(__half22float2(v), f2(pc.shift(q)));
     } else {
-        return add2(__bfloat1622float2(v), f2(pc.shift(q)));
+        return make_float2(pc.ld(v.x, q), pc.ld(v.y, q)); // (one mixed-precision add each)
     }
 }
 
