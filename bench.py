@@ -567,7 +567,7 @@ def main():
     # of that step's front heights and exact Eq. 6 sums into pinned host
     # buffers (lbm_front_heights_async, no wait per step), one wait at the end,
     # Eq. 6 worked out on the host for every step, lbm_destroy
-    from paper_2303_02210_gb300.lbm import lbm_eq6
+    from paper_2303_02210_gb300.lbm import lbm_eq6_n
     # (a fixed job of 1000 steps, whatever --steps is)
     e2e_steps = 1000
     W = params["width"]
@@ -581,7 +581,7 @@ def main():
         sim2.step(1)
         sim2.lbm_front_heights_async(hbuf[k], sbuf[k])
     sim2.sync()
-    eq6 = [lbm_eq6(a, b, W) for a, b in sbuf.tolist()]
+    eq6 = lbm_eq6_n(sbuf, W)[1]
     st2 = sim2.stats()
     sim2.close()
     torch.cuda.synchronize()
@@ -623,7 +623,7 @@ def main():
                 "d2h_bytes_per_step": d2h,
                 "what": (f"lbm_create from host parameters, then {e2e_steps} x (lbm_step(1) + "
                          f"lbm_front_heights_async of that step's heights and Eq. 6 sums into pinned host "
-                         f"buffers), one wait, Eq. 6 on the host for every step, lbm_destroy")},
+                         f"buffers), one wait, Eq. 6 on the host for every step (lbm_eq6_n), lbm_destroy")},
         "gpu_launches": int(launches),
         "clocks": clk,
         "status": status,

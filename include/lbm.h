@@ -195,6 +195,13 @@ int lbm_front_heights_async(lbm_sim *sim, int32_t *h_host, int64_t *sums_host);
  * double, as the kernels' FP64 wall rule). Host only. */
 int lbm_eq6(int64_t s1, int64_t s2, int32_t width, double *hbar, double *w);
 
+/* lbm_eq6 for n pairs (Sec. III, Eq. 6): sums holds n (S1, S2) pairs, the
+ * layout lbm_front_heights_async writes (int64 [n][2]); hbar[i] and w[i]
+ * receive pair i's values, bit for bit those of lbm_eq6. All arrays are the
+ * caller's host memory. LBM_ERR_INVALID_ARG if width < 1, n < 0, or a
+ * pointer is NULL while n > 0. Host only. */
+int lbm_eq6_n(const int64_t *sums, int64_t n, int32_t width, double *hbar, double *w);
+
 /* Density rho = sum_i f_i and velocity u = sum_i f_i e_i / rho (Eq. 1; u = 0
  * where rho = 0) of the current populations into caller host arrays of W*H
  * doubles, row-major [y][x]. Syncs. */

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -190,14 +191,32 @@ void front_rows(const lbm_params_t &p, std::vector<int32_t> &rows)
             const u32x4 r = philox4x32_10(u32x4{(uint32_t)k, 1u, STREAM_INIT, p.sim_id}, pk);
             phi.push_back(two_pi * u01(r.x));
         }
-        double smax = 0.0;
-        for (int x = 0; x < W; ++x) {
-            double S = 0.0;
-            for (int k = p.front_kmin; k <= p.front_kmax; ++k)
-                S = S + std::sin(((two_pi * (double)k) * (double)x) / (double)W + phi[k - p.front_kmin]);
-            h0[x] = S;
-            if (std::fabs(S) > smax) smax = std::fabs(S);
+        // each column's sum in the same order whatever thread forms it (so
+        // the values do not depend on the split); columns split over host
+        // threads when the sum is long (4096 columns x 64 modes: ~4 ms on one
+        // core, inside every lbm_create of the benchmark workload)
+        auto columns = [&](int x0, int x1) {
+            for (int x = x0; x < x1; ++x) {
+                double S = 0.0;
+                for (int k = p.front_kmin; k <= p.front_kmax; ++k)
+                    S = S + std::sin(((two_pi * (double)k) * (double)x) / (double)W + phi[k - p.front_kmin]);
+                h0[x] = S;
+            }
+        };
+        const long long work = (long long)W * (long long)phi.size();
+        const int nt = (int)std::min<long long>({(long long)std::max(1u, std::thread::hardware_concurrency()), 16LL,
+                                                 work / 16384 + 1});
+        if (nt <= 1) {
+            columns(0, W);
+        } else {
+            std::vector<std::thread> pool;
+            for (int i = 1; i < nt; ++i) pool.emplace_back(columns, (int)((long long)W * i / nt), (int)((long long)W * (i + 1) / nt));
+            columns(0, (int)((long long)W / nt));
+            for (std::thread &t : pool) t.join();
         }
+        double smax = 0.0;
+        for (int x = 0; x < W; ++x)
+            if (std::fabs(h0[x]) > smax) smax = std::fabs(h0[x]);
         for (int x = 0; x < W; ++x)
             h0[x] = smax > 0.0 ? p.front_row + p.front_amp * (h0[x] / smax) : p.front_row;
     }
@@ -732,6 +751,13 @@ int lbm_eq6(int64_t s1, int64_t s2, int32_t width, double *hbar, double *w)
 {
     if (width < 1 || !hbar || !w) return LBM_ERR_INVALID_ARG;
     eq6((long long)s1, (long long)s2, width, hbar, w);
+    return LBM_OK;
+}
+
+int lbm_eq6_n(const int64_t *sums, int64_t n, int32_t width, double *hbar, double *w)
+{
+    if (width < 1 || n < 0 || (n > 0 && (!sums || !hbar || !w))) return LBM_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < n; ++i) eq6((long long)sums[2 * i], (long long)sums[2 * i + 1], width, &hbar[i], &w[i]);
     return LBM_OK;
 }
 

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "lbm_front_heights_async": (ctypes.c_int, [_P, _P, _P]),
     "lbm_eq6": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]),
+    "lbm_eq6_n": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, _P]),
     "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_params_t), _P, _P, ctypes.c_uint64,
                                   ctypes.POINTER(_P)]),
     "lbm_step": (ctypes.c_int, [_P, ctypes.c_int64]),
@@ -205,6 +206,20 @@ def lbm_eq6(s1: int, s2: int, width: int):
     hbar, w = ctypes.c_double(), ctypes.c_double()
     _check(load_library().lbm_eq6(int(s1), int(s2), int(width), ctypes.byref(hbar), ctypes.byref(w)), "lbm_eq6")
     return hbar.value, w.value
+
+
+def lbm_eq6_n(sums, width: int):
+    """Eq. 6 for n (S1, S2) pairs: `sums` is a host int64 array or CPU tensor
+    of shape (n, 2) (the layout lbm_front_heights_async writes); returns
+    float64 arrays (hbar, w) of length n, each pair as lbm_eq6 gives it."""
+    import numpy as np
+    a = np.ascontiguousarray(sums.numpy() if hasattr(sums, "numpy") else sums, dtype=np.int64).reshape(-1, 2)
+    n = a.shape[0]
+    hbar = np.empty(n, dtype=np.float64)
+    w = np.empty(n, dtype=np.float64)
+    _check(load_library().lbm_eq6_n(_P(a.ctypes.data), n, int(width), _P(hbar.ctypes.data), _P(w.ctypes.data)),
+           "lbm_eq6_n")
+    return hbar, w
 
 
 def lbm_front_heights_noalloc(mask_dev, width: int, height: int, heights_dev, stats_dev, stream=None):

@@ -103,6 +103,20 @@ def test_eq6_host_helper_matches_mean_and_population_std(lib):
     assert lib.lbm_eq6(1, 1, 0, None, None) == -1
 
 
+def test_eq6_n_matches_eq6_pair_by_pair(lib):
+    rng = np.random.default_rng(6)
+    for W in (1, 37, 4096):
+        h = rng.integers(0, 3000, (50, W)).astype(np.int64)
+        sums = np.stack([h.sum(1), (h * h).sum(1)], axis=1)
+        hbar, w = lbm.lbm_eq6_n(sums, W)
+        for k in range(len(sums)):
+            assert (hbar[k], w[k]) == lbm.lbm_eq6(int(sums[k, 0]), int(sums[k, 1]), W)
+    assert lib.lbm_eq6_n(None, 0, 5, None, None) == 0
+    assert lib.lbm_eq6_n(None, 1, 5, None, None) == -1
+    assert lib.lbm_eq6_n(None, -1, 5, None, None) == -1
+    assert lib.lbm_eq6_n(None, 0, 0, None, None) == -1
+
+
 def test_plan_capacity_grows_with_growth_rate_and_lattice():
     a = lbm.lbm_plan_capacity(wl.lattice_small())
     b = lbm.lbm_plan_capacity(wl.lattice_small(growth_rate=1e-3))
