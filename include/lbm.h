@@ -186,9 +186,11 @@ int lbm_front_heights(lbm_sim *sim, int32_t *h_host, double *hbar, double *w);
 /* The same without waiting: enqueues on the simulation's stream the copies of
  * h(x) into h_host (W int32; NULL skips it) and of the exact Eq. 6 sums
  * S1 = sum h, S2 = sum h^2 into sums_host[0..1]. Host buffers should be
- * pinned (cudaHostAlloc) for the copies to be asynchronous; they hold the
- * values once the stream has reached this point (lbm_sync). Eq. 6 from the
- * sums: lbm_eq6. Enqueues only. */
+ * pinned (cudaHostAlloc, cudaHostRegister) for the copies to be
+ * asynchronous; pinned buffers that the device can address are written by
+ * one small kernel, others by cudaMemcpyAsync. They hold the values once
+ * the stream has reached this point (lbm_sync). Eq. 6 from the sums:
+ * lbm_eq6 or lbm_eq6_n. Enqueues only. */
 int lbm_front_heights_async(lbm_sim *sim, int32_t *h_host, int64_t *sums_host);
 
 /* Eq. 6 from the exact sums: hbar = S1 / W, w = sqrt(W S2 - S1^2) / W (IEEE

@@ -295,6 +295,34 @@ struct lbm_sim {
     int64_t timing_stride, timing_count;
 };
 
+namespace {
+// Copies the front heights (W int32) and the two Eq. 6 sums into host memory
+// that the device can address (pinned, mapped), by stores from the GPU: one
+// small launch in place of two copy-engine transfers, each of which would
+// stall the stream for several microseconds between two steps.
+__global__ void k_export_front(const int32_t *__restrict__ h, const long long *__restrict__ s12, int W,
+                               int32_t *h_out, long long *s_out)
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); // (the next update may start its prologue)
+    const int stride = (int)(gridDim.x * blockDim.x);
+    if (h_out)
+        for (int i = (int)(blockIdx.x * blockDim.x + threadIdx.x); i < W; i += stride) h_out[i] = h[i];
+    if (blockIdx.x == 0 && threadIdx.x < 2) s_out[threadIdx.x] = s12[threadIdx.x];
+}
+
+// The device's address of host memory p, or nullptr if the current device
+// cannot address it (pageable memory, or pinned memory not mapped for it).
+void *device_alias(void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError(); // (pageable memory may leave an error on older runtimes)
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+} // namespace
+
 extern "C" {
 
 int lbm_validate(const lbm_params_t *p)
@@ -741,8 +769,17 @@ int lbm_front_heights_async(lbm_sim *s, int32_t *h_host, int64_t *sums_host)
 {
     if (!s || !sums_host) return LBM_ERR_INVALID_ARG;
     USE_DEVICE(s);
+    const int W = s->p.width;
+    int32_t *h_dev = h_host ? (int32_t *)device_alias(h_host) : nullptr;
+    long long *s_dev = (long long *)device_alias(sums_host);
+    if (s_dev && (h_dev || !h_host)) {
+        const int blocks = std::min((W + 255) / 256, 32);
+        k_export_front<<<blocks, 256, 0, s->stream>>>(s->d.heights, &s->d.sc->S1, W, h_dev, s_dev);
+        CK(cudaGetLastError());
+        return LBM_OK;
+    }
     if (h_host)
-        CK(cudaMemcpyAsync(h_host, s->d.heights, sizeof(int32_t) * s->p.width, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(h_host, s->d.heights, sizeof(int32_t) * W, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(sums_host, &s->d.sc->S1, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s->stream));
     return LBM_OK;
 }

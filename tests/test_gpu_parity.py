@@ -307,24 +307,32 @@ def test_runaway_mass_is_flagged_not_faulting():
     assert h.max() <= 128
 
 
-def test_async_heights_readback_equals_the_synchronous_one():
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+def test_async_heights_readback_equals_the_synchronous_one(pinned):
     """lbm_front_heights_async copies every step's heights and exact Eq. 6
-    sums into pinned buffers without waiting; after one wait they hold what
-    lbm_front_heights returns step by step."""
+    sums into host buffers without waiting (pinned buffers the device can
+    address: stores by a small kernel; pageable ones: cudaMemcpyAsync);
+    after one wait they hold what lbm_front_heights returns step by step."""
     import torch
-    from paper_2303_02210_gb300.lbm import Simulation, lbm_eq6
-    p = wl.lattice_small(seed=3, growth_rate=3e-3, front_kind="sinusoidal", front_amp=3.0, front_kmax=8)
+    from paper_2303_02210_gb300.lbm import Simulation, lbm_eq6, lbm_eq6_n
+    p = wl.lattice_small(seed=3, growth_rate=3e-3, front_kind="sinusoidal", front_amp=3.0, front_kmax=8,
+                         width=300)
     a, b = gpu_sim(p, "fp32"), gpu_sim(p, "fp32")
     n = 20
-    hb = torch.empty((n, p["width"]), dtype=torch.int32, pin_memory=True)
-    sb = torch.empty((n, 2), dtype=torch.int64, pin_memory=True)
+    hb = torch.full((n, p["width"]), -7, dtype=torch.int32, pin_memory=pinned)
+    sb = torch.full((n, 2), -7, dtype=torch.int64, pin_memory=pinned)
+    sb_only = torch.full((n, 2), -7, dtype=torch.int64, pin_memory=pinned)
     want = []
     for k in range(n):
         a.step(1)
         a.lbm_front_heights_async(hb[k], sb[k])
+        a.lbm_front_heights_async(None, sb_only[k])
         b.step(1)
         want.append(b.front_heights())
     a.sync()
+    hbar_n, w_n = lbm_eq6_n(sb, p["width"])
     for k, (h, hbar, w) in enumerate(want):
         assert np.array_equal(hb[k].numpy(), h)
         assert lbm_eq6(int(sb[k, 0]), int(sb[k, 1]), p["width"]) == (hbar, w)
+        assert (hbar_n[k], w_n[k]) == (hbar, w)
+    assert np.array_equal(sb_only.numpy(), sb.numpy())
