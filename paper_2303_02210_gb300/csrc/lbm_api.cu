@@ -300,10 +300,13 @@ namespace {
 // that the device can address (pinned, mapped), by stores from the GPU: one
 // small launch in place of two copy-engine transfers, each of which would
 // stall the stream for several microseconds between two steps.
+// Launched as a programmatic dependent of the planner: it may start while the
+// planner finishes and waits for it before reading.
 __global__ void k_export_front(const int32_t *__restrict__ h, const long long *__restrict__ s12, int W,
                                int32_t *h_out, long long *s_out)
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); // (the next update may start its prologue)
+    asm volatile("griddepcontrol.wait;" ::: "memory");               // what the planner wrote
     const int stride = (int)(gridDim.x * blockDim.x);
     if (h_out)
         for (int i = (int)(blockIdx.x * blockDim.x + threadIdx.x); i < W; i += stride) h_out[i] = h[i];
@@ -773,9 +776,17 @@ int lbm_front_heights_async(lbm_sim *s, int32_t *h_host, int64_t *sums_host)
     int32_t *h_dev = h_host ? (int32_t *)device_alias(h_host) : nullptr;
     long long *s_dev = (long long *)device_alias(sums_host);
     if (s_dev && (h_dev || !h_host)) {
-        const int blocks = std::min((W + 255) / 256, 32);
-        k_export_front<<<blocks, 256, 0, s->stream>>>(s->d.heights, &s->d.sc->S1, W, h_dev, s_dev);
-        CK(cudaGetLastError());
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)std::min((W + 255) / 256, 32));
+        cfg.blockDim = dim3(256);
+        cfg.stream = s->stream;
+        cudaLaunchAttribute la[1];
+        la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        la[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = la;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, k_export_front, (const int32_t *)s->d.heights, (const long long *)&s->d.sc->S1, W,
+                              h_dev, s_dev));
         return LBM_OK;
     }
     if (h_host)
